@@ -1,0 +1,210 @@
+"""h-/p-multigrid hierarchy, point smoothers, V-cycle and the two outer solvers (oracle).
+
+TEST INFRASTRUCTURE ONLY. Follows the paper:
+
+* Sec. 3.1.1 / 3.1.2 and Sec. 4.3: h-multigrid keeps p and halves the mesh; p-multigrid
+  halves p down to 1 and then coarsens the mesh; "three meshes" per hierarchy;
+  every level is rediscretized (mu evaluated at that level's quadrature points).
+* Sec. 3.2.1 / 3.2.2: point-Jacobi with omega = 2/3; Chebyshev-accelerated Jacobi
+  targeting [lambda_max/4, lambda_max] of D^-1 A, lambda_max from 10 Arnoldi iterations.
+* Sec. 3.2.2 / 4.3: V-cycle with nu_pre / nu_post smoothing steps and an exact solve
+  on the coarsest grid; MG as solver until the residual norm drops by 1e8.
+* Algorithm 1: MG-preconditioned CG, one V-cycle per iteration.
+
+Readings where the paper is silent or garbled (the CUDA library follows the same):
+* Chebyshev: the three-term recurrence of Saad, "Iterative Methods for Sparse Linear
+  Systems" (2nd ed.), Alg. 12.1, applied to D^-1 A with an explicit residual each step;
+  the polynomial degree equals the number of smoothing steps.
+* Arnoldi: modified Gram-Schmidt on D^-1 A (interior unknowns) from a SplitMix64
+  U(-1,1) start vector (counter = global node number, seed 0x1402593800000000 + level),
+  lambda = largest real part of the Ritz values; min(10, n) steps on an n-unknown level.
+* Algorithm 1 uses rho before computing it; it is read as standard PCG:
+  r0 = b - A u0, z0 = V(r0), p0 = z0, then alpha = (z,r)/(p,Ap), ..., beta = (z',r')/(z,r).
+* Stopping: ||r||_2 <= rtol * ||r_0||_2 over interior unknowns, u0 = 0.
+* Coarsest grid: dense Cholesky factorization (exact solve).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from .fem import Discretization
+from .transfer import prolongation
+
+ARNOLDI_SEED = 0x1402593800000000
+
+
+def _splitmix64_uniform(seed, counters):
+    """SplitMix64 (Steele, Lea & Flood 2014) in counter form, output mapped to U(-1,1):
+    z = seed + (c+1)*0x9E3779B97F4A7C15; z = (z^(z>>30))*0xBF58476D1CE4E5B9;
+    z = (z^(z>>27))*0x94D049BB133111EB; z ^= z>>31; u = 2*(z>>11)*2^-53 - 1."""
+    mask = (1 << 64) - 1
+    out = np.empty(len(counters))
+    for k, c in enumerate(counters):
+        z = (seed + (int(c) + 1) * 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z = z ^ (z >> 31)
+        out[k] = 2.0 * (z >> 11) * (2.0 ** -53) - 1.0
+    return out
+
+
+def level_shapes(prob):
+    """(nelem, p) of every level, finest first (Sec. 4.3)."""
+    E = tuple(prob["nelem"])
+    p = int(prob["order"])
+    out = [(E, p)]
+    if prob["hier"] == "p":
+        while p > 1:
+            p = max(1, p // 2)
+            out.append((E, p))
+    n_h = int(prob["n_hlevels"])
+    for _ in range(n_h - 1):
+        if any(e % 2 for e in E):
+            raise ValueError("mesh cannot be halved")
+        E = tuple(e // 2 for e in E)
+        out.append((E, p))
+    return out
+
+
+class Level:
+    def __init__(self, disc: Discretization):
+        self.disc = disc
+        self.A = disc.stiffness()
+        self.dinv = 1.0 / self.A.diagonal()
+        self.P = None          # prolongation from the next coarser level to this one
+        self.lam = None
+        self.chol = None
+
+
+class Hierarchy:
+    def __init__(self, prob, arnoldi=True):
+        self.prob = prob
+        self.levels = []
+        for E, p in level_shapes(prob):
+            disc = Discretization(prob["dim"], E, p, warp_amp=prob["warp_amp"],
+                                  mu_a=prob["mu_a"], mu_b=prob["mu_b"], mu_k=prob["mu_k"])
+            self.levels.append(Level(disc))
+        for k in range(len(self.levels) - 1):
+            self.levels[k].P = prolongation(self.levels[k].disc, self.levels[k + 1].disc)
+        last = self.levels[-1]
+        last.chol = sla.cho_factor(last.A.toarray(), lower=True)
+        if arnoldi and prob["smoother"] == "cheb":
+            for k, L in enumerate(self.levels[:-1]):
+                L.lam = arnoldi_lambda_max(L, int(prob["arnoldi_iters"]), ARNOLDI_SEED + k)
+        self.fine_applies = 0
+
+    @property
+    def fine(self):
+        return self.levels[0]
+
+    # ------------------------------------------------------------------ smoothers
+    def _apply(self, k, x):
+        if k == 0:
+            self.fine_applies += 1
+        return self.levels[k].A @ x
+
+    def jacobi(self, k, b, x, steps):
+        """x <- x + omega D^-1 (b - A x), `steps` times (Sec. 3.2.2, omega = 2/3)."""
+        L, w = self.levels[k], self.prob["omega"]
+        for s in range(steps):
+            r = b if x is None else b - self._apply(k, x)
+            x = (0.0 if x is None else x) + w * L.dinv * r
+        return x
+
+    def chebyshev(self, k, b, x, steps):
+        """Chebyshev acceleration of Jacobi on [lo, hi] = [frac*s*lam, s*lam] (Saad Alg. 12.1)."""
+        L = self.levels[k]
+        hi = self.prob["cheb_safety"] * L.lam
+        lo = self.prob["cheb_lo_frac"] * hi
+        theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        r = b if x is None else b - self._apply(k, x)
+        d = L.dinv * r / theta
+        x = d.copy() if x is None else x + d
+        for s in range(1, steps):
+            r = b - self._apply(k, x)
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            d = rho_new * rho * d + (2.0 * rho_new / delta) * L.dinv * r
+            x = x + d
+            rho = rho_new
+        return x
+
+    def smooth(self, k, b, x, steps):
+        if steps == 0:
+            return np.zeros_like(b) if x is None else x
+        if self.prob["smoother"] == "jacobi":
+            return self.jacobi(k, b, x, steps)
+        return self.chebyshev(k, b, x, steps)
+
+    # ------------------------------------------------------------------ V-cycle
+    def vcycle(self, b, x=None, k=0):
+        """One V(nu_pre, nu_post) cycle on level k; x=None means a zero initial guess."""
+        L = self.levels[k]
+        if k == len(self.levels) - 1:
+            return sla.cho_solve(L.chol, b)
+        x = self.smooth(k, b, x, self.prob["nu_pre"])
+        r = b - self._apply(k, x)
+        rc = L.P.T @ r
+        ec = self.vcycle(rc, None, k + 1)
+        x = x + L.P @ ec
+        return self.smooth(k, b, x, self.prob["nu_post"])
+
+    # ------------------------------------------------------------------ solvers
+    def solve_mg(self, b, rtol=1e-8, maxit=1000):
+        """MG as solver: V-cycles until ||b - A x|| <= rtol ||b|| (x0 = 0)."""
+        x = np.zeros_like(b)
+        r0 = np.linalg.norm(b)
+        hist = [r0]
+        for it in range(1, maxit + 1):
+            x = self.vcycle(b, None if it == 1 else x)
+            r = b - self._apply(0, x)
+            hist.append(np.linalg.norm(r))
+            if hist[-1] <= rtol * r0:
+                return x, it, np.array(hist), True
+        return x, maxit, np.array(hist), False
+
+    def solve_pcg(self, b, rtol=1e-8, maxit=1000):
+        """Algorithm 1 (read as standard PCG, x0 = 0), one V-cycle per iteration."""
+        u = np.zeros_like(b)
+        r = b.copy()
+        r0 = np.linalg.norm(r)
+        hist = [r0]
+        z = self.vcycle(r)
+        p = z.copy()
+        rho = z @ r
+        for it in range(1, maxit + 1):
+            h = self._apply(0, p)
+            alpha = rho / (p @ h)
+            u = u + alpha * p
+            r = r - alpha * h
+            hist.append(np.linalg.norm(r))
+            if hist[-1] <= rtol * r0:
+                return u, it, np.array(hist), True
+            z = self.vcycle(r)
+            rho_new = z @ r
+            beta = rho_new / rho
+            rho = rho_new
+            p = z + beta * p
+        return u, maxit, np.array(hist), False
+
+
+def arnoldi_lambda_max(L: Level, iters: int, seed: int):
+    """Largest real part of the Ritz values of D^-1 A after `iters` Arnoldi steps
+    (modified Gram-Schmidt) from a seeded start vector."""
+    disc = L.disc
+    v = _splitmix64_uniform(seed, disc.interior)
+    m = min(iters, disc.n_interior)
+    H = np.zeros((m + 1, m))
+    V = [v / np.linalg.norm(v)]
+    for j in range(m):
+        w = L.dinv * (L.A @ V[j])
+        for i in range(j + 1):
+            H[i, j] = w @ V[i]
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if j + 1 < m:
+            V.append(w / H[j + 1, j])
+    ritz = np.linalg.eigvals(H[:m, :m])
+    return float(np.max(ritz.real))

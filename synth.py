@@ -1,0 +1,81 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the multigrid method: it only draws random
+numbers (SplitMix64, Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) and describes the workloads as plain parameter sets.
+
+Workloads follow the paper's test problems (Sec. 4.1: unit square/cube, constant
+or strongly varying coefficient on a warped domain) at the sizes used by the
+benchmarks of this library; the warp map and coefficient amplitude are given
+explicitly because the paper only shows its warped meshes as a figure (Fig. 4).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """Outputs start..start+count-1 of the SplitMix64 stream seeded with `seed`.
+
+    Counter form: output_i = mix(seed + (i + 1) * gamma) (mod 2^64).
+    """
+    with np.errstate(over="ignore"):
+        i = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * GOLDEN_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_pm1(seed: int, count: int, start: int = 0) -> np.ndarray:
+    """U(-1,1) doubles: 2 * (z >> 11) * 2^-53 - 1."""
+    z = splitmix64(seed, count, start)
+    return 2.0 * (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) - 1.0
+
+
+def nodal_field(seed: int, n_nodes: int) -> np.ndarray:
+    """Seeded nodal right-hand-side samples f ~ U(-1,1), one per global node."""
+    return uniform_pm1(seed, n_nodes)
+
+
+# ---------------------------------------------------------------------------
+# Workload descriptions (plain parameters; both implementations read them).
+# mu(x) = mu_a + mu_b * sum_i cos^2(mu_k * pi * x_i); warp x_i += amp * prod_j sin(pi x_j)
+# ---------------------------------------------------------------------------
+
+def problem(dim, nelem, order, *, warp_amp=0.0, mu_a=1.0, mu_b=0.0, mu_k=2.0,
+            hier="h", n_hlevels=3, smoother="cheb", nu_pre=3, nu_post=3,
+            omega=2.0 / 3.0, arnoldi_iters=10, cheb_lo_frac=0.25, cheb_safety=1.0):
+    if isinstance(nelem, int):
+        nelem = (nelem,) * dim
+    return dict(dim=dim, nelem=tuple(nelem), order=order, warp_amp=warp_amp,
+                mu_a=mu_a, mu_b=mu_b, mu_k=mu_k, hier=hier, n_hlevels=n_hlevels,
+                smoother=smoother, nu_pre=nu_pre, nu_post=nu_post, omega=omega,
+                arnoldi_iters=arnoldi_iters, cheb_lo_frac=cheb_lo_frac,
+                cheb_safety=cheb_safety)
+
+
+def mms2d_poisson(nelem=8, order=4, **kw):
+    """2D unit square, mu = 1, Q_order on nelem^2 affine quads, h-MG V(2,2) Chebyshev:
+    manufactured u = sin(pi x) sin(pi y), f = 2 pi^2 sin(pi x) sin(pi y)."""
+    base = dict(hier="h", n_hlevels=3, smoother="cheb", nu_pre=2, nu_post=2)
+    base.update(kw)
+    return problem(2, nelem, order, **base)
+
+
+def warped_var3d(nelem=16, order=4, hier="h", **kw):
+    """3D warped cube (amp 0.1), mu = 1 + 1e3 sum cos^2(2 pi x_i), V(3,3) Chebyshev."""
+    base = dict(warp_amp=0.1, mu_a=1.0, mu_b=1.0e3, mu_k=2.0, hier=hier,
+                n_hlevels=3, smoother="cheb", nu_pre=3, nu_post=3)
+    base.update(kw)
+    return problem(3, nelem, order, **base)
+
+
+# Seeds of the nodal right-hand sides for the 3D workloads.
+SEED_WARPED_VAR3D = 2
+SEED_PSWEEP3D = 3

@@ -1,0 +1,142 @@
+"""Pins of the oracle's discretization (Sec. 2.1, 2.3): textbook stencils, brute-force
+quadrature, operator invariants, an exact patch test and manufactured-solution
+convergence at the rate O(h^(p+1))."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fem
+
+
+def test_q1_square_element_matrix_textbook():
+    # Bilinear element on the unit square, mu = 1: diagonal 2/3, edge neighbours -1/6,
+    # the opposite corner -1/3 (local order (0,0),(1,0),(0,1),(1,1)).
+    d = fem.Discretization(2, 1, 1)
+    K = d.element_matrices([0])[0]
+    ref = np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6.0
+    assert np.allclose(K, ref, atol=1e-15)
+
+
+def test_q1_assembled_stencils_2d_3d():
+    d2 = fem.Discretization(2, 4, 1)
+    A2 = d2.assemble().toarray()
+    g = 2 * 5 + 2                                   # centre node of the 5x5 grid
+    row = A2[g].reshape(5, 5)[1:4, 1:4]
+    # bilinear Laplacian 9-point stencil: centre 8/3, all eight neighbours -1/3
+    assert np.isclose(row[1, 1], 8 / 3)
+    nb = np.delete(row.ravel(), 4)
+    assert np.allclose(nb, -1 / 3)
+    assert abs(A2[g].sum()) < 1e-14
+    # 3D trilinear Laplacian on a uniform grid (spacing h = 1/4): centre 8h/3, faces 0,
+    # edges -h/6, corners -h/12.
+    d3 = fem.Discretization(3, 4, 1)
+    A3 = d3.assemble()
+    g = (2 * 5 + 2) * 5 + 2
+    row = A3[g].toarray().reshape(5, 5, 5)[1:4, 1:4, 1:4]
+    h = 0.25
+    cnt = np.abs(np.indices((3, 3, 3)) - 1).sum(axis=0)
+    assert np.isclose(row[1, 1, 1], 8 * h / 3)
+    assert np.allclose(row[cnt == 1], 0.0, atol=1e-15)
+    assert np.allclose(row[cnt == 2], -h / 6)
+    assert np.allclose(row[cnt == 3], -h / 12)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 3), (2, 6), (3, 2), (3, 3)])
+def test_affine_elements_exact_with_p_plus_1_gauss_points(dim, p):
+    # Rectangular (affine) elements, mu = 1: q = p+1 integrates the stiffness exactly, so a
+    # brute-force rule with q = p+3 must give the same element matrices.
+    d = fem.Discretization(dim, (2, 3, 1)[:dim], p)
+    els = np.arange(d.n_elem)
+    assert np.allclose(d.element_matrices(els), d.element_matrices(els, q=p + 3), atol=1e-12)
+    assert np.allclose(d.element_matrices(els, mass=True),
+                       d.element_matrices(els, q=p + 3, mass=True), atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,E,p", [(2, 3, 4), (3, 2, 3)])
+def test_operator_symmetric_neumann_kernel_and_spd(dim, E, p):
+    d = fem.Discretization(dim, E, p, warp_amp=0.1, mu_a=1.0, mu_b=1e3, mu_k=2.0)
+    Af = d.assemble()
+    scale = abs(Af).max()
+    assert abs(Af - Af.T).max() <= 1e-14 * scale
+    # pure-Neumann operator annihilates constants
+    assert np.max(np.abs(Af @ np.ones(d.N))) <= 1e-12 * scale
+    A = d.stiffness().toarray()
+    np.linalg.cholesky(A)               # positive definite on the interior
+
+
+def test_patch_test_linear_function_2d_warped():
+    # mu = 1: a linear function of the PHYSICAL coordinates lies in the isoparametric
+    # space, and a(x_k, phi_i) = 0 for interior i (Laplace of a linear function), exactly
+    # in 2D with q = p+1 Gauss points. A transposed Jacobian breaks this.
+    for p in (1, 2, 4):
+        d = fem.Discretization(2, 3, p, warp_amp=0.1)
+        Af = d.assemble()
+        X = d.node_coords()
+        for k in range(2):
+            r = (Af @ X[:, k])[d.interior]
+            assert np.max(np.abs(r)) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mapped_domain_measure(dim):
+    # The warp fixes the boundary, so the mapped domain is still the unit square/cube.
+    d = fem.Discretization(dim, 3, 3, warp_amp=0.1)
+    Phi, dPhi, W = d.basis_tables()
+    _, _, detJ = d.element_geometry(np.arange(d.n_elem))
+    vol = np.sum(W[None, :] * detJ)
+    assert np.all(detJ > 0)
+    assert abs(vol - 1.0) < (1e-13 if dim == 2 else 1e-6)
+
+
+def _mms_error(dim, E, p, warp, mu_b):
+    """L2 error of the Galerkin solution for u = prod sin(pi x_i) with
+    mu = 1 + mu_b sum cos^2(2 pi x_i) (f = -div(mu grad u) written out by hand)."""
+    d = fem.Discretization(dim, E, p, warp_amp=warp, mu_a=1.0, mu_b=mu_b, mu_k=2.0)
+    k = 2.0
+
+    def u_ex(x):
+        return np.prod(np.sin(np.pi * x), axis=1)
+
+    def f_ex(x):
+        mu = 1.0 + mu_b * np.sum(np.cos(k * np.pi * x) ** 2, axis=1)
+        f = dim * np.pi ** 2 * mu * u_ex(x)
+        for i in range(dim):
+            # -dmu/dx_i * du/dx_i, dmu/dx_i = -mu_b k pi sin(2 k pi x_i)
+            du = np.pi * np.cos(np.pi * x[:, i]) * np.prod(
+                np.sin(np.pi * np.delete(x, i, axis=1)), axis=1)
+            f += mu_b * k * np.pi * np.sin(2 * k * np.pi * x[:, i]) * du
+        return f
+
+    X = d.node_coords()
+    b = d.rhs(f_ex(X))
+    u = spla.spsolve(d.stiffness().tocsc(), b)
+    uf = d.to_full(u)
+    tables = d.basis_tables()
+    Phi, _, W = tables
+    els = np.arange(d.n_elem)
+    xq, _, detJ = d.element_geometry(els, tables)
+    uq = np.einsum("qa,ea->eq", Phi, uf[d.element_nodes(els)])
+    err = uq - u_ex(xq.reshape(-1, dim)).reshape(uq.shape)
+    return np.sqrt(np.sum(W[None, :] * detJ * err ** 2))
+
+
+@pytest.mark.parametrize("dim,p,Es", [(2, 1, (16, 32)), (2, 2, (32, 64)), (2, 3, (16, 32)),
+                                      (2, 4, (16, 32)), (3, 1, (8, 16)), (3, 2, (4, 8))])
+def test_mms_convergence_rate_p_plus_1_warped_variable_mu(dim, p, Es):
+    # Asymptotic L2 rate p+1; on the coarser pairs the rate still approaches p+1 from
+    # above (pre-asymptotic), so only the lower side is tight. A wrong geometric factor,
+    # quadrature weight or coefficient evaluation stalls the rate near 0.
+    errs = [_mms_error(dim, E, p, 0.1, 1.0) for E in Es]
+    rate = np.log(errs[-2] / errs[-1]) / np.log(Es[-1] / Es[-2])
+    assert p + 1 - 0.3 < rate < p + 1 + 2.5, (errs, rate)
+    assert errs[-1] < 1e-2
+
+
+def test_apply_rows_equals_assembled_rows():
+    d = fem.Discretization(3, 2, 3, warp_amp=0.1, mu_a=1.0, mu_b=1e3)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-1, 1, d.N)
+    x[d.boundary] = 0
+    rows = d.interior[rng.choice(d.n_interior, 12, replace=False)]
+    ref = (d.assemble() @ x)[rows]
+    assert np.allclose(d.apply_rows(x, rows), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())

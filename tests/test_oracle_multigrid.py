@@ -1,0 +1,150 @@
+"""Pins of the oracle's smoothers, eigenvalue estimate, V-cycle and solvers
+(Sec. 3.2, 4.3, Algorithm 1): closed-form error multipliers against a dense
+eigensolve, V-cycle symmetry, the 7-matvec cost model, and the iteration counts of
+the paper's Tables 1 and 4 (loose pins, +-2)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import synth
+from oracle import fem, multigrid
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def _tiny(smoother="cheb", **kw):
+    prob = synth.problem(2, 4, 2, warp_amp=0.1, mu_a=1.0, mu_b=1e3, smoother=smoother,
+                         n_hlevels=2, **kw)
+    return prob, multigrid.Hierarchy(prob)
+
+
+def _sym_eig(L):
+    A = L.A.toarray()
+    Dh = np.sqrt(L.dinv)
+    S = Dh[:, None] * A * Dh[None, :]          # D^-1/2 A D^-1/2
+    lam, V = np.linalg.eigh(S)
+    return lam, V, Dh
+
+
+def test_jacobi_step_multiplies_eigencomponents_by_1_minus_omega_lambda():
+    prob, H = _tiny("jacobi")
+    L = H.fine
+    lam, V, Dh = _sym_eig(L)
+    b = np.zeros(L.A.shape[0])
+    for i in (0, len(lam) // 2, len(lam) - 1):
+        x0 = Dh * V[:, i]                       # error = D^-1/2 v_i
+        x1 = H.jacobi(0, b, x0, 1)
+        assert np.allclose(x1, (1 - prob["omega"] * lam[i]) * x0, atol=1e-12 * np.abs(x0).max())
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 4])
+def test_chebyshev_error_polynomial(steps):
+    prob, H = _tiny("cheb")
+    L = H.fine
+    lam, V, Dh = _sym_eig(L)
+    L.lam = lam[-1]
+    hi, lo = L.lam, L.lam / 4
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+
+    def T(k, x):
+        return np.cosh(k * np.arccosh(x)) if abs(x) >= 1 else np.cos(k * np.arccos(x))
+
+    b = np.zeros(L.A.shape[0])
+    for i in (0, 3, len(lam) // 2, len(lam) - 1):
+        x0 = Dh * V[:, i]
+        xk = H.chebyshev(0, b, x0, steps)
+        mult = T(steps, (theta - lam[i]) / delta) / T(steps, theta / delta)
+        assert np.allclose(xk, mult * x0, atol=1e-11 * np.abs(x0).max())
+
+
+@pytest.mark.parametrize("case", [dict(dim=2, nelem=4, order=2, warp_amp=0.1, mu_b=1e3),
+                                  dict(dim=2, nelem=8, order=1),
+                                  dict(dim=3, nelem=2, order=3, warp_amp=0.1, mu_b=1e3)])
+def test_arnoldi_estimate_close_to_true_lambda_max(case):
+    prob = synth.problem(**case, n_hlevels=2)
+    H = multigrid.Hierarchy(prob)
+    lam, _, _ = _sym_eig(H.fine)
+    est = H.fine.lam
+    assert 0.9 * lam[-1] <= est <= 1.0 * lam[-1] * (1 + 1e-10)
+
+
+def test_arnoldi_exhausts_tiny_levels():
+    # on a level with n < 10 unknowns, n Arnoldi steps give the exact largest eigenvalue
+    prob = synth.problem(2, 2, 2, warp_amp=0.1, mu_b=10.0, n_hlevels=2)
+    H = multigrid.Hierarchy(prob)
+    lam, _, _ = _sym_eig(H.fine)
+    assert H.fine.disc.n_interior == 9
+    assert abs(H.fine.lam - lam[-1]) < 1e-9 * lam[-1]
+
+
+def test_coarse_exact_solve():
+    prob, H = _tiny()
+    L = H.levels[-1]
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(L.A.shape[0])
+    x = sla.cho_solve(L.chol, b)
+    assert np.linalg.norm(L.A @ x - b) <= 1e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("smoother,hier", [("cheb", "h"), ("jacobi", "p"), ("cheb", "p")])
+def test_vcycle_is_symmetric_operator(smoother, hier):
+    # With equal pre/post smoothing, R = P^T and an exact coarse solve, the V-cycle from a
+    # zero guess is a symmetric linear map r -> z (what PCG needs).
+    prob = synth.problem(2, 4, 4, warp_amp=0.1, mu_b=1e3, smoother=smoother, hier=hier,
+                         nu_pre=2, nu_post=2)
+    H = multigrid.Hierarchy(prob)
+    n = H.fine.A.shape[0]
+    rng = np.random.default_rng(3)
+    r1, r2 = rng.standard_normal(n), rng.standard_normal(n)
+    a, b = H.vcycle(r1) @ r2, r1 @ H.vcycle(r2)
+    assert abs(a - b) <= 1e-11 * abs(a)
+    # and linear
+    z = H.vcycle(2 * r1 - r2)
+    assert np.allclose(z, 2 * H.vcycle(r1) - H.vcycle(r2), atol=1e-11 * np.abs(z).max())
+
+
+def test_pcg_costs_seven_fine_matvecs_per_iteration():
+    # Sec. 4.3: one residual plus 6 smoothing matvecs per V(3,3) cycle -> 7 N g_p.
+    prob = synth.problem(2, 8, 2, nu_pre=3, nu_post=3)
+    H = multigrid.Hierarchy(prob)
+    d = H.fine.disc
+    b = d.rhs(synth.nodal_field(1, d.N))
+    H.fine_applies = 0
+    _, it, _, ok = H.solve_pcg(b)
+    # initial V-cycle from zero (6) + per iteration A p (1) + V-cycle (6), except the last
+    assert ok and H.fine_applies == 6 + it * 1 + (it - 1) * 6
+
+
+def test_fig2_problem_sizes():
+    g = GOLDEN["fig2_interior_dofs"]
+    for E, p in g["cases"]:
+        assert fem.Discretization(2, E, p).n_interior == g["n_unknowns"]
+
+
+def _paper_cases():
+    out = []
+    for tab, orders in (("table1_2d_const", (1, 2, 4)), ("table4_3d_const", (1, 2))):
+        for key in ("MG jacobi h", "MG cheb h", "PCG jacobi h", "PCG cheb h",
+                    "MG jacobi p", "MG cheb p", "PCG jacobi p", "PCG cheb p"):
+            for p in orders:
+                if str(p) in GOLDEN[tab][key]:
+                    out.append((tab, key, p))
+    return out
+
+
+@pytest.mark.parametrize("tab,key,p", _paper_cases())
+def test_iteration_counts_match_paper_tables_loosely(tab, key, p):
+    t = GOLDEN[tab]
+    mode, smoother, hier = key.split()
+    prob = synth.problem(t["dim"], t["nelem"], p, hier=hier, smoother=smoother,
+                         nu_pre=3, nu_post=3)
+    H = multigrid.Hierarchy(prob)
+    d = H.fine.disc
+    b = d.rhs(synth.nodal_field(7, d.N))
+    solve = H.solve_mg if mode == "MG" else H.solve_pcg
+    _, it, hist, ok = solve(b)
+    assert ok
+    assert abs(it - t[key][str(p)]) <= 2, (it, t[key][str(p)])
