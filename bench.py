@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Benchmark of the matrix-free high-order multigrid solver (one JSON line on rank 0).
+
+Workload (one "step"): a full MG-preconditioned CG solve (Algorithm 1) to a 1e-8 relative
+residual of the 3D variable-coefficient problem on a 16^3 hex mesh of the unit cube warped
+by x_i += 0.1 prod_j sin(pi x_j), Q_4 (65^3 = 274,625 DOF incl. boundary nodes),
+mu = 1 + 1e3 sum_i cos^2(2 pi x_i), seeded f ~ U(-1,1) at the nodes, V(3,3) cycles with
+Chebyshev-Jacobi smoothing, FP64 throughout. The hierarchy (geometry, diagonal, Chebyshev
+bounds, coarsest inverse) is built once before timing and reported as setup_ms.
+
+value = DOF solved per second (N / solve time), whole job over all ranks (replicas).
+The operator apply itself is timed separately for the roofline object.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--hier p|h] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GDOF/s of order-p operator apply; solve time to 1e-8; serve p50/p99 latency"
+WORKLOAD = "3D warped var-coef Q4 16^3 (65^3=274,625 DOF), mu=1+1e3*sum cos^2(2 pi x_i), PCG + V(3,3) Chebyshev(3) to 1e-8, FP64"
+# FP64 peak of one GB300: 152 SMs x 2.07 GHz x 4 FP64 flops/clock/SM (2 FMA lanes) = 1.259 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload(hier):
+    import synth
+    return synth.warped_var3d(16, 4, hier=hier)
+
+
+def oracle_sample_problem(hier):
+    import synth
+    return synth.warped_var3d(8, 4, hier=hier)
+
+
+# ------------------------------------------------------------------ oracle arm (CPU)
+def run_reference(args):
+    """Time the FP64 CPU oracle (assembled sparse operators) on a bounded sample of the
+    same workload: 8^3 elements instead of 16^3, same order, coefficient, warp, cycle."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import synth
+    from oracle import multigrid
+    prob = oracle_sample_problem(args.hier)
+    t0 = time.perf_counter()
+    H = multigrid.Hierarchy(prob)
+    d = H.fine.disc
+    b = d.rhs(synth.nodal_field(synth.SEED_WARPED_VAR3D, d.N))
+    setup_s = time.perf_counter() - t0
+    times, its = [], []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        _, it, hist, ok = H.solve_pcg(b)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt)
+            its.append(it)
+    t_step = statistics.mean(times)
+    value = d.N / t_step / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "hier": args.hier},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+                         "sample": f"oracle PCG solve of the same warped var-coef Q4 problem on 8^3 elements "
+                                   f"({d.N} DOF) instead of 16^3; setup {setup_s:.1f}s excluded; "
+                                   f"{its[0]} iterations"},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(hier):
+    """Oracle timed in a child process on the host (single-threaded BLAS), one step."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               RANK="0", WORLD_SIZE="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "2", "--warmup", "1", "--hier", hier],
+                       capture_output=True, text=True, env=env, timeout=600)
+    for ln in r.stdout.splitlines()[::-1]:
+        if ln.startswith("{"):
+            return json.loads(ln)["cpu_baseline"]
+    return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        if not self.out:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1402_5938_gb300 import Problem, launch_count
+
+    prob = workload(args.hier)
+    t0 = time.perf_counter()
+    P = Problem(prob)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    N = P.ndof(0)
+    f_host = torch.from_numpy(synth.nodal_field(synth.SEED_WARPED_VAR3D, N)).pin_memory()
+    f = f_host.to(dev)
+    b = torch.zeros(N, dtype=torch.float64, device=dev)
+    u = torch.zeros_like(b)
+    P.rhs(f, b)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    its = []
+    for _ in range(args.warmup):
+        st, it, hist = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+        its.append(it)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    a0 = P.fine_applies()
+    barrier()
+    l0 = launch_count()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                                   # L2 flush between timed solves
+            ev[k][0].record(stream)
+            st, it, hist = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+            ev[k][1].record(stream)
+            its.append(it)
+        barrier()
+    launches = launch_count() - l0
+    applies = (P.fine_applies() - a0) / args.steps
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    t_step = sum(step_ms) / len(step_ms)
+    t_max = torch.tensor([t_step], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    t_step = float(t_max.item())
+    value = world * N / (t_step * 1e-3) / 1e9
+    rel_res = float(hist[-1] / hist[0])
+
+    # ---- end to end through the public API: pinned host f -> rhs -> solve -> host u
+    u_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    barrier()
+    e2e_ev[0].record(stream)
+    for k in range(args.steps):
+        f.copy_(f_host, non_blocking=True)
+        P.rhs(f, b)
+        P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+        u_host.copy_(u, non_blocking=True)
+    e2e_ev[1].record(stream)
+    barrier()
+    e2e_ms = e2e_ev[0].elapsed_time(e2e_ev[1]) / args.steps
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * N / (float(e2e_t.item()) * 1e-3) / 1e9
+
+    # ---- the dominant kernel: the FP64 order-p apply on the finest level, timed alone
+    x = torch.from_numpy(synth.uniform_pm1(7, N)).to(dev)
+    y = torch.zeros_like(x)
+    for _ in range(3):
+        P.apply(0, x, y)
+    reps = 50
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ea.record(stream)
+    for _ in range(reps):
+        flush.zero_()
+        P.apply(0, x, y)
+    eb.record(stream)
+    barrier()
+    ef, eg = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ef.record(stream)
+    for _ in range(reps):
+        flush.zero_()
+    eg.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = (ea.elapsed_time(eb) - ef.elapsed_time(eg)) / reps
+    (E3, p, _) = P.level_info(0)
+    n = p + 1
+    E = E3[0] * E3[1] * E3[2]
+    flops = E * (24 * n ** 4 + 15 * n ** 3)
+    achieved_tf = flops / (apply_ms * 1e-3) / 1e12
+
+    if rank == 0:
+        cpu = cpu_baseline(args.hier)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "hier": args.hier, "global_batch": world, "dof": N,
+                       "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed solves"},
+            "solve_ms": t_step, "setup_ms": setup_ms, "iterations": its[-1], "final_rel_residual": rel_res,
+            "fine_applies_per_solve": applies, "apply_gdofs": N / (apply_ms * 1e-3) / 1e9,
+            "apply_ms": apply_ms,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": f"k_apply<3,{n},double>",
+                         "note": "FP64 pipe; peak = 152 SM x 2.07 GHz x 4 flop/clk (nominal); "
+                                 "algorithmic flops 24n^4+15n^3 per element"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--hier", choices=["h", "p"], default="p")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * hmg.h -- C ABI of a matrix-free high-order h-/p-multigrid solver for
+ *          -div(mu grad u) = f,  u = 0 on the boundary,
+ * discretized with continuous Q_p elements (1 <= p <= 16) on Gauss-Lobatto-Legendre
+ * nodes of a structured, smoothly mapped quadrilateral (2D) or hexahedral (3D) mesh,
+ * after H. Sundar, G. Stadler, G. Biros, "Comparison of multigrid algorithms for
+ * high-order continuous finite element discretizations" (arXiv:1402.5938).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Every function returns hmg_status (0 = OK, < 0 = error). No C++ exception crosses
+ *   the ABI. hmg_last_error() gives a message for the calling thread's last failure.
+ * - A problem handle owns its multigrid hierarchy in device memory of the device that
+ *   was current at hmg_setup(); later calls must run with that device current.
+ *   Handles are not thread-safe: use one handle per host thread.
+ * - "_dev" pointers are device pointers owned by the caller (for example PyTorch
+ *   tensors): contiguous FP64 vectors of the level's length hmg_ndof(), global nodes
+ *   numbered lexicographically with x fastest, Dirichlet (boundary) nodes included.
+ *   Boundary entries are ignored on input and written as zero on output.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream). Work is queued on it in
+ *   order; functions that return host results (hmg_solve, hmg_lambda_max) synchronize
+ *   that stream before returning.
+ * - Level 0 is the finest level; level nlevels-1 is the coarsest (exact solve).
+ */
+#ifndef HMG_H
+#define HMG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMG_OK = 0,
+  HMG_EINVAL = -1,   /* invalid argument or descriptor */
+  HMG_ENOMEM = -2,   /* device or host allocation failed, or over the memory budget */
+  HMG_ENOCONV = -3,  /* solver reached maxit; solution and history are still written */
+  HMG_EDEVICE = -4,  /* a CUDA call failed */
+  HMG_ETIMEOUT = -5, /* a bounded wait gave up */
+  HMG_EBUSY = -6,    /* result not ready yet (serving) */
+  HMG_ENAN = -7      /* a non-finite value was detected in the input or the iteration */
+} hmg_status;
+
+typedef enum { HMG_HIER_H = 0, HMG_HIER_P = 1 } hmg_hier;
+typedef enum { HMG_SMOOTH_JACOBI = 0, HMG_SMOOTH_CHEB = 1 } hmg_smoother;
+typedef enum { HMG_MODE_MG = 0, HMG_MODE_PCG = 1 } hmg_mode;
+typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1 } hmg_prec;
+
+/*
+ * Problem descriptor (paper Sec. 2 problem statement, Sec. 2.3 meshing, Sec. 4.3 settings).
+ *   dim, nelem, order  : structured nelem[0] x nelem[1] (x nelem[2]) mesh of [0,1]^dim, Q_order.
+ *   warp_amp           : the mesh is mapped by x_i += warp_amp * prod_j sin(pi X_j) applied to
+ *                        the reference coordinates X (0 = unit square/cube). The map fixes the
+ *                        boundary; |warp_amp| * pi < 1 keeps it a diffeomorphism.
+ *   mu_a, mu_b, mu_k   : coefficient mu(x) = mu_a + mu_b * sum_i cos^2(mu_k * pi * x_i), evaluated
+ *                        at each level's Gauss points (q = p+1 per direction); needs mu > 0.
+ *   hier, n_hlevels    : h-multigrid (Sec. 3.1.1): n_hlevels meshes at fixed p, each halving the
+ *                        elements per axis. p-multigrid (Sec. 3.1.2): p, p/2, ..., 1 on the fine
+ *                        mesh, then n_hlevels-1 mesh halvings at p = 1.
+ *   smoother, nu_pre, nu_post, omega : point-Jacobi x += omega D^-1 (b - A x) or Chebyshev-
+ *                        accelerated Jacobi of degree nu (Sec. 3.2.1); omega only for Jacobi.
+ *   arnoldi_iters, cheb_lo_frac, cheb_safety : Chebyshev interval [lo_frac*s*lam, s*lam] with
+ *                        lam the largest Ritz value of D^-1 A after arnoldi_iters Arnoldi steps
+ *                        (Sec. 3.2.2: [lam/4, lam], 10 iterations).
+ *   arnoldi_seed       : base seed of the SplitMix64 start vectors (level k uses seed + k);
+ *                        0 selects 0x1402593800000000.
+ *   smooth_prec        : HMG_PREC_FP64, or HMG_PREC_FP32 for the V-cycle's smoother, residual and
+ *                        transfer work below the FP64 fine residual / PCG / coarsest solve.
+ */
+typedef struct hmg_desc {
+  int dim;
+  int nelem[3];
+  int order;
+  double warp_amp;
+  double mu_a, mu_b, mu_k;
+  int hier;
+  int n_hlevels;
+  int smoother;
+  int nu_pre, nu_post;
+  double omega;
+  int arnoldi_iters;
+  double cheb_lo_frac;
+  double cheb_safety;
+  unsigned long long arnoldi_seed;
+  int smooth_prec;
+} hmg_desc;
+
+typedef struct hmg_problem hmg_problem;
+
+/* Fill *d with the paper's defaults: 3D, 8^3 Q_4, unit cube, mu = 1, h-MG with 3 meshes,
+ * Chebyshev(3,3), omega 2/3, 10 Arnoldi iterations, interval [lam/4, lam], FP64. */
+hmg_status hmg_desc_default(hmg_desc* d);
+
+/* Build the hierarchy on the current device: per level the geometric factors
+ * G = mu w det(J) J^-1 J^-T at every Gauss point (Sec. 2.3), D^-1 (Sec. 3.2.1), the Chebyshev
+ * bound (Sec. 3.2.2), the 1D transfer stencils (Sec. 2.2), and the inverse of the coarsest
+ * operator. Work runs on `stream`; the call synchronizes it. Owns all memory it allocates.
+ * Errors: HMG_EINVAL (bad descriptor), HMG_ENOMEM, HMG_EDEVICE. */
+hmg_status hmg_setup(const hmg_desc* desc, void* stream, hmg_problem** out);
+hmg_status hmg_destroy(hmg_problem* prob);
+
+/* Hierarchy introspection. level_info writes nelem[3], order and the node count. */
+int hmg_nlevels(const hmg_problem* prob);
+size_t hmg_ndof(const hmg_problem* prob, int level);
+hmg_status hmg_level_info(const hmg_problem* prob, int level, int* nelem3, int* order, size_t* ndof);
+size_t hmg_device_bytes(const hmg_problem* prob);
+
+/* Physical node coordinates of a level, written as xyz_dev[c * N + node], c < dim. */
+hmg_status hmg_node_coords(hmg_problem* prob, int level, double* xyz_dev, void* stream);
+
+/* Load vector b_j = (f_h, phi_j) for the nodal interpolant f_h of f (all N nodal values used),
+ * by the same Gauss rule (Sec. 2.1 f_k); boundary entries of b are zero. */
+hmg_status hmg_rhs(hmg_problem* prob, const double* f_nodal_dev, double* b_dev, void* stream);
+
+/* y = A_k x on level k: the matrix-free sum-factorized stiffness apply (Sec. 2.3 matrix-free
+ * discussion; (A_k)_ij = a(phi_i, phi_j), Sec. 2.1), Dirichlet nodes masked. */
+hmg_status hmg_apply(hmg_problem* prob, int level, const double* x_dev, double* y_dev, void* stream);
+
+/* D^-1 of level k (inverse diagonal of A_k; 0 on boundary nodes), Sec. 3.2.1. */
+hmg_status hmg_diag_inv(hmg_problem* prob, int level, double* dinv_dev, void* stream);
+
+/* Chebyshev bound of level k (largest Ritz value of D^-1 A_k after the Arnoldi steps), Sec. 3.2.2. */
+hmg_status hmg_lambda_max(const hmg_problem* prob, int level, double* lam);
+
+/* Inter-grid transfer between level k (fine) and k+1 (coarse), Sec. 2.2 Eq. (Pstencil):
+ * x_f = P x_c (overwrites x_f) and r_c = P^T r_f. */
+hmg_status hmg_prolong(hmg_problem* prob, int level, const double* xc_dev, double* xf_dev, void* stream);
+hmg_status hmg_restrict(hmg_problem* prob, int level, const double* rf_dev, double* rc_dev, void* stream);
+
+/* `steps` smoothing steps on level k for A_k x = b (Jacobi or Chebyshev per the descriptor);
+ * zero_guess != 0 treats x as zero on input. */
+hmg_status hmg_smooth(hmg_problem* prob, int level, const double* b_dev, double* x_dev, int steps,
+                      int zero_guess, void* stream);
+
+/* z = V-cycle(r) from a zero initial guess on the finest level (Sec. 3.2.2, 4.3). */
+hmg_status hmg_vcycle(hmg_problem* prob, const double* r_dev, double* z_dev, void* stream);
+
+/* Solve A u = b on the finest level to ||r||_2 <= rtol ||b||_2 (Sec. 4.3), from u = 0:
+ * HMG_MODE_MG repeats V-cycles; HMG_MODE_PCG is Algorithm 1 (one V-cycle per iteration).
+ * iters: V-cycles (MG) or CG iterations (PCG). res_hist: host array of >= maxit+1 doubles,
+ * res_hist[i] = ||r_i||_2 (may be NULL). Returns HMG_ENOCONV (u and history written) if
+ * maxit is reached, HMG_ENAN on a non-finite residual. Synchronizes `stream`. */
+hmg_status hmg_solve(hmg_problem* prob, int mode, const double* b_dev, double* u_dev, double rtol,
+                     int maxit, int* iters, double* res_hist, void* stream);
+
+/* Number of finest-level operator applies issued since setup (cost-model accounting,
+ * Sec. 4.2/4.3: 7 per V(3,3) cycle). */
+long long hmg_fine_applies(const hmg_problem* prob);
+
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+long long hmg_launch_count(void);
+
+const char* hmg_status_string(hmg_status s);
+const char* hmg_last_error(void);
+
+/* ---- host-only helpers (no device needed): the library's own 1D tables and eigen step ---- */
+
+/* GLL nodes r[p+1], Gauss points g[p+1] and weights w[p+1] on [0,1] (Sec. 2.3, Fig. 1). */
+hmg_status hmg_host_basis(int order, double* gll, double* gauss_x, double* gauss_w);
+
+/* Largest real part of the eigenvalues of an m x m upper Hessenberg matrix (row-major),
+ * by the Francis double-shift QR algorithm: the Ritz-value step of the Chebyshev bound. */
+hmg_status hmg_host_hessenberg_max_real_eig(const double* H, int m, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMG_H */

@@ -1,0 +1,412 @@
+// Element kernels of the sum-factorized, matrix-free Q_p operator (templated on the
+// dimension DIM, the 1D node count N = p+1 and the precision T).
+//
+// Every kernel stages `epb` consecutive elements per thread block in shared memory as
+// tensor tiles t[k][j][i] (x fastest) and applies the 1D (N x N) tables along one
+// direction at a time ("sum factorization": O(N^{d+1}) per element instead of O(N^{2d}),
+// paper Sec. 2.3). A contraction phase gives each thread one whole 1D line: it reads the
+// N line values into registers and applies the table with compile-time indices, so
+// every table entry is a uniform (broadcast) operand read from the kernel's parameter
+// space.
+#pragma once
+
+#include "common.cuh"
+
+namespace hmg {
+
+template <int DIM, int N>
+struct Sh {
+  static constexpr int NP = DIM == 3 ? N * N * N : N * N;  // points per element
+  static constexpr int NL = DIM == 3 ? N * N : N;          // lines per direction
+  static constexpr int NC = DIM == 3 ? 6 : 3;              // symmetric G components
+};
+
+// First element offset and node strides of line l along direction dir in a tile.
+template <int DIM, int N>
+__device__ __forceinline__ void line_of(int dir, int l, int& base, int& stride) {
+  if (DIM == 2) {
+    if (dir == 0) { base = l * N; stride = 1; }
+    else { base = l; stride = N; }
+  } else {
+    const int a = l % N, b = l / N;
+    if (dir == 0) { base = (b * N + a) * N; stride = 1; }
+    else if (dir == 1) { base = b * N * N + a; stride = N; }
+    else { base = b * N + a; stride = N * N; }
+  }
+}
+
+// Global node number of local node `a` of element e; bd = node lies on the boundary.
+template <int DIM, int N>
+__device__ __forceinline__ long long elem_node(const Mesh& m, long long e, int a, bool& bd) {
+  const int i = a % N;
+  const int j = (a / N) % N;
+  const long long ex = e % m.E[0];
+  const long long r1 = e / m.E[0];
+  const long long I = ex * m.p + i;
+  long long J, K = 0;
+  if (DIM == 3) {
+    const int k = a / (N * N);
+    const long long ey = r1 % m.E[1];
+    const long long ez = r1 / m.E[1];
+    J = ey * m.p + j;
+    K = ez * m.p + k;
+    bd = (I == 0) | (I == m.Nn[0] - 1) | (J == 0) | (J == m.Nn[1] - 1) | (K == 0) | (K == m.Nn[2] - 1);
+    return (K * m.Nn[1] + J) * m.Nn[0] + I;
+  } else {
+    J = r1 * m.p + j;
+    bd = (I == 0) | (I == m.Nn[0] - 1) | (J == 0) | (J == m.Nn[1] - 1);
+    return J * m.Nn[0] + I;
+  }
+}
+
+// Interior numbering (boundary nodes removed, x fastest) of an interior global node g.
+template <int DIM>
+__device__ __forceinline__ long long interior_index(const Mesh& m, long long g) {
+  const long long I = g % m.Nn[0];
+  const long long r = g / m.Nn[0];
+  if (DIM == 3) {
+    const long long J = r % m.Nn[1], K = r / m.Nn[1];
+    return ((K - 1) * (m.Nn[1] - 2) + (J - 1)) * (m.Nn[0] - 2) + (I - 1);
+  }
+  return (r - 1) * (m.Nn[0] - 2) + (I - 1);
+}
+
+// dst (=, or += if ACC) table contraction of src along `dir` for the `ne` tiles of the block.
+//   TRN = false: out[i] = sum_m M[i*N+m] in[m]   (nodes -> Gauss points)
+//   TRN = true : out[i] = sum_m M[m*N+i] in[m]   (transpose, Gauss points -> nodes)
+// src may equal dst: each thread reads its whole line before writing it.
+template <int DIM, int N, typename T, bool TRN, bool ACC>
+__device__ __forceinline__ void contract(const T* src, T* dst, const T* M, int dir, int ne) {
+  constexpr int NP = Sh<DIM, N>::NP, NL = Sh<DIM, N>::NL;
+  const int total = ne * NL;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int e = t / NL, l = t - e * NL;
+    int base, stride;
+    line_of<DIM, N>(dir, l, base, stride);
+    base += e * NP;
+    T in[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) in[m] = src[base + m * stride];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      T s = (TRN ? M[i] : M[i * N]) * in[0];
+#pragma unroll
+      for (int m = 1; m < N; ++m) s = fma(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
+      if (ACC) dst[base + i * stride] += s;
+      else dst[base + i * stride] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// y += alpha * A x on one level: gather, interpolate to Gauss points (B), collocated
+// reference gradient (D), pointwise G (mu w detJ J^-1 J^-T), transpose, scatter-add.
+// Boundary nodes read as 0 and are never written. G layout [E][NC][NP].
+// Shared memory: (1 + DIM) * epb * NP values of T.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N, typename T>
+__global__ void __launch_bounds__(256)
+k_apply(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ G, const Mesh m,
+        const __grid_constant__ Tab<N, T> tab, const T alpha, const int epb) {
+  constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* U = reinterpret_cast<T*>(smem_raw);
+  T* V = U + epb * NP;
+  const long long e0 = (long long)blockIdx.x * epb;
+  const int ne = (int)min((long long)epb, m.nelem - e0);
+
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    bool bd;
+    const long long g = elem_node<DIM, N>(m, e0 + e, a, bd);
+    U[t] = bd ? T(0) : x[g];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    contract<DIM, N, T, false, false>(U, U, tab.B, d, ne);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) contract<DIM, N, T, false, false>(U, V + d * epb * NP, tab.D, d, ne);
+  __syncthreads();
+
+  const T* Gb = G + e0 * NC * NP;
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, q = t - e * NP;
+    const T* g = Gb + (long long)e * NC * NP + q;
+    if (DIM == 3) {
+      const T u0 = V[t], u1 = V[epb * NP + t], u2 = V[2 * epb * NP + t];
+      const T g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
+      V[t] = g00 * u0 + g01 * u1 + g02 * u2;
+      V[epb * NP + t] = g01 * u0 + g11 * u1 + g12 * u2;
+      V[2 * epb * NP + t] = g02 * u0 + g12 * u1 + g22 * u2;
+    } else {
+      const T u0 = V[t], u1 = V[epb * NP + t];
+      const T g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
+      V[t] = g00 * u0 + g01 * u1;
+      V[epb * NP + t] = g01 * u0 + g11 * u1;
+    }
+  }
+  __syncthreads();
+  contract<DIM, N, T, true, false>(V, U, tab.D, 0, ne);
+  __syncthreads();
+  contract<DIM, N, T, true, true>(V + epb * NP, U, tab.D, 1, ne);
+  __syncthreads();
+  if (DIM == 3) {
+    contract<DIM, N, T, true, true>(V + 2 * epb * NP, U, tab.D, 2, ne);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    contract<DIM, N, T, true, false>(U, U, tab.B, d, ne);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    bool bd;
+    const long long g = elem_node<DIM, N>(m, e0 + e, a, bd);
+    if (!bd) atomicAdd(y + g, alpha * U[t]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Geometry, stage 1: node coordinates x = X + amp prod sin(pi X) of every element node,
+// interpolated to the Gauss points (x_q) and differentiated (dx_c/dxi_d), written to
+// J[e][c*(DIM+1) + s][NP] with s = 0 for x_q and s = 1+d for dx_c/dxi_d.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256)
+k_geom_stage(double* __restrict__ J, const Mesh m, const double warp_amp,
+             const __grid_constant__ GeoTab<N> tab, const int epb) {
+  constexpr int NP = Sh<DIM, N>::NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* U = reinterpret_cast<double*>(smem_raw);
+  double* V = U + epb * NP;
+  const long long e0 = (long long)blockIdx.x * epb;
+  const int ne = (int)min((long long)epb, m.nelem - e0);
+  for (int c = 0; c < DIM; ++c) {
+    for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+      const int e = t / NP, a = t - e * NP;
+      const long long eg = e0 + e;
+      const int idx[3] = {a % N, (a / N) % N, a / (N * N)};
+      const long long ee[3] = {eg % m.E[0], (eg / m.E[0]) % m.E[1], eg / ((long long)m.E[0] * m.E[1])};
+      double X[3], s = 1.0;
+      for (int d = 0; d < DIM; ++d) {
+        X[d] = ((double)ee[d] + tab.r[idx[d]]) / (double)m.E[d];
+        s *= sinpi(X[d]);
+      }
+      U[t] = X[c] + warp_amp * s;
+    }
+    __syncthreads();
+    for (int d = 0; d < DIM; ++d) {
+      contract<DIM, N, double, false, false>(U, U, tab.B, d, ne);
+      __syncthreads();
+    }
+    for (int d = 0; d < DIM; ++d) contract<DIM, N, double, false, false>(U, V + d * epb * NP, tab.D, d, ne);
+    __syncthreads();
+    for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+      const int e = t / NP, q = t - e * NP;
+      double* o = J + ((e0 + e) * (DIM * (DIM + 1)) + c * (DIM + 1)) * NP + q;
+      o[0] = U[t];
+      for (int d = 0; d < DIM; ++d) o[(1 + d) * NP] = V[d * epb * NP + t];
+    }
+    __syncthreads();
+  }
+}
+
+// Geometry, stage 2: G = mu(x_q) w_q det(J) J^-1 J^-T (symmetric, NC entries) and
+// w_q det(J), one thread per Gauss point. Returns the minimum det J through *min_det
+// (as ordered int bits of a positive double; 0 if non-positive).
+template <int DIM, int N>
+__global__ void k_geom_point(const double* __restrict__ J, double* __restrict__ G,
+                             double* __restrict__ wdetJ, const Mesh m, const double mu_a,
+                             const double mu_b, const double mu_k,
+                             const __grid_constant__ GeoTab<N> tab, int* __restrict__ bad) {
+  constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+  const long long tot = m.nelem * NP;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / NP;
+    const int q = (int)(t - e * NP);
+    const double* src = J + e * (DIM * (DIM + 1)) * NP + q;
+    double xq[3], A[3][3];
+    for (int c = 0; c < DIM; ++c) {
+      xq[c] = src[(c * (DIM + 1)) * NP];
+      for (int d = 0; d < DIM; ++d) A[c][d] = src[(c * (DIM + 1) + 1 + d) * NP];
+    }
+    double mu = 0.0;
+    for (int c = 0; c < DIM; ++c) {
+      const double cs = cospi(mu_k * xq[c]);
+      mu += cs * cs;
+    }
+    mu = mu_a + mu_b * mu;
+    double w = tab.w[q % N] * tab.w[(q / N) % N];
+    if (DIM == 3) w *= tab.w[q / (N * N)];
+    double* g = G + e * NC * NP + q;
+    if (DIM == 3) {
+      // adjugate: Jinv = adj / det, adj[i][c] = cofactor of A[c][i]
+      double adj[3][3];
+      adj[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+      adj[0][1] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+      adj[0][2] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+      adj[1][0] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+      adj[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+      adj[1][2] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+      adj[2][0] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+      adj[2][1] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+      adj[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+      const double det = A[0][0] * adj[0][0] + A[0][1] * adj[1][0] + A[0][2] * adj[2][0];
+      if (!(det > 0.0)) atomicExch(bad, 1);
+      const double s = mu * w / det;
+      const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+      for (int c = 0; c < 6; ++c) {
+        const int i = ii[c], j = jj[c];
+        g[c * NP] = s * (adj[i][0] * adj[j][0] + adj[i][1] * adj[j][1] + adj[i][2] * adj[j][2]);
+      }
+      wdetJ[e * NP + q] = w * det;
+    } else {
+      const double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+      if (!(det > 0.0)) atomicExch(bad, 1);
+      // adj = [[A11, -A01], [-A10, A00]]
+      const double a00 = A[1][1], a01 = -A[0][1], a10 = -A[1][0], a11 = A[0][0];
+      const double s = mu * w / det;
+      g[0] = s * (a00 * a00 + a01 * a01);
+      g[NP] = s * (a00 * a10 + a01 * a11);
+      g[2 * NP] = s * (a10 * a10 + a11 * a11);
+      wdetJ[e * NP + q] = w * det;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// diag(A): diag_a = sum_q sum_ij G_ij (dphi_a/dxi_i)(dphi_a/dxi_j), sum-factorized per
+// symmetric pair (i,j) with the 1D product tables BB, BD, DD; scatter-added (boundary skipped).
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256)
+k_diag(const double* __restrict__ G, double* __restrict__ diag, const Mesh m,
+       const __grid_constant__ GeoTab<N> tab, const int epb) {
+  constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* U = reinterpret_cast<double*>(smem_raw);
+  double* Dt = U + epb * NP;
+  const long long e0 = (long long)blockIdx.x * epb;
+  const int ne = (int)min((long long)epb, m.nelem - e0);
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) Dt[t] = 0.0;
+  const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
+  const int qi_[3] = {0, 0, 1}, qj_[3] = {0, 1, 1};
+  for (int c = 0; c < NC; ++c) {
+    const int i = DIM == 3 ? pi_[c] : qi_[c];
+    const int j = DIM == 3 ? pj_[c] : qj_[c];
+    const double f = (i == j) ? 1.0 : 2.0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+      const int e = t / NP, q = t - e * NP;
+      U[t] = f * G[((e0 + e) * NC + c) * NP + q];
+    }
+    __syncthreads();
+    for (int d = 0; d < DIM; ++d) {
+      const int k = (d == i) + (d == j);
+      if (k == 0) contract<DIM, N, double, true, false>(U, U, tab.BB, d, ne);
+      else if (k == 1) contract<DIM, N, double, true, false>(U, U, tab.BD, d, ne);
+      else contract<DIM, N, double, true, false>(U, U, tab.DD, d, ne);
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) Dt[t] += U[t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    bool bd;
+    const long long g = elem_node<DIM, N>(m, e0 + e, a, bd);
+    if (!bd) atomicAdd(diag + g, Dt[t]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// b += M f (load vector of the nodal interpolant, Sec. 2.1 f_k): B to Gauss points, times
+// w det J, B^T back, scatter-add to interior nodes. f is read at all nodes.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256)
+k_mass(const double* __restrict__ f, double* __restrict__ b, const double* __restrict__ wdetJ,
+       const Mesh m, const __grid_constant__ GeoTab<N> tab, const int epb) {
+  constexpr int NP = Sh<DIM, N>::NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* U = reinterpret_cast<double*>(smem_raw);
+  const long long e0 = (long long)blockIdx.x * epb;
+  const int ne = (int)min((long long)epb, m.nelem - e0);
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    bool bd;
+    U[t] = f[elem_node<DIM, N>(m, e0 + e, a, bd)];
+  }
+  __syncthreads();
+  for (int d = 0; d < DIM; ++d) {
+    contract<DIM, N, double, false, false>(U, U, tab.B, d, ne);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) U[t] *= wdetJ[e0 * NP + t];
+  __syncthreads();
+  for (int d = 0; d < DIM; ++d) {
+    contract<DIM, N, double, true, false>(U, U, tab.B, d, ne);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    bool bd;
+    const long long g = elem_node<DIM, N>(m, e0 + e, a, bd);
+    if (!bd) atomicAdd(b + g, U[t]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Dense interior operator of a (small, coarsest) level: one block per element, one thread
+// per entry (a,b): K_ab = sum_q sum_ij G_ij(q) dphi_a/dxi_i(q) dphi_b/dxi_j(q), added into
+// A[ia*nI + ib] for interior nodes (interior numbering, x fastest).
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
+                             const __grid_constant__ GeoTab<N> tab, const long long nI) {
+  constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+  const long long e = blockIdx.x;
+  const double* Ge = G + e * NC * NP;
+  for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) {
+    const int a = t / NP, b = t - a * NP;
+    bool bda, bdb;
+    const long long ga = elem_node<DIM, N>(m, e, a, bda);
+    const long long gb = elem_node<DIM, N>(m, e, b, bdb);
+    if (bda || bdb) continue;
+    const int ai[3] = {a % N, (a / N) % N, a / (N * N)};
+    const int bi[3] = {b % N, (b / N) % N, b / (N * N)};
+    double s = 0.0;
+    for (int q = 0; q < NP; ++q) {
+      const int qi[3] = {q % N, (q / N) % N, q / (N * N)};
+      double da[3], db[3];  // reference gradients of phi_a, phi_b at Gauss point q
+      for (int i = 0; i < DIM; ++i) {
+        double pa = 1.0, pb = 1.0;
+        for (int d = 0; d < DIM; ++d) {
+          const double* T1 = (d == i) ? tab.Bd : tab.B;
+          pa *= T1[qi[d] * N + ai[d]];
+          pb *= T1[qi[d] * N + bi[d]];
+        }
+        da[i] = pa;
+        db[i] = pb;
+      }
+      const double* g = Ge + q;
+      if (DIM == 3) {
+        const double g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
+        s += da[0] * (g00 * db[0] + g01 * db[1] + g02 * db[2]) +
+             da[1] * (g01 * db[0] + g11 * db[1] + g12 * db[2]) +
+             da[2] * (g02 * db[0] + g12 * db[1] + g22 * db[2]);
+      } else {
+        const double g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
+        s += da[0] * (g00 * db[0] + g01 * db[1]) + da[1] * (g01 * db[0] + g11 * db[1]);
+      }
+    }
+    atomicAdd(A + interior_index<DIM>(m, ga) * nI + interior_index<DIM>(m, gb), s);
+  }
+}
+
+}  // namespace hmg

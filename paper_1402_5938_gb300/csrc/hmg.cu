@@ -1,0 +1,822 @@
+// C ABI of libhmg: hierarchy setup and the multigrid / PCG drivers. Every step of the
+// numerical path runs in this library's CUDA kernels; the host only sequences launches
+// on the caller's stream and reads back one residual norm per iteration.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ops.cuh"
+#include "vector.cuh"
+
+namespace hmg {
+
+namespace {
+thread_local std::string g_err;
+}
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+long long add_launches(long long n) { return g_launches.fetch_add(n) + n; }
+
+struct Level {
+  Mesh m{};
+  Basis1D basis{};
+  long long nI = 0;       // interior nodes
+  double* G = nullptr;    // [E][NC][NP] geometric factors mu w detJ J^-1 J^-T
+  double* wdetJ = nullptr;
+  double* dinv = nullptr;
+  float* G32 = nullptr;
+  float* dinv32 = nullptr;
+  double lam = 0.0;       // Chebyshev bound
+  double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d32 = nullptr;
+  Axis1D P[3]{}, PT[3]{};  // transfer to the next coarser level: P rows fine, PT rows coarse
+  double* Ainv = nullptr;  // coarsest: dense inverse of the interior operator
+  long long* gmap = nullptr;
+};
+
+struct ProblemImpl {
+  hmg_desc desc{};
+  int device = 0;
+  std::vector<Level> L;
+  double* S = nullptr;        // device scalars
+  double* partial = nullptr;  // reduction partials
+  double* hostS = nullptr;    // pinned host copy of a scalar
+  void* t1 = nullptr;         // transfer intermediates
+  void* t2 = nullptr;
+  double *pr = nullptr, *pz = nullptr, *pp = nullptr, *ph = nullptr;
+  std::vector<void*> dev_allocs;
+  size_t bytes = 0;
+  long long fine_applies = 0;
+
+  cudaError_t alloc(void** p, size_t nbytes) {
+    *p = nullptr;
+    if (nbytes == 0) nbytes = 16;
+    cudaError_t e = cudaMalloc(p, nbytes);
+    if (e != cudaSuccess) return e;
+    dev_allocs.push_back(*p);
+    bytes += nbytes;
+    return cudaMemset(*p, 0, nbytes);
+  }
+  ~ProblemImpl() {
+    for (void* p : dev_allocs) cudaFree(p);
+    if (hostS) cudaFreeHost(hostS);
+  }
+};
+
+}  // namespace hmg
+
+struct hmg_problem {
+  hmg::ProblemImpl impl;
+};
+
+using namespace hmg;
+
+#define TRY(expr)                                                            \
+  do {                                                                       \
+    cudaError_t _e = (expr);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+      return _e == cudaErrorMemoryAllocation ? HMG_ENOMEM : HMG_EDEVICE;     \
+    }                                                                        \
+  } while (0)
+
+#define CHECK(expr)                        \
+  do {                                     \
+    hmg_status _s = (expr);                \
+    if (_s != HMG_OK) return _s;           \
+  } while (0)
+
+namespace {
+
+Mesh make_mesh(int dim, const int E[3], int p) {
+  Mesh m{};
+  m.dim = dim;
+  m.p = p;
+  m.nelem = 1;
+  m.N = 1;
+  for (int a = 0; a < 3; ++a) {
+    m.E[a] = a < dim ? E[a] : 1;
+    m.Nn[a] = a < dim ? (long long)E[a] * p + 1 : 1;
+    m.nelem *= m.E[a];
+    m.N *= m.Nn[a];
+  }
+  return m;
+}
+
+long long interior_count(const Mesh& m) {
+  long long n = 1;
+  for (int a = 0; a < m.dim; ++a) n *= std::max(0LL, m.Nn[a] - 2);
+  return n;
+}
+
+int nc_of(int dim) { return dim == 3 ? 6 : 3; }
+long long np_of(const Mesh& m) { return m.dim == 3 ? (long long)(m.p + 1) * (m.p + 1) * (m.p + 1) : (long long)(m.p + 1) * (m.p + 1); }
+
+// (nelem, p) of every level, finest first.
+hmg_status level_shapes(const hmg_desc& d, std::vector<std::pair<std::vector<int>, int>>& out) {
+  std::vector<int> E(d.nelem, d.nelem + 3);
+  int p = d.order;
+  out.clear();
+  out.push_back({E, p});
+  if (d.hier == HMG_HIER_P) {
+    while (p > 1) {
+      p = std::max(1, p / 2);
+      out.push_back({E, p});
+    }
+  } else if (d.hier != HMG_HIER_H) {
+    set_error("hier must be HMG_HIER_H or HMG_HIER_P");
+    return HMG_EINVAL;
+  }
+  for (int k = 1; k < d.n_hlevels; ++k) {
+    for (int a = 0; a < d.dim; ++a) {
+      if (E[a] % 2) {
+        set_error("mesh cannot be halved n_hlevels-1 times (odd element count)");
+        return HMG_EINVAL;
+      }
+      E[a] /= 2;
+    }
+    out.push_back({E, p});
+  }
+  return HMG_OK;
+}
+
+hmg_status validate(const hmg_desc* d) {
+  if (!d) { set_error("null descriptor"); return HMG_EINVAL; }
+  if (d->dim != 2 && d->dim != 3) { set_error("dim must be 2 or 3"); return HMG_EINVAL; }
+  if (d->order < 1 || d->order > 16) { set_error("order must be in 1..16"); return HMG_EINVAL; }
+  for (int a = 0; a < d->dim; ++a)
+    if (d->nelem[a] < 1 || d->nelem[a] > (1 << 20)) { set_error("nelem out of range"); return HMG_EINVAL; }
+  if (d->n_hlevels < 1 || d->n_hlevels > 30) { set_error("n_hlevels must be >= 1"); return HMG_EINVAL; }
+  if (d->smoother != HMG_SMOOTH_JACOBI && d->smoother != HMG_SMOOTH_CHEB) { set_error("bad smoother"); return HMG_EINVAL; }
+  if (d->nu_pre < 0 || d->nu_post < 0 || d->nu_pre > 64 || d->nu_post > 64) { set_error("bad nu"); return HMG_EINVAL; }
+  if (!(fabs(d->warp_amp) * M_PI < 1.0)) { set_error("|warp_amp| * pi must be < 1"); return HMG_EINVAL; }
+  if (!(d->mu_a > 0.0) || !(d->mu_a + (d->mu_b < 0 ? d->mu_b * d->dim : 0.0) > 0.0)) {
+    set_error("mu must stay positive"); return HMG_EINVAL;
+  }
+  if (d->smoother == HMG_SMOOTH_CHEB && (d->arnoldi_iters < 1 || !(d->cheb_lo_frac > 0.0 && d->cheb_lo_frac < 1.0) ||
+                                         !(d->cheb_safety > 0.0))) {
+    set_error("bad Chebyshev parameters"); return HMG_EINVAL;
+  }
+  if (d->smooth_prec != HMG_PREC_FP64 && d->smooth_prec != HMG_PREC_FP32) { set_error("bad smooth_prec"); return HMG_EINVAL; }
+  return HMG_OK;
+}
+
+// ---- 1D transfer stencils (Sec. 2.2: P_ij = coarse basis j at fine node i, per axis) ----
+hmg_status build_axis(ProblemImpl& P, const Level& f, const Level& c, int a, Axis1D* Pax, Axis1D* PTax) {
+  const int ratio = f.m.E[a] / c.m.E[a];
+  if (ratio != 1 && ratio != 2) { set_error("levels not nested"); return HMG_EINVAL; }
+  const int nf = (int)f.m.Nn[a], ncn = (int)c.m.Nn[a];
+  const int pf = f.m.p, pc = c.m.p;
+  std::vector<std::vector<std::pair<int, double>>> rows(nf), cols(ncn);
+  double vals[kMaxN];
+  for (int I = 0; I < nf; ++I) {
+    const int ef = std::min(I / pf, f.m.E[a] - 1);
+    const int i = I - ef * pf;
+    const int ec = ef / ratio;
+    const double xi = ((ef % ratio) + f.basis.r[i]) / ratio;
+    lagrange_row(c.basis.r, pc + 1, xi, vals);
+    for (int k = 0; k <= pc; ++k) {
+      if (vals[k] == 0.0) continue;
+      const int J = ec * pc + k;
+      rows[I].push_back({J, vals[k]});
+      cols[J].push_back({I, vals[k]});
+    }
+  }
+  auto upload = [&](const std::vector<std::vector<std::pair<int, double>>>& R, int n_in, Axis1D* out) -> hmg_status {
+    std::vector<int> rp(1, 0), ci;
+    std::vector<double> v;
+    std::vector<float> v32;
+    for (auto& row : R) {
+      for (auto& e : row) { ci.push_back(e.first); v.push_back(e.second); v32.push_back((float)e.second); }
+      rp.push_back((int)ci.size());
+    }
+    out->n_out = (int)R.size();
+    out->n_in = n_in;
+    TRY(P.alloc((void**)&out->rowptr, rp.size() * sizeof(int)));
+    TRY(P.alloc((void**)&out->col, ci.size() * sizeof(int)));
+    TRY(P.alloc((void**)&out->val, v.size() * sizeof(double)));
+    TRY(P.alloc((void**)&out->val32, v32.size() * sizeof(float)));
+    TRY(cudaMemcpy(out->rowptr, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(out->col, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(out->val, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(out->val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return HMG_OK;
+  };
+  CHECK(upload(rows, ncn, Pax));
+  CHECK(upload(cols, nf, PTax));
+  return HMG_OK;
+}
+
+// ---- precision-generic accessors ----
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  static double* b(Level& l) { return l.b; }
+  static double* x(Level& l) { return l.x; }
+  static double* r(Level& l) { return l.r; }
+  static double* d(Level& l) { return l.d; }
+  static const double* dinv(Level& l) { return l.dinv; }
+  static void* scratch(void* p) { return p; }
+};
+template <> struct Acc<float> {
+  static float* b(Level& l) { return l.b32; }
+  static float* x(Level& l) { return l.x32; }
+  static float* r(Level& l) { return l.r32; }
+  static float* d(Level& l) { return l.d32; }
+  static const float* dinv(Level& l) { return l.dinv32; }
+};
+
+hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double alpha, cudaStream_t s) {
+  Level& l = P.L[k];
+  if (k == 0) P.fine_applies++;
+  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, s));
+  return HMG_OK;
+}
+hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
+  Level& l = P.L[k];
+  if (k == 0) P.fine_applies++;
+  TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, s));
+  return HMG_OK;
+}
+
+// x_f (=, or += if acc) P x_c between level k (fine) and k+1 (coarse).
+template <typename T>
+hmg_status prolong(ProblemImpl& P, int k, const T* xc, T* xf, bool acc, cudaStream_t s) {
+  Level& f = P.L[k];
+  Level& c = P.L[k + 1];
+  const int dim = f.m.dim;
+  long long od[3] = {c.m.Nn[0], c.m.Nn[1], c.m.Nn[2]};
+  const T* in = xc;
+  T* bufs[2] = {(T*)P.t1, (T*)P.t2};
+  for (int a = 0; a < dim; ++a) {
+    od[a] = f.m.Nn[a];
+    const bool last = (a == dim - 1);
+    T* out = last ? xf : bufs[a & 1];
+    TRY(axis_pass<T>(in, out, od, a, f.P[a], a == 0, last, last && acc, s));
+    in = out;
+  }
+  return HMG_OK;
+}
+
+// r_c = P^T r_f between level k (fine) and k+1 (coarse).
+template <typename T>
+hmg_status restrict_(ProblemImpl& P, int k, const T* rf, T* rc, cudaStream_t s) {
+  Level& f = P.L[k];
+  Level& c = P.L[k + 1];
+  const int dim = f.m.dim;
+  long long od[3] = {f.m.Nn[0], f.m.Nn[1], f.m.Nn[2]};
+  const T* in = rf;
+  T* bufs[2] = {(T*)P.t1, (T*)P.t2};
+  for (int a = 0; a < dim; ++a) {
+    od[a] = c.m.Nn[a];
+    const bool last = (a == dim - 1);
+    T* out = last ? rc : bufs[a & 1];
+    TRY(axis_pass<T>(in, out, od, a, f.PT[a], a == 0, last, 0, s));
+    in = out;
+  }
+  return HMG_OK;
+}
+
+// `steps` smoothing steps on level k. zero: x is taken as 0 on input.
+template <typename T>
+hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero, cudaStream_t s) {
+  Level& l = P.L[k];
+  const hmg_desc& D = P.desc;
+  const long long n = l.m.N;
+  T* r = Acc<T>::r(l);
+  T* d = Acc<T>::d(l);
+  const T* dinv = Acc<T>::dinv(l);
+  if (steps <= 0) {
+    if (zero) TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+    return HMG_OK;
+  }
+  if (D.smoother == HMG_SMOOTH_JACOBI) {
+    const T w = (T)D.omega;
+    for (int st = 0; st < steps; ++st) {
+      if (st == 0 && zero) {
+        TRY(jacobi_first<T>(x, b, dinv, n, w, s));
+      } else {
+        TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CHECK(apply_level(P, k, x, r, (T)-1, s));
+        TRY(jacobi_step<T>(x, r, b, dinv, n, w, 0, s));
+      }
+    }
+    return HMG_OK;
+  }
+  // Chebyshev acceleration of Jacobi on [lo, hi] (Saad, Iterative Methods, Alg. 12.1)
+  const double hi = D.cheb_safety * l.lam, lo = D.cheb_lo_frac * hi;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  for (int st = 0; st < steps; ++st) {
+    if (st == 0) {
+      if (zero) {
+        TRY(cheb_first<T>(x, d, b, dinv, n, (T)(1.0 / theta), s));
+      } else {
+        TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        CHECK(apply_level(P, k, x, r, (T)-1, s));
+        TRY(cheb_step<T>(x, d, r, b, dinv, n, (T)0, (T)(1.0 / theta), 0, s));
+      }
+      continue;
+    }
+    TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    CHECK(apply_level(P, k, x, r, (T)-1, s));
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    TRY(cheb_step<T>(x, d, r, b, dinv, n, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), 0, s));
+    rho = rho_new;
+  }
+  return HMG_OK;
+}
+
+hmg_status coarse(ProblemImpl& P, int k, const double* b, double* x, cudaStream_t s) {
+  Level& l = P.L[k];
+  TRY(cudaMemsetAsync(x, 0, l.m.N * sizeof(double), s));
+  if (l.nI > 0) TRY(coarse_solve(l.Ainv, b, x, l.gmap, l.nI, s));
+  return HMG_OK;
+}
+hmg_status coarse(ProblemImpl& P, int k, const float* b, float* x, cudaStream_t s) {
+  Level& l = P.L[k];
+  TRY(cudaMemsetAsync(x, 0, l.m.N * sizeof(float), s));
+  if (l.nI > 0) TRY(coarse_solve_f32(l.Ainv, b, x, l.gmap, l.nI, s));
+  return HMG_OK;
+}
+
+// One V(nu_pre, nu_post) cycle on level k for A_k x = b (zero: x starts at 0).
+template <typename T>
+hmg_status vcycle(ProblemImpl& P, int k, const T* b, T* x, bool zero, cudaStream_t s) {
+  const int last = (int)P.L.size() - 1;
+  if (k == last) return coarse(P, k, b, x, s);
+  Level& l = P.L[k];
+  Level& c = P.L[k + 1];
+  const long long n = l.m.N;
+  T* r = Acc<T>::r(l);
+  CHECK(smooth<T>(P, k, b, x, P.desc.nu_pre, zero, s));
+  TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CHECK(apply_level(P, k, x, r, (T)-1, s));
+  CHECK(restrict_<T>(P, k, r, Acc<T>::b(c), s));
+  CHECK(vcycle<T>(P, k + 1, Acc<T>::b(c), Acc<T>::x(c), true, s));
+  CHECK(prolong<T>(P, k, Acc<T>::x(c), x, true, s));
+  CHECK(smooth<T>(P, k, b, x, P.desc.nu_post, false, s));
+  return HMG_OK;
+}
+
+// z = B r on the finest level (FP64 in and out; FP32 internally for the mixed form).
+hmg_status precondition(ProblemImpl& P, const double* r, double* z, cudaStream_t s) {
+  if (P.desc.smooth_prec == HMG_PREC_FP32 && P.L.size() > 1) {
+    Level& l = P.L[0];
+    TRY(to_f32(l.b32, r, l.m.N, s));
+    CHECK(vcycle<float>(P, 0, l.b32, l.x32, true, s));
+    TRY(to_f64(z, l.x32, l.m.N, s));
+    return HMG_OK;
+  }
+  return vcycle<double>(P, 0, r, z, true, s);
+}
+
+hmg_status dot_to(ProblemImpl& P, const double* x, const double* y, long long n, int op, int idx, int aux,
+                  bool to_host, cudaStream_t s) {
+  TRY(dot_partial(x, y, n, P.partial, s));
+  TRY(finish(P.partial, P.S, op, idx, aux, to_host ? P.hostS : nullptr, s));
+  return HMG_OK;
+}
+
+hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
+  Level& l = P.L[k];
+  const int m = (int)std::min<long long>(P.desc.arnoldi_iters, l.nI);
+  if (m < 1) { l.lam = 1.0; return HMG_OK; }
+  const long long n = l.m.N;
+  std::vector<double*> V(m + 1, nullptr);
+  double* Hd = nullptr;
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* p : tmp) cudaFree(p); };
+  for (int j = 0; j <= m; ++j) {
+    if (cudaMalloc((void**)&V[j], n * sizeof(double)) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
+    tmp.push_back(V[j]);
+  }
+  if (cudaMalloc((void**)&Hd, (m + 1) * m * sizeof(double)) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
+  tmp.push_back(Hd);
+  hmg_status st = [&]() -> hmg_status {
+    TRY(cudaMemsetAsync(Hd, 0, (m + 1) * m * sizeof(double), s));
+    const unsigned long long seed = (P.desc.arnoldi_seed ? P.desc.arnoldi_seed : 0x1402593800000000ull) + (unsigned long long)k;
+    TRY(start_vector(V[0], l.m, seed, s));
+    TRY(dot_partial(V[0], V[0], n, P.partial, s));
+    TRY(finish(P.partial, P.S, FIN_SQRT, S_TMP, 0, nullptr, s));
+    TRY(div_dev(V[0], V[0], n, P.S + S_TMP, s));
+    for (int j = 0; j < m; ++j) {
+      double* w = V[j + 1];
+      TRY(cudaMemsetAsync(w, 0, n * sizeof(double), s));
+      TRY(launch_apply_f64(l.m, l.basis, V[j], w, l.G, 1.0, s));
+      TRY(scale_by(w, l.dinv, n, s));
+      for (int i = 0; i <= j; ++i) {
+        TRY(dot_partial(w, V[i], n, P.partial, s));
+        TRY(finish(P.partial, Hd, FIN_STORE, i * m + j, 0, nullptr, s));
+        TRY(axpy_dev(w, V[i], n, Hd + i * m + j, -1.0, s));
+      }
+      TRY(dot_partial(w, w, n, P.partial, s));
+      TRY(finish(P.partial, Hd, FIN_SQRT, (j + 1) * m + j, 0, nullptr, s));
+      if (j + 1 < m) TRY(div_dev(w, w, n, Hd + (j + 1) * m + j, s));
+    }
+    std::vector<double> H((m + 1) * m);
+    TRY(cudaMemcpyAsync(H.data(), Hd, H.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    l.lam = hessenberg_max_real_eig(H.data(), m);
+    if (!(l.lam > 0.0) || !isfinite(l.lam)) { set_error("Chebyshev bound estimate failed"); return HMG_ENAN; }
+    return HMG_OK;
+  }();
+  cleanup();
+  return st;
+}
+
+hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
+  const long long nI = l.nI;
+  if (nI == 0) return HMG_OK;
+  if (nI > 12000) {
+    set_error("coarsest level has " + std::to_string(nI) + " unknowns; the dense exact solve allows 12000: add levels");
+    return HMG_EINVAL;
+  }
+  TRY(P.alloc((void**)&l.Ainv, (size_t)nI * nI * sizeof(double)));
+  std::vector<long long> gm;
+  gm.reserve(nI);
+  for (long long g = 0; g < l.m.N; ++g) {
+    const long long I = g % l.m.Nn[0], r = g / l.m.Nn[0], J = r % l.m.Nn[1], K = r / l.m.Nn[1];
+    bool bd = I == 0 || I == l.m.Nn[0] - 1 || J == 0 || J == l.m.Nn[1] - 1;
+    if (l.m.dim == 3) bd = bd || K == 0 || K == l.m.Nn[2] - 1;
+    if (!bd) gm.push_back(g);
+  }
+  TRY(P.alloc((void**)&l.gmap, nI * sizeof(long long)));
+  TRY(cudaMemcpy(l.gmap, gm.data(), nI * sizeof(long long), cudaMemcpyHostToDevice));
+  TRY(launch_elem_dense(l.m, l.basis, l.G, l.Ainv, nI, s));
+  double *rowk = nullptr, *colk = nullptr;
+  TRY(cudaMalloc((void**)&rowk, nI * sizeof(double)));
+  if (cudaMalloc((void**)&colk, nI * sizeof(double)) != cudaSuccess) { cudaFree(rowk); set_error("alloc"); return HMG_ENOMEM; }
+  cudaError_t e = gauss_jordan_inverse(l.Ainv, nI, rowk, colk, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(rowk);
+  cudaFree(colk);
+  TRY(e);
+  TRY(e2);
+  return HMG_OK;
+}
+
+hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
+  const hmg_desc& D = P.desc;
+  std::vector<std::pair<std::vector<int>, int>> shapes;
+  CHECK(level_shapes(D, shapes));
+  P.L.resize(shapes.size());
+  size_t max_stage = 0, max_tbuf = 0;
+  for (size_t k = 0; k < shapes.size(); ++k) {
+    Level& l = P.L[k];
+    l.m = make_mesh(D.dim, shapes[k].first.data(), shapes[k].second);
+    make_basis(l.m.p, &l.basis);
+    l.nI = interior_count(l.m);
+    max_stage = std::max(max_stage, (size_t)(l.m.nelem * np_of(l.m) * D.dim * (D.dim + 1)) * sizeof(double));
+  }
+  // transfer intermediates: largest partial product over all passes
+  for (size_t k = 0; k + 1 < P.L.size(); ++k) {
+    const Mesh& f = P.L[k].m;
+    const Mesh& c = P.L[k + 1].m;
+    long long od[3] = {c.Nn[0], c.Nn[1], c.Nn[2]};
+    for (int a = 0; a < D.dim; ++a) { od[a] = f.Nn[a]; max_tbuf = std::max(max_tbuf, (size_t)(od[0] * od[1] * od[2])); }
+    long long rd[3] = {f.Nn[0], f.Nn[1], f.Nn[2]};
+    for (int a = 0; a < D.dim; ++a) { rd[a] = c.Nn[a]; max_tbuf = std::max(max_tbuf, (size_t)(rd[0] * rd[1] * rd[2])); }
+  }
+  TRY(P.alloc((void**)&P.S, 64 * sizeof(double)));
+  TRY(P.alloc((void**)&P.partial, kRedBlocks * sizeof(double)));
+  TRY(cudaMallocHost((void**)&P.hostS, 16 * sizeof(double)));
+  TRY(P.alloc(&P.t1, max_tbuf * sizeof(double)));
+  TRY(P.alloc(&P.t2, max_tbuf * sizeof(double)));
+  const long long N0 = P.L[0].m.N;
+  TRY(P.alloc((void**)&P.pr, N0 * sizeof(double)));
+  TRY(P.alloc((void**)&P.pz, N0 * sizeof(double)));
+  TRY(P.alloc((void**)&P.pp, N0 * sizeof(double)));
+  TRY(P.alloc((void**)&P.ph, N0 * sizeof(double)));
+
+  double* Jstage = nullptr;
+  int* bad = nullptr;
+  TRY(cudaMalloc((void**)&Jstage, max_stage));
+  if (cudaMalloc((void**)&bad, sizeof(int)) != cudaSuccess) { cudaFree(Jstage); set_error("alloc"); return HMG_ENOMEM; }
+  hmg_status st = [&]() -> hmg_status {
+    const bool mixed = D.smooth_prec == HMG_PREC_FP32;
+    for (size_t k = 0; k < P.L.size(); ++k) {
+      Level& l = P.L[k];
+      const long long n = l.m.N;
+      const long long gsz = l.m.nelem * np_of(l.m);
+      TRY(P.alloc((void**)&l.G, gsz * nc_of(D.dim) * sizeof(double)));
+      TRY(P.alloc((void**)&l.wdetJ, gsz * sizeof(double)));
+      TRY(P.alloc((void**)&l.dinv, n * sizeof(double)));
+      TRY(P.alloc((void**)&l.b, n * sizeof(double)));
+      TRY(P.alloc((void**)&l.x, n * sizeof(double)));
+      TRY(P.alloc((void**)&l.r, n * sizeof(double)));
+      TRY(P.alloc((void**)&l.d, n * sizeof(double)));
+      TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      TRY(launch_geometry(l.m, l.basis, D.warp_amp, D.mu_a, D.mu_b, D.mu_k, Jstage, l.G, l.wdetJ, bad, s));
+      int hbad = 0;
+      TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRY(cudaStreamSynchronize(s));
+      if (hbad) { set_error("non-positive Jacobian determinant: the mapped mesh is folded"); return HMG_EINVAL; }
+      // diagonal -> D^-1 (the diagonal is accumulated in l.r, then cleared)
+      TRY(launch_diag(l.m, l.basis, l.G, l.r, s));
+      TRY(dinv_from_diag(l.r, l.dinv, n, s));
+      TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));
+      if (mixed) {
+        TRY(P.alloc((void**)&l.G32, gsz * nc_of(D.dim) * sizeof(float)));
+        TRY(P.alloc((void**)&l.dinv32, n * sizeof(float)));
+        TRY(P.alloc((void**)&l.b32, n * sizeof(float)));
+        TRY(P.alloc((void**)&l.x32, n * sizeof(float)));
+        TRY(P.alloc((void**)&l.r32, n * sizeof(float)));
+        TRY(P.alloc((void**)&l.d32, n * sizeof(float)));
+        TRY(to_f32(l.G32, l.G, gsz * nc_of(D.dim), s));
+        TRY(to_f32(l.dinv32, l.dinv, n, s));
+      }
+    }
+    for (size_t k = 0; k + 1 < P.L.size(); ++k)
+      for (int a = 0; a < D.dim; ++a) CHECK(build_axis(P, P.L[k], P.L[k + 1], a, &P.L[k].P[a], &P.L[k].PT[a]));
+    CHECK(build_coarse(P, P.L.back(), s));
+    if (D.smoother == HMG_SMOOTH_CHEB)
+      for (size_t k = 0; k + 1 < P.L.size(); ++k) CHECK(arnoldi(P, (int)k, s));
+    TRY(cudaStreamSynchronize(s));
+    return HMG_OK;
+  }();
+  cudaFree(Jstage);
+  cudaFree(bad);
+  return st;
+}
+
+bool level_ok(const hmg_problem* p, int level) {
+  if (!p || level < 0 || level >= (int)p->impl.L.size()) {
+    set_error("invalid problem handle or level");
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+hmg_status hmg_desc_default(hmg_desc* d) {
+  if (!d) return HMG_EINVAL;
+  memset(d, 0, sizeof(*d));
+  d->dim = 3;
+  d->nelem[0] = d->nelem[1] = d->nelem[2] = 8;
+  d->order = 4;
+  d->warp_amp = 0.0;
+  d->mu_a = 1.0;
+  d->mu_b = 0.0;
+  d->mu_k = 2.0;
+  d->hier = HMG_HIER_H;
+  d->n_hlevels = 3;
+  d->smoother = HMG_SMOOTH_CHEB;
+  d->nu_pre = 3;
+  d->nu_post = 3;
+  d->omega = 2.0 / 3.0;
+  d->arnoldi_iters = 10;
+  d->cheb_lo_frac = 0.25;
+  d->cheb_safety = 1.0;
+  d->arnoldi_seed = 0;
+  d->smooth_prec = HMG_PREC_FP64;
+  return HMG_OK;
+}
+
+hmg_status hmg_setup(const hmg_desc* desc, void* stream, hmg_problem** out) {
+  if (!out) { set_error("null output handle"); return HMG_EINVAL; }
+  *out = nullptr;
+  CHECK(validate(desc));
+  hmg_problem* p = new (std::nothrow) hmg_problem();
+  if (!p) { set_error("host allocation failed"); return HMG_ENOMEM; }
+  p->impl.desc = *desc;
+  if (cudaGetDevice(&p->impl.device) != cudaSuccess) {
+    delete p;
+    set_error("no CUDA device");
+    return HMG_EDEVICE;
+  }
+  hmg_status st = setup_impl(p->impl, (cudaStream_t)stream);
+  if (st != HMG_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    delete p;
+    return st;
+  }
+  p->impl.fine_applies = 0;
+  *out = p;
+  return HMG_OK;
+}
+
+hmg_status hmg_destroy(hmg_problem* p) {
+  if (!p) return HMG_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->impl.device) cudaSetDevice(p->impl.device);
+  delete p;
+  if (cur != p->impl.device) cudaSetDevice(cur);
+  return HMG_OK;
+}
+
+int hmg_nlevels(const hmg_problem* p) { return p ? (int)p->impl.L.size() : 0; }
+
+size_t hmg_ndof(const hmg_problem* p, int level) {
+  if (!level_ok(p, level)) return 0;
+  return (size_t)p->impl.L[level].m.N;
+}
+
+hmg_status hmg_level_info(const hmg_problem* p, int level, int* nelem3, int* order, size_t* ndof) {
+  if (!level_ok(p, level)) return HMG_EINVAL;
+  const Mesh& m = p->impl.L[level].m;
+  if (nelem3) for (int a = 0; a < 3; ++a) nelem3[a] = m.E[a];
+  if (order) *order = m.p;
+  if (ndof) *ndof = (size_t)m.N;
+  return HMG_OK;
+}
+
+size_t hmg_device_bytes(const hmg_problem* p) { return p ? p->impl.bytes : 0; }
+
+hmg_status hmg_node_coords(hmg_problem* p, int level, double* xyz, void* stream) {
+  if (!level_ok(p, level) || !xyz) { set_error("null argument"); return HMG_EINVAL; }
+  const Level& l = p->impl.L[level];
+  TRY(node_coords(xyz, l.m, l.basis.r, p->impl.desc.warp_amp, (cudaStream_t)stream));
+  return HMG_OK;
+}
+
+hmg_status hmg_rhs(hmg_problem* p, const double* f, double* b, void* stream) {
+  if (!level_ok(p, 0) || !f || !b) { set_error("null argument"); return HMG_EINVAL; }
+  Level& l = p->impl.L[0];
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(cudaMemsetAsync(b, 0, l.m.N * sizeof(double), s));
+  TRY(launch_mass(l.m, l.basis, f, b, l.wdetJ, s));
+  return HMG_OK;
+}
+
+hmg_status hmg_apply(hmg_problem* p, int level, const double* x, double* y, void* stream) {
+  if (!level_ok(p, level) || !x || !y) { set_error("null argument"); return HMG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(cudaMemsetAsync(y, 0, p->impl.L[level].m.N * sizeof(double), s));
+  return apply_level(p->impl, level, x, y, 1.0, s);
+}
+
+hmg_status hmg_diag_inv(hmg_problem* p, int level, double* dinv, void* stream) {
+  if (!level_ok(p, level) || !dinv) { set_error("null argument"); return HMG_EINVAL; }
+  Level& l = p->impl.L[level];
+  TRY(cudaMemcpyAsync(dinv, l.dinv, l.m.N * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return HMG_OK;
+}
+
+hmg_status hmg_lambda_max(const hmg_problem* p, int level, double* lam) {
+  if (!level_ok(p, level) || !lam) { set_error("null argument"); return HMG_EINVAL; }
+  *lam = p->impl.L[level].lam;
+  return HMG_OK;
+}
+
+hmg_status hmg_prolong(hmg_problem* p, int level, const double* xc, double* xf, void* stream) {
+  if (!level_ok(p, level) || level + 1 >= (int)p->impl.L.size() || !xc || !xf) {
+    set_error("prolongation needs a level with a coarser level below it");
+    return HMG_EINVAL;
+  }
+  return prolong<double>(p->impl, level, xc, xf, false, (cudaStream_t)stream);
+}
+
+hmg_status hmg_restrict(hmg_problem* p, int level, const double* rf, double* rc, void* stream) {
+  if (!level_ok(p, level) || level + 1 >= (int)p->impl.L.size() || !rf || !rc) {
+    set_error("restriction needs a level with a coarser level below it");
+    return HMG_EINVAL;
+  }
+  return restrict_<double>(p->impl, level, rf, rc, (cudaStream_t)stream);
+}
+
+hmg_status hmg_smooth(hmg_problem* p, int level, const double* b, double* x, int steps, int zero_guess,
+                      void* stream) {
+  if (!level_ok(p, level) || !b || !x || steps < 0) { set_error("bad argument"); return HMG_EINVAL; }
+  ProblemImpl& P = p->impl;
+  Level& l = P.L[level];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (level == (int)P.L.size() - 1 || (P.desc.smoother == HMG_SMOOTH_CHEB && !(l.lam > 0))) {
+    set_error("no smoother on the coarsest level");
+    return HMG_EINVAL;
+  }
+  // caller vectors may carry values on boundary nodes: smooth on masked copies
+  TRY(copy_masked(l.b, b, l.m, s));
+  if (!zero_guess) TRY(copy_masked(l.x, x, l.m, s));
+  CHECK(smooth<double>(P, level, l.b, l.x, steps, zero_guess != 0, s));
+  TRY(cudaMemcpyAsync(x, l.x, l.m.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return HMG_OK;
+}
+
+hmg_status hmg_vcycle(hmg_problem* p, const double* r, double* z, void* stream) {
+  if (!level_ok(p, 0) || !r || !z) { set_error("null argument"); return HMG_EINVAL; }
+  ProblemImpl& P = p->impl;
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(copy_masked(P.pr, r, P.L[0].m, s));
+  return precondition(P, P.pr, z, s);
+}
+
+hmg_status hmg_solve(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit, int* iters,
+                     double* res_hist, void* stream) {
+  if (!level_ok(p, 0) || !b || !u || maxit < 0 || !(rtol >= 0.0)) { set_error("bad argument"); return HMG_EINVAL; }
+  if (mode != HMG_MODE_MG && mode != HMG_MODE_PCG) { set_error("bad mode"); return HMG_EINVAL; }
+  ProblemImpl& P = p->impl;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Level& l0 = P.L[0];
+  const long long n = l0.m.N;
+  double* r = P.pr;
+  double* z = P.pz;
+  if (iters) *iters = 0;
+  TRY(cudaMemsetAsync(u, 0, n * sizeof(double), s));
+  TRY(copy_masked(r, b, l0.m, s));
+  CHECK(dot_to(P, r, r, n, FIN_STORE, S_RR0, 0, true, s));
+  TRY(cudaStreamSynchronize(s));
+  const double r0 = sqrt(*P.hostS);
+  if (!isfinite(r0)) { set_error("non-finite right-hand side"); return HMG_ENAN; }
+  if (res_hist) res_hist[0] = r0;
+  if (r0 == 0.0) return HMG_OK;
+  const double tol = rtol * r0;
+  if (mode == HMG_MODE_MG) {
+    double* bm = P.ph;  // masked copy of b
+    TRY(cudaMemcpyAsync(bm, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    for (int it = 1; it <= maxit; ++it) {
+      CHECK(precondition(P, r, z, s));  // z = B (b - A u)
+      TRY(axpy(u, z, n, 1.0, s));       // u += z
+      TRY(cudaMemcpyAsync(r, bm, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CHECK(apply_level(P, 0, u, r, -1.0, s));
+      CHECK(dot_to(P, r, r, n, FIN_STORE, S_RR, 0, true, s));
+      TRY(cudaStreamSynchronize(s));
+      const double rn = sqrt(*P.hostS);
+      if (res_hist) res_hist[it] = rn;
+      if (iters) *iters = it;
+      if (!isfinite(rn)) { set_error("non-finite residual"); return HMG_ENAN; }
+      if (rn <= tol) return HMG_OK;
+    }
+    set_error("maximum number of V-cycles reached");
+    return HMG_ENOCONV;
+  }
+  // PCG (Algorithm 1, read as standard preconditioned CG from u0 = 0)
+  double* pp = P.pp;
+  double* h = P.ph;
+  CHECK(precondition(P, r, z, s));
+  TRY(cudaMemcpyAsync(pp, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CHECK(dot_to(P, z, r, n, FIN_STORE, S_RHO, 0, false, s));
+  for (int it = 1; it <= maxit; ++it) {
+    TRY(cudaMemsetAsync(h, 0, n * sizeof(double), s));
+    CHECK(apply_level(P, 0, pp, h, 1.0, s));
+    CHECK(dot_to(P, pp, h, n, FIN_STORE, S_PH, 0, false, s));
+    TRY(pcg_update(u, r, pp, h, n, P.S, P.partial, s));
+    TRY(finish(P.partial, P.S, FIN_STORE, S_RR, 0, P.hostS, s));
+    TRY(cudaStreamSynchronize(s));
+    const double rn = sqrt(*P.hostS);
+    if (res_hist) res_hist[it] = rn;
+    if (iters) *iters = it;
+    if (!isfinite(rn)) { set_error("non-finite residual"); return HMG_ENAN; }
+    if (rn <= tol) return HMG_OK;
+    CHECK(precondition(P, r, z, s));
+    CHECK(dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s));
+    TRY(pcg_direction(pp, z, n, P.S, s));
+  }
+  set_error("maximum number of PCG iterations reached");
+  return HMG_ENOCONV;
+}
+
+long long hmg_fine_applies(const hmg_problem* p) { return p ? p->impl.fine_applies : 0; }
+
+long long hmg_launch_count(void) { return add_launches(0); }
+
+const char* hmg_status_string(hmg_status s) {
+  switch (s) {
+    case HMG_OK: return "ok";
+    case HMG_EINVAL: return "invalid argument";
+    case HMG_ENOMEM: return "out of memory";
+    case HMG_ENOCONV: return "not converged";
+    case HMG_EDEVICE: return "CUDA error";
+    case HMG_ETIMEOUT: return "timed out";
+    case HMG_EBUSY: return "busy";
+    case HMG_ENAN: return "non-finite value";
+  }
+  return "unknown status";
+}
+
+const char* hmg_last_error(void) { return g_err.c_str(); }
+
+hmg_status hmg_host_basis(int order, double* gll, double* gx, double* gw) {
+  if (order < 1 || order > 16) { set_error("order must be in 1..16"); return HMG_EINVAL; }
+  Basis1D b;
+  make_basis(order, &b);
+  for (int i = 0; i <= order; ++i) {
+    if (gll) gll[i] = b.r[i];
+    if (gx) gx[i] = b.g[i];
+    if (gw) gw[i] = b.w[i];
+  }
+  return HMG_OK;
+}
+
+hmg_status hmg_host_hessenberg_max_real_eig(const double* H, int m, double* out) {
+  if (!H || !out || m < 1) { set_error("bad argument"); return HMG_EINVAL; }
+  *out = hessenberg_max_real_eig(H, m);
+  return isfinite(*out) ? HMG_OK : HMG_ENOCONV;
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// Host launchers of the element kernels, dispatched from the runtime order p to the
+// compile-time node count N = p + 1 (2..17).
+#pragma once
+
+#include "common.cuh"
+
+namespace hmg {
+
+// y += alpha * A x (FP64 or FP32 data; G in the same precision).
+cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
+                             const double* G, double alpha, cudaStream_t s);
+cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
+                             const float* G, float alpha, cudaStream_t s);
+
+// Geometry: stage buffer J [E][dim*(dim+1)][NP], then G [E][NC][NP] and wdetJ [E][NP].
+// *bad (device int) is set to 1 where det J <= 0.
+cudaError_t launch_geometry(const Mesh& m, const Basis1D& b, double warp_amp, double mu_a,
+                            double mu_b, double mu_k, double* Jstage, double* G, double* wdetJ,
+                            int* bad, cudaStream_t s);
+// diag += diag(A) over interior nodes.
+cudaError_t launch_diag(const Mesh& m, const Basis1D& b, const double* G, double* diag, cudaStream_t s);
+// b += M f over interior rows.
+cudaError_t launch_mass(const Mesh& m, const Basis1D& b, const double* f, double* out,
+                        const double* wdetJ, cudaStream_t s);
+// A[nI x nI] += interior stiffness (dense).
+cudaError_t launch_elem_dense(const Mesh& m, const Basis1D& b, const double* G, double* A,
+                              long long nI, cudaStream_t s);
+
+// Elements per block and dynamic shared memory of the apply kernel.
+int apply_epb(int dim, int n, size_t elem_bytes);
+
+}  // namespace hmg

@@ -1,0 +1,457 @@
+// Level-vector kernels (see vector.cuh). All loops are grid-stride with a fixed grid so
+// that every reduction sums its terms in the same order on every call (deterministic).
+#include <math.h>
+
+#include <type_traits>
+
+#include "vector.cuh"
+
+namespace hmg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(long long n) {
+  long long g = (n + kThreads - 1) / kThreads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (blockDim.x == kThreads); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[kThreads / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = lane < kThreads / 32 ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dot_partial(const T* __restrict__ x, const T* __restrict__ y,
+                                                          long long n, double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    acc = fma((double)x[i], (double)y[i], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ partial, double* S, int op,
+                                                     int idx, int aux) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < kRedBlocks; i += kThreads) acc += partial[i];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    if (op == FIN_STORE) S[idx] = acc;
+    else if (op == FIN_SQRT) S[idx] = sqrt(acc);
+    else {  // FIN_RHO_BETA: beta = new / old, rho = new
+      S[aux] = acc / S[idx];
+      S[idx] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pcg_update(double* __restrict__ u, double* __restrict__ r,
+                                                         const double* __restrict__ p, const double* __restrict__ h,
+                                                         long long n, const double* __restrict__ S,
+                                                         double* __restrict__ partial) {
+  const double alpha = S[S_RHO] / S[S_PH];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    u[i] = fma(alpha, p[i], u[i]);
+    const double ri = fma(-alpha, h[i], r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void k_pcg_dir(double* __restrict__ p, const double* __restrict__ z, long long n,
+                          const double* __restrict__ S) {
+  const double beta = S[S_BETA];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+template <typename T>
+__global__ void k_jacobi_first(T* __restrict__ x, const T* __restrict__ b, const T* __restrict__ dinv, long long n,
+                               T omega) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] = omega * dinv[i] * b[i];
+}
+
+template <typename T>
+__global__ void k_jacobi(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ b, const T* __restrict__ dinv,
+                         long long n, T omega, int reset) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    x[i] = fma(omega * dinv[i], r[i], x[i]);
+    if (reset) r[i] = b[i];
+  }
+}
+
+template <typename T>
+__global__ void k_cheb_first(T* __restrict__ x, T* __restrict__ d, const T* __restrict__ b,
+                             const T* __restrict__ dinv, long long n, T inv_theta) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T v = dinv[i] * b[i] * inv_theta;
+    d[i] = v;
+    x[i] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_cheb(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r, const T* __restrict__ b,
+                       const T* __restrict__ dinv, long long n, T c1, T c2, int reset) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T v = fma(c1, d[i], c2 * dinv[i] * r[i]);
+    d[i] = v;
+    x[i] += v;
+    if (reset) r[i] = b[i];
+  }
+}
+
+__global__ void k_dinv(const double* __restrict__ diag, double* __restrict__ dinv, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dinv[i] = diag[i] != 0.0 ? 1.0 / diag[i] : 0.0;
+}
+
+__device__ __forceinline__ bool on_boundary(long long g, const Mesh& m) {
+  const long long I = g % m.Nn[0];
+  const long long r = g / m.Nn[0];
+  const long long J = r % m.Nn[1];
+  const long long K = r / m.Nn[1];
+  bool b = (I == 0) | (I == m.Nn[0] - 1) | (J == 0) | (J == m.Nn[1] - 1);
+  if (m.dim == 3) b |= (K == 0) | (K == m.Nn[2] - 1);
+  return b;
+}
+
+__global__ void k_mask(double* __restrict__ v, const Mesh m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m.N; i += (long long)gridDim.x * blockDim.x)
+    if (on_boundary(i, m)) v[i] = 0.0;
+}
+
+__global__ void k_copy_masked(double* __restrict__ d, const double* __restrict__ s, const Mesh m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m.N; i += (long long)gridDim.x * blockDim.x)
+    d[i] = on_boundary(i, m) ? 0.0 : s[i];
+}
+
+__global__ void k_to_f32(float* __restrict__ d, const double* __restrict__ s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = (float)s[i];
+}
+
+__global__ void k_to_f64(double* __restrict__ d, const float* __restrict__ s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    d[i] = (double)s[i];
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014), counter form: z = seed + (c+1)*gamma, two
+// xor-shift-multiply rounds, final xor-shift; U(-1,1) = 2*(z>>11)*2^-53 - 1.
+__global__ void k_start(double* __restrict__ v, const Mesh m, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m.N; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const double u = 2.0 * (double)(z >> 11) * 0x1.0p-53 - 1.0;
+    v[i] = on_boundary(i, m) ? 0.0 : u;
+  }
+}
+
+__global__ void k_scale_by(double* __restrict__ w, const double* __restrict__ dinv, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    w[i] *= dinv[i];
+}
+
+__global__ void k_axpy_dev(double* __restrict__ y, const double* __restrict__ x, long long n,
+                           const double* __restrict__ coef, double sign) {
+  const double c = sign * coef[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(c, x[i], y[i]);
+}
+
+__global__ void k_div_dev(double* __restrict__ y, const double* __restrict__ x, long long n,
+                          const double* __restrict__ den) {
+  const double c = den[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] / c;
+}
+
+__global__ void k_copy_scalar(double* d, const double* s) { d[0] = s[0]; }
+
+__global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, long long n, double a) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+
+struct Gll {
+  double r[kMaxN];
+};
+
+__global__ void k_node_coords(double* __restrict__ xyz, const Mesh m, const Gll g, double amp) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < m.N; t += (long long)gridDim.x * blockDim.x) {
+    const long long idx[3] = {t % m.Nn[0], (t / m.Nn[0]) % m.Nn[1], t / (m.Nn[0] * m.Nn[1])};
+    double X[3], s = 1.0;
+    for (int a = 0; a < m.dim; ++a) {
+      const long long e = min(idx[a] / m.p, (long long)m.E[a] - 1);
+      X[a] = ((double)e + g.r[idx[a] - e * m.p]) / (double)m.E[a];
+      s *= sinpi(X[a]);
+    }
+    for (int a = 0; a < m.dim; ++a) xyz[a * m.N + t] = X[a] + amp * s;
+  }
+}
+
+template <typename T, typename V>
+__global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, long long o0, long long o1, long long o2,
+                       int axis, int n_in, const int* __restrict__ rowptr, const int* __restrict__ col,
+                       const V* __restrict__ val, int mask_in, int mask_out, int acc) {
+  const long long tot = o0 * o1 * o2;
+  long long id[3] = {0, 0, 0};
+  long long idim[3] = {o0, o1, o2};
+  idim[axis] = n_in;
+  const long long odim[3] = {o0, o1, o2};
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    id[0] = t % o0;
+    id[1] = (t / o0) % o1;
+    id[2] = t / (o0 * o1);
+    bool obd = false;
+    if (mask_out) {
+      for (int a = 0; a < 3; ++a)
+        if (odim[a] > 1) obd |= (id[a] == 0) | (id[a] == odim[a] - 1);
+    }
+    T s = T(0);
+    if (!obd) {
+      const int row = (int)id[axis];
+      for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) {
+        long long ii[3] = {id[0], id[1], id[2]};
+        ii[axis] = col[k];
+        if (mask_in) {
+          bool ibd = false;
+          for (int a = 0; a < 3; ++a)
+            if (idim[a] > 1) ibd |= (ii[a] == 0) | (ii[a] == idim[a] - 1);
+          if (ibd) continue;
+        }
+        s = fma((T)val[k], in[(ii[2] * idim[1] + ii[1]) * idim[0] + ii[0]], s);
+      }
+    }
+    if (acc) {
+      if (!obd) out[t] += s;
+    } else {
+      out[t] = s;
+    }
+  }
+}
+
+__global__ void k_gj_copy(const double* __restrict__ A, long long n, long long k, double* __restrict__ rowk,
+                          double* __restrict__ colk) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    rowk[i] = A[k * n + i];
+    colk[i] = A[i * n + k];
+  }
+}
+
+__global__ void k_gj_update(double* __restrict__ A, long long n, long long k, const double* __restrict__ rowk,
+                            const double* __restrict__ colk) {
+  const double piv = rowk[k];
+  const double ipiv = 1.0 / piv;
+  const long long tot = n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t / n, j = t - i * n;
+    double v;
+    if (i == k && j == k) v = ipiv;
+    else if (i == k) v = rowk[j] * ipiv;
+    else if (j == k) v = -colk[i] * ipiv;
+    else v = A[t] - colk[i] * rowk[j] * ipiv;
+    A[t] = v;
+  }
+}
+
+// one warp per output row
+template <typename T>
+__global__ void k_coarse_gemv(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x,
+                              const long long* __restrict__ gmap, long long n) {
+  const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+  const int lane = threadIdx.x & 31;
+  for (long long i = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); i < n; i += warps) {
+    double acc = 0.0;
+    const double* row = Ainv + i * n;
+    for (long long j = lane; j < n; j += 32) acc = fma(row[j], (double)b[gmap[j]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x[gmap[i]] = (T)acc;
+  }
+}
+
+}  // namespace
+
+cudaError_t dot_partial(const double* x, const double* y, long long n, double* partial, cudaStream_t s) {
+  k_dot_partial<double><<<kRedBlocks, kThreads, 0, s>>>(x, y, n, partial);
+  return counted(cudaGetLastError());
+}
+cudaError_t dot_partial_f32(const float* x, const float* y, long long n, double* partial, cudaStream_t s) {
+  k_dot_partial<float><<<kRedBlocks, kThreads, 0, s>>>(x, y, n, partial);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t finish(const double* partial, double* S, int op, int idx, int aux, double* host_copy, cudaStream_t s) {
+  k_finish<<<1, kThreads, 0, s>>>(partial, S, op, idx, aux);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || host_copy == nullptr) return e;
+  return cudaMemcpyAsync(host_copy, S + idx, sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t pcg_update(double* u, double* r, const double* p, const double* h, long long n, const double* S,
+                       double* partial, cudaStream_t s) {
+  k_pcg_update<<<kRedBlocks, kThreads, 0, s>>>(u, r, p, h, n, S, partial);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t pcg_direction(double* p, const double* z, long long n, const double* S, cudaStream_t s) {
+  k_pcg_dir<<<grid_for(n), kThreads, 0, s>>>(p, z, n, S);
+  return counted(cudaGetLastError());
+}
+
+template <typename T>
+cudaError_t jacobi_first(T* x, const T* b, const T* dinv, long long n, T omega, cudaStream_t s) {
+  k_jacobi_first<T><<<grid_for(n), kThreads, 0, s>>>(x, b, dinv, n, omega);
+  return counted(cudaGetLastError());
+}
+template <typename T>
+cudaError_t jacobi_step(T* x, T* r, const T* b, const T* dinv, long long n, T omega, int reset, cudaStream_t s) {
+  k_jacobi<T><<<grid_for(n), kThreads, 0, s>>>(x, r, b, dinv, n, omega, reset);
+  return counted(cudaGetLastError());
+}
+template <typename T>
+cudaError_t cheb_first(T* x, T* d, const T* b, const T* dinv, long long n, T inv_theta, cudaStream_t s) {
+  k_cheb_first<T><<<grid_for(n), kThreads, 0, s>>>(x, d, b, dinv, n, inv_theta);
+  return counted(cudaGetLastError());
+}
+template <typename T>
+cudaError_t cheb_step(T* x, T* d, T* r, const T* b, const T* dinv, long long n, T c1, T c2, int reset,
+                      cudaStream_t s) {
+  k_cheb<T><<<grid_for(n), kThreads, 0, s>>>(x, d, r, b, dinv, n, c1, c2, reset);
+  return counted(cudaGetLastError());
+}
+template cudaError_t jacobi_first<double>(double*, const double*, const double*, long long, double, cudaStream_t);
+template cudaError_t jacobi_first<float>(float*, const float*, const float*, long long, float, cudaStream_t);
+template cudaError_t jacobi_step<double>(double*, double*, const double*, const double*, long long, double, int,
+                                         cudaStream_t);
+template cudaError_t jacobi_step<float>(float*, float*, const float*, const float*, long long, float, int,
+                                        cudaStream_t);
+template cudaError_t cheb_first<double>(double*, double*, const double*, const double*, long long, double,
+                                        cudaStream_t);
+template cudaError_t cheb_first<float>(float*, float*, const float*, const float*, long long, float, cudaStream_t);
+template cudaError_t cheb_step<double>(double*, double*, double*, const double*, const double*, long long, double,
+                                       double, int, cudaStream_t);
+template cudaError_t cheb_step<float>(float*, float*, float*, const float*, const float*, long long, float, float,
+                                      int, cudaStream_t);
+
+cudaError_t dinv_from_diag(const double* diag, double* dinv, long long n, cudaStream_t s) {
+  k_dinv<<<grid_for(n), kThreads, 0, s>>>(diag, dinv, n);
+  return counted(cudaGetLastError());
+}
+cudaError_t mask_boundary(double* v, const Mesh& m, cudaStream_t s) {
+  k_mask<<<grid_for(m.N), kThreads, 0, s>>>(v, m);
+  return counted(cudaGetLastError());
+}
+cudaError_t copy_masked(double* dst, const double* src, const Mesh& m, cudaStream_t s) {
+  k_copy_masked<<<grid_for(m.N), kThreads, 0, s>>>(dst, src, m);
+  return counted(cudaGetLastError());
+}
+cudaError_t to_f32(float* dst, const double* src, long long n, cudaStream_t s) {
+  k_to_f32<<<grid_for(n), kThreads, 0, s>>>(dst, src, n);
+  return counted(cudaGetLastError());
+}
+cudaError_t to_f64(double* dst, const float* src, long long n, cudaStream_t s) {
+  k_to_f64<<<grid_for(n), kThreads, 0, s>>>(dst, src, n);
+  return counted(cudaGetLastError());
+}
+cudaError_t start_vector(double* v, const Mesh& m, unsigned long long seed, cudaStream_t s) {
+  k_start<<<grid_for(m.N), kThreads, 0, s>>>(v, m, seed);
+  return counted(cudaGetLastError());
+}
+cudaError_t scale_by(double* w, const double* dinv, long long n, cudaStream_t s) {
+  k_scale_by<<<grid_for(n), kThreads, 0, s>>>(w, dinv, n);
+  return counted(cudaGetLastError());
+}
+cudaError_t axpy_dev(double* y, const double* x, long long n, const double* coef, double sign, cudaStream_t s) {
+  k_axpy_dev<<<grid_for(n), kThreads, 0, s>>>(y, x, n, coef, sign);
+  return counted(cudaGetLastError());
+}
+cudaError_t div_dev(double* y, const double* x, long long n, const double* den, cudaStream_t s) {
+  k_div_dev<<<grid_for(n), kThreads, 0, s>>>(y, x, n, den);
+  return counted(cudaGetLastError());
+}
+cudaError_t copy_scalar(double* dst, const double* src, cudaStream_t s) {
+  k_copy_scalar<<<1, 1, 0, s>>>(dst, src);
+  return counted(cudaGetLastError());
+}
+cudaError_t axpy(double* y, const double* x, long long n, double a, cudaStream_t s) {
+  k_axpy<<<grid_for(n), kThreads, 0, s>>>(y, x, n, a);
+  return counted(cudaGetLastError());
+}
+cudaError_t node_coords(double* xyz, const Mesh& m, const double* gll, double amp, cudaStream_t s) {
+  Gll g;
+  for (int i = 0; i < kMaxN; ++i) g.r[i] = i <= m.p ? gll[i] : 0.0;
+  k_node_coords<<<grid_for(m.N), kThreads, 0, s>>>(xyz, m, g, amp);
+  return counted(cudaGetLastError());
+}
+
+template <typename T>
+cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, const Axis1D& M, int mask_in,
+                      int mask_out, int accumulate, cudaStream_t s) {
+  const long long tot = od[0] * od[1] * od[2];
+  if (std::is_same<T, float>::value)
+    k_axis<T, float><<<grid_for(tot), kThreads, 0, s>>>(in, out, od[0], od[1], od[2], axis, M.n_in, M.rowptr,
+                                                         M.col, M.val32, mask_in, mask_out, accumulate);
+  else
+    k_axis<T, double><<<grid_for(tot), kThreads, 0, s>>>(in, out, od[0], od[1], od[2], axis, M.n_in, M.rowptr,
+                                                          M.col, M.val, mask_in, mask_out, accumulate);
+  return counted(cudaGetLastError());
+}
+template cudaError_t axis_pass<double>(const double*, double*, const long long*, int, const Axis1D&, int, int,
+                                       int, cudaStream_t);
+template cudaError_t axis_pass<float>(const float*, float*, const long long*, int, const Axis1D&, int, int, int,
+                                      cudaStream_t);
+
+cudaError_t gauss_jordan_inverse(double* A, long long n, double* rowk, double* colk, cudaStream_t s) {
+  const long long tot = n * n;
+  long long g = (tot + kThreads - 1) / kThreads;
+  if (g > 152LL * 16) g = 152LL * 16;
+  for (long long k = 0; k < n; ++k) {
+    k_gj_copy<<<grid_for(n), kThreads, 0, s>>>(A, n, k, rowk, colk);
+    k_gj_update<<<(unsigned)g, kThreads, 0, s>>>(A, n, k, rowk, colk);
+  }
+  return counted(cudaGetLastError(), 2 * n - 1);
+}
+
+cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const long long* gmap, long long n,
+                         cudaStream_t s) {
+  long long g = (n + 7) / 8;
+  if (g > 152LL * 16) g = 152LL * 16;
+  k_coarse_gemv<double><<<(unsigned)g, kThreads, 0, s>>>(Ainv, b, x, gmap, n);
+  return counted(cudaGetLastError());
+}
+cudaError_t coarse_solve_f32(const double* Ainv, const float* b, float* x, const long long* gmap, long long n,
+                             cudaStream_t s) {
+  long long g = (n + 7) / 8;
+  if (g > 152LL * 16) g = 152LL * 16;
+  k_coarse_gemv<float><<<(unsigned)g, kThreads, 0, s>>>(Ainv, b, x, gmap, n);
+  return counted(cudaGetLastError());
+}
+
+}  // namespace hmg

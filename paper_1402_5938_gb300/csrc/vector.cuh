@@ -1,0 +1,88 @@
+// Level-vector kernels: deterministic reductions, smoother and PCG updates, 1D transfer
+// passes, the dense coarsest solve, and the Arnoldi helpers.
+#pragma once
+
+#include "common.cuh"
+
+namespace hmg {
+
+// Scalars kept on the device (no host round trip inside an iteration).
+enum Scalar : int {
+  S_RHO = 0,    // (z, r) of PCG
+  S_PH = 1,     // (p, A p)
+  S_RR = 2,     // ||r||^2
+  S_BETA = 3,   // PCG beta
+  S_TMP = 4,    // scratch scalar (Arnoldi h_ij, norms)
+  S_RR0 = 5,    // ||r_0||^2
+  S_COUNT = 8
+};
+
+enum FinishOp : int { FIN_STORE = 0, FIN_SQRT = 1, FIN_RHO_BETA = 2 };
+
+constexpr int kRedBlocks = 1216;  // fixed partial count (8 x 152 SMs); fixed => deterministic sums
+
+// Axis transfer: one 1D CSR matrix (rows = output indices along the axis).
+struct Axis1D {
+  int n_out, n_in;
+  int* rowptr;       // device, n_out + 1
+  int* col;          // device, nnz
+  double* val;       // device, nnz
+  float* val32;      // device, nnz
+};
+
+// reductions: partial[kRedBlocks] then finish into S
+cudaError_t dot_partial(const double* x, const double* y, long long n, double* partial, cudaStream_t s);
+cudaError_t dot_partial_f32(const float* x, const float* y, long long n, double* partial, cudaStream_t s);
+cudaError_t finish(const double* partial, double* S, int op, int idx, int aux, double* host_copy,
+                   cudaStream_t s);
+
+// PCG: alpha = S_RHO / S_PH; u += alpha p; r -= alpha h; partial <- ||r||^2
+cudaError_t pcg_update(double* u, double* r, const double* p, const double* h, long long n,
+                       const double* S, double* partial, cudaStream_t s);
+// p = z + S_BETA * p
+cudaError_t pcg_direction(double* p, const double* z, long long n, const double* S, cudaStream_t s);
+
+// smoother updates (T = double or float)
+template <typename T>
+cudaError_t jacobi_first(T* x, const T* b, const T* dinv, long long n, T omega, cudaStream_t s);
+template <typename T>
+cudaError_t jacobi_step(T* x, T* r, const T* b, const T* dinv, long long n, T omega, int reset_r,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t cheb_first(T* x, T* d, const T* b, const T* dinv, long long n, T inv_theta, cudaStream_t s);
+template <typename T>
+cudaError_t cheb_step(T* x, T* d, T* r, const T* b, const T* dinv, long long n, T c1, T c2, int reset_r,
+                      cudaStream_t s);
+
+cudaError_t dinv_from_diag(const double* diag, double* dinv, long long n, cudaStream_t s);
+cudaError_t mask_boundary(double* v, const Mesh& m, cudaStream_t s);
+cudaError_t copy_masked(double* dst, const double* src, const Mesh& m, cudaStream_t s);
+cudaError_t to_f32(float* dst, const double* src, long long n, cudaStream_t s);
+cudaError_t to_f64(double* dst, const float* src, long long n, cudaStream_t s);
+
+// Arnoldi helpers
+cudaError_t start_vector(double* v, const Mesh& m, unsigned long long seed, cudaStream_t s);
+cudaError_t scale_by(double* w, const double* dinv, long long n, cudaStream_t s);
+cudaError_t axpy_dev(double* y, const double* x, long long n, const double* coef, double sign, cudaStream_t s);
+cudaError_t div_dev(double* y, const double* x, long long n, const double* den, cudaStream_t s);
+cudaError_t copy_scalar(double* dst, const double* src, cudaStream_t s);
+cudaError_t axpy(double* y, const double* x, long long n, double a, cudaStream_t s);
+// xyz[c*N + g] = physical coordinate c of node g (warp of the reference GLL grid)
+cudaError_t node_coords(double* xyz, const Mesh& m, const double* gll, double warp_amp, cudaStream_t s);
+
+// out (=, or += if accumulate) M_axis in, for a 3D array with output dims od[3]; input dims
+// equal od except along `axis` (n_in). mask_in: treat input nodes on the input grid's
+// boundary as zero; mask_out: write zero on output boundary nodes (no accumulation).
+template <typename T>
+cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, const Axis1D& M, int mask_in,
+                      int mask_out, int accumulate, cudaStream_t s);
+
+// Dense coarsest level: Gauss-Jordan inverse in place (SPD, no pivoting), and the solve
+// x[gmap[i]] = sum_j Ainv[i][j] b[gmap[j]].
+cudaError_t gauss_jordan_inverse(double* A, long long nI, double* rowk, double* colk, cudaStream_t s);
+cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const long long* gmap,
+                         long long nI, cudaStream_t s);
+cudaError_t coarse_solve_f32(const double* Ainv, const float* b, float* x, const long long* gmap,
+                             long long nI, cudaStream_t s);
+
+}  // namespace hmg

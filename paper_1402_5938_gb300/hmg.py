@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libhmg (include/hmg.h): argument marshalling only.
+
+Every function takes and returns the same things as its C counterpart; device vectors are
+passed as CUDA tensors (float64, contiguous, on the problem's device) and the stream is
+the current PyTorch stream unless one is given. No numerical work happens in Python.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhmg.so")
+
+HMG_OK, HMG_EINVAL, HMG_ENOMEM, HMG_ENOCONV, HMG_EDEVICE, HMG_ETIMEOUT, HMG_EBUSY, HMG_ENAN = 0, -1, -2, -3, -4, -5, -6, -7
+HIER = {"h": 0, "p": 1}
+SMOOTHER = {"jacobi": 0, "cheb": 1}
+MODE = {"mg": 0, "pcg": 1}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class HmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"hmg status {status}: {msg}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nelem", ctypes.c_int * 3), ("order", ctypes.c_int),
+        ("warp_amp", ctypes.c_double), ("mu_a", ctypes.c_double), ("mu_b", ctypes.c_double),
+        ("mu_k", ctypes.c_double), ("hier", ctypes.c_int), ("n_hlevels", ctypes.c_int),
+        ("smoother", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+        ("omega", ctypes.c_double), ("arnoldi_iters", ctypes.c_int),
+        ("cheb_lo_frac", ctypes.c_double), ("cheb_safety", ctypes.c_double),
+        ("arnoldi_seed", ctypes.c_ulonglong), ("smooth_prec", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P, _D, _I, _V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+_SIGS = {
+    "hmg_desc_default": (_I, [ctypes.POINTER(Desc)]),
+    "hmg_setup": (_I, [ctypes.POINTER(Desc), _V, ctypes.POINTER(_P)]),
+    "hmg_destroy": (_I, [_P]),
+    "hmg_nlevels": (_I, [_P]),
+    "hmg_ndof": (ctypes.c_size_t, [_P, _I]),
+    "hmg_level_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_size_t)]),
+    "hmg_device_bytes": (ctypes.c_size_t, [_P]),
+    "hmg_node_coords": (_I, [_P, _I, _V, _V]),
+    "hmg_rhs": (_I, [_P, _V, _V, _V]),
+    "hmg_apply": (_I, [_P, _I, _V, _V, _V]),
+    "hmg_diag_inv": (_I, [_P, _I, _V, _V]),
+    "hmg_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "hmg_prolong": (_I, [_P, _I, _V, _V, _V]),
+    "hmg_restrict": (_I, [_P, _I, _V, _V, _V]),
+    "hmg_smooth": (_I, [_P, _I, _V, _V, _I, _I, _V]),
+    "hmg_vcycle": (_I, [_P, _V, _V, _V]),
+    "hmg_solve": (_I, [_P, _I, _V, _V, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _V]),
+    "hmg_fine_applies": (ctypes.c_longlong, [_P]),
+    "hmg_launch_count": (ctypes.c_longlong, []),
+    "hmg_status_string": (ctypes.c_char_p, [_I]),
+    "hmg_last_error": (ctypes.c_char_p, []),
+    "hmg_host_basis": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "hmg_host_hessenberg_max_real_eig": (_I, [ctypes.POINTER(_D), _I, ctypes.POINTER(_D)]),
+}
+
+
+def lib():
+    """Load libhmg.so (built in-tree by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != HMG_OK:
+        raise HmgError(status, lib().hmg_last_error().decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, n=None):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"tensor has {t.numel()} entries, the level needs {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_desc(prob: dict) -> Desc:
+    """hmg_desc from a workload dictionary (see synth.problem)."""
+    d = Desc()
+    _check(lib().hmg_desc_default(ctypes.byref(d)))
+    d.dim = prob["dim"]
+    E = list(prob["nelem"]) + [1] * (3 - len(prob["nelem"]))
+    d.nelem = (ctypes.c_int * 3)(*E)
+    d.order = prob["order"]
+    d.warp_amp = prob.get("warp_amp", 0.0)
+    d.mu_a, d.mu_b, d.mu_k = prob.get("mu_a", 1.0), prob.get("mu_b", 0.0), prob.get("mu_k", 2.0)
+    d.hier = HIER[prob.get("hier", "h")]
+    d.n_hlevels = prob.get("n_hlevels", 3)
+    d.smoother = SMOOTHER[prob.get("smoother", "cheb")]
+    d.nu_pre, d.nu_post = prob.get("nu_pre", 3), prob.get("nu_post", 3)
+    d.omega = prob.get("omega", 2.0 / 3.0)
+    d.arnoldi_iters = prob.get("arnoldi_iters", 10)
+    d.cheb_lo_frac = prob.get("cheb_lo_frac", 0.25)
+    d.cheb_safety = prob.get("cheb_safety", 1.0)
+    d.arnoldi_seed = prob.get("arnoldi_seed", 0)
+    d.smooth_prec = PREC[prob.get("smooth_prec", "fp64")]
+    return d
+
+
+class Problem:
+    """Owner of one hmg_problem handle (device-resident hierarchy)."""
+
+    def __init__(self, prob: dict, stream=None):
+        self.desc = make_desc(prob)
+        h = ctypes.c_void_p()
+        _check(lib().hmg_setup(ctypes.byref(self.desc), _stream(stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # introspection
+    def nlevels(self):
+        return lib().hmg_nlevels(self.h)
+
+    def ndof(self, level=0):
+        return lib().hmg_ndof(self.h, level)
+
+    def level_info(self, level):
+        E = (ctypes.c_int * 3)()
+        p = ctypes.c_int()
+        n = ctypes.c_size_t()
+        _check(lib().hmg_level_info(self.h, level, E, ctypes.byref(p), ctypes.byref(n)))
+        return tuple(E), p.value, n.value
+
+    def device_bytes(self):
+        return lib().hmg_device_bytes(self.h)
+
+    def fine_applies(self):
+        return lib().hmg_fine_applies(self.h)
+
+    # operations (same names as the C ABI without the prefix)
+    def node_coords(self, level, xyz, stream=None):
+        _check(lib().hmg_node_coords(self.h, level, _ptr(xyz, self.desc.dim * self.ndof(level)), _stream(stream)))
+
+    def rhs(self, f, b, stream=None):
+        n = self.ndof(0)
+        _check(lib().hmg_rhs(self.h, _ptr(f, n), _ptr(b, n), _stream(stream)))
+
+    def apply(self, level, x, y, stream=None):
+        n = self.ndof(level)
+        _check(lib().hmg_apply(self.h, level, _ptr(x, n), _ptr(y, n), _stream(stream)))
+
+    def diag_inv(self, level, out, stream=None):
+        _check(lib().hmg_diag_inv(self.h, level, _ptr(out, self.ndof(level)), _stream(stream)))
+
+    def lambda_max(self, level):
+        v = ctypes.c_double()
+        _check(lib().hmg_lambda_max(self.h, level, ctypes.byref(v)))
+        return v.value
+
+    def prolong(self, level, xc, xf, stream=None):
+        _check(lib().hmg_prolong(self.h, level, _ptr(xc, self.ndof(level + 1)), _ptr(xf, self.ndof(level)),
+                                 _stream(stream)))
+
+    def restrict(self, level, rf, rc, stream=None):
+        _check(lib().hmg_restrict(self.h, level, _ptr(rf, self.ndof(level)), _ptr(rc, self.ndof(level + 1)),
+                                  _stream(stream)))
+
+    def smooth(self, level, b, x, steps, zero_guess=False, stream=None):
+        n = self.ndof(level)
+        _check(lib().hmg_smooth(self.h, level, _ptr(b, n), _ptr(x, n), int(steps), int(bool(zero_guess)),
+                                _stream(stream)))
+
+    def vcycle(self, r, z, stream=None):
+        n = self.ndof(0)
+        _check(lib().hmg_vcycle(self.h, _ptr(r, n), _ptr(z, n), _stream(stream)))
+
+    def solve(self, mode, b, u, rtol=1e-8, maxit=1000, stream=None, raise_on_noconv=False):
+        """Returns (status, iterations, residual history as a numpy array)."""
+        n = self.ndof(0)
+        it = ctypes.c_int()
+        hist = (ctypes.c_double * (maxit + 1))()
+        st = lib().hmg_solve(self.h, MODE[mode], _ptr(b, n), _ptr(u, n), float(rtol), int(maxit),
+                             ctypes.byref(it), hist, _stream(stream))
+        if st not in (HMG_OK, HMG_ENOCONV) or (raise_on_noconv and st != HMG_OK):
+            _check(st)
+        return st, it.value, np.array(hist[: it.value + 1])
+
+
+def launch_count():
+    """Kernels launched by libhmg so far in this process."""
+    return lib().hmg_launch_count()
+
+
+def host_basis(order):
+    n = order + 1
+    r, g, w = (ctypes.c_double * n)(), (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    _check(lib().hmg_host_basis(order, r, g, w))
+    return np.array(r), np.array(g), np.array(w)
+
+
+def host_hessenberg_max_real_eig(H):
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    m = H.shape[0]
+    out = ctypes.c_double()
+    st = lib().hmg_host_hessenberg_max_real_eig(H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), m,
+                                                ctypes.byref(out))
+    _check(st)
+    return out.value

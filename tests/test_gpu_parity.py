@@ -1,0 +1,241 @@
+"""GPU parity: every operation of the CUDA library, called through the C ABI, against
+the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 operator-level results (apply, diagonal, load vector, transfers,
+smoothing steps, one V-cycle) within 1e-12 relative (max-norm over interior nodes,
+relative to the largest reference entry) -- the operator apply of the specification;
+the V-cycle and smoother chains compose several applies and a dense inverse and are
+held to 1e-10. Solves: iteration counts within +-1 of the oracle, final relative
+residual <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, multigrid, transfer
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1402_5938_gb300 as pkg
+    return pkg
+
+
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def _z(n):
+    return torch.zeros(n, dtype=torch.float64, device=DEV)
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# Meshes spanning several thread-block tiles with ragged tails, 2D and 3D, p = 1..16.
+CASES = [
+    dict(dim=3, nelem=(5, 3, 2), order=2),
+    dict(dim=3, nelem=(3, 2, 2), order=4),
+    dict(dim=3, nelem=(4, 4, 4), order=1),
+    dict(dim=3, nelem=(2, 1, 1), order=7),
+    dict(dim=3, nelem=(2, 2, 1), order=8),
+    dict(dim=3, nelem=(1, 1, 1), order=16),
+    dict(dim=3, nelem=(2, 1, 1), order=11),
+    dict(dim=2, nelem=(7, 5), order=3),
+    dict(dim=2, nelem=(9, 8), order=1),
+    dict(dim=2, nelem=(3, 2), order=16),
+    dict(dim=2, nelem=(13, 11), order=6),
+]
+
+
+def _prob(case, **kw):
+    base = dict(warp_amp=0.1, mu_a=1.0, mu_b=1e3, mu_k=2.0, n_hlevels=1, smoother="jacobi")
+    base.update(kw)
+    return synth.problem(case["dim"], case["nelem"], case["order"], **base)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['dim']}d-{c['nelem']}-p{c['order']}")
+def test_apply_diag_rhs_coords_match_oracle(hmg, case):
+    prob = _prob(case)
+    P = hmg.Problem(prob)
+    d = fem.Discretization(case["dim"], case["nelem"], case["order"], warp_amp=0.1, mu_a=1.0, mu_b=1e3)
+    N = d.N
+    assert P.ndof(0) == N
+    x = synth.uniform_pm1(11, N)
+    y = _z(N)
+    P.apply(0, _t(x), y)
+    xyz = _z(case["dim"] * N)
+    P.node_coords(0, xyz)
+    dinv = _z(N)
+    P.diag_inv(0, dinv)
+    f = synth.nodal_field(5, N)
+    b = _z(N)
+    P.rhs(_t(f), b)
+    torch.cuda.synchronize()
+    y, xyz, dinv, b = (v.cpu().numpy() for v in (y, xyz, dinv, b))
+
+    A = d.stiffness()
+    x_int = x[d.interior]                    # boundary entries of x are ignored by the library
+    assert _rel(y[d.interior], A @ x_int) < 1e-12
+    assert np.all(y[d.boundary] == 0.0)
+    assert _rel(xyz.reshape(case["dim"], N).T, d.node_coords()) < 1e-14
+    assert _rel(dinv[d.interior], 1.0 / A.diagonal()) < 1e-12
+    assert np.all(dinv[d.boundary] == 0.0)
+    assert _rel(b[d.interior], d.rhs(f)) < 1e-12
+    P.close()
+
+
+TRANSFER_CASES = [
+    (dict(dim=3, nelem=(4, 2, 2), order=3), "h"),
+    (dict(dim=3, nelem=(2, 2, 2), order=8), "p"),
+    (dict(dim=3, nelem=(3, 1, 2), order=6), "p"),
+    (dict(dim=2, nelem=(6, 4), order=2), "h"),
+    (dict(dim=2, nelem=(3, 5), order=16), "p"),
+]
+
+
+@pytest.mark.parametrize("case,hier", TRANSFER_CASES, ids=lambda c: str(c))
+def test_prolong_restrict_match_oracle(hmg, case, hier):
+    prob = _prob(case, hier=hier, n_hlevels=1 if hier == "p" else 2)
+    P = hmg.Problem(prob)
+    (Ef, pf, Nf), (Ec, pc, Nc) = P.level_info(0), P.level_info(1)
+    dim = case["dim"]
+    fine = fem.Discretization(dim, Ef[:dim], pf, warp_amp=0.1)
+    coarse = fem.Discretization(dim, Ec[:dim], pc, warp_amp=0.1)
+    Pm = transfer.prolongation(fine, coarse)
+    xc = synth.uniform_pm1(21, Nc)
+    rf = synth.uniform_pm1(22, Nf)
+    xf, rc = _z(Nf), _z(Nc)
+    P.prolong(0, _t(xc), xf)
+    P.restrict(0, _t(rf), rc)
+    torch.cuda.synchronize()
+    xf, rc = xf.cpu().numpy(), rc.cpu().numpy()
+    assert _rel(xf[fine.interior], Pm @ xc[coarse.interior]) < 1e-13
+    assert _rel(rc[coarse.interior], Pm.T @ rf[fine.interior]) < 1e-13
+    assert np.all(xf[fine.boundary] == 0) and np.all(rc[coarse.boundary] == 0)
+    P.close()
+
+
+SMOOTH_CASES = [
+    (dict(dim=3, nelem=(4, 4, 2), order=2), "cheb", "h"),
+    (dict(dim=3, nelem=(2, 2, 2), order=4), "jacobi", "p"),
+    (dict(dim=2, nelem=(8, 6), order=4), "cheb", "p"),
+    (dict(dim=2, nelem=(4, 4), order=8), "cheb", "h"),
+]
+
+
+@pytest.mark.parametrize("case,smoother,hier", SMOOTH_CASES, ids=lambda c: str(c))
+def test_lambda_smoother_vcycle_match_oracle(hmg, case, smoother, hier):
+    prob = _prob(case, smoother=smoother, hier=hier, n_hlevels=2, nu_pre=2, nu_post=3)
+    P = hmg.Problem(prob)
+    H = multigrid.Hierarchy(prob)
+    assert P.nlevels() == len(H.levels)
+    if smoother == "cheb":
+        for k, L in enumerate(H.levels[:-1]):
+            assert abs(P.lambda_max(k) - L.lam) <= 1e-10 * L.lam
+    d = H.fine.disc
+    N = d.N
+    b = synth.uniform_pm1(31, N)
+    x0 = synth.uniform_pm1(32, N)
+    b[d.boundary] = 0
+    x0[d.boundary] = 0
+    # smoothing from a nonzero and from a zero guess
+    xg = _t(x0)
+    P.smooth(0, _t(b), xg, 3)
+    xz = _z(N)
+    P.smooth(0, _t(b), xz, 2, zero_guess=True)
+    z = _z(N)
+    P.vcycle(_t(b), z)
+    torch.cuda.synchronize()
+    ref_g = H.smooth(0, b[d.interior], x0[d.interior], 3)
+    ref_z = H.smooth(0, b[d.interior], None, 2)
+    ref_v = H.vcycle(b[d.interior])
+    assert _rel(xg.cpu().numpy()[d.interior], ref_g) < 1e-10
+    assert _rel(xz.cpu().numpy()[d.interior], ref_z) < 1e-10
+    assert _rel(z.cpu().numpy()[d.interior], ref_v) < 1e-10
+    P.close()
+
+
+SOLVE_CASES = [
+    (synth.mms2d_poisson(8, 4), "mg"),
+    (synth.mms2d_poisson(8, 4), "pcg"),
+    (synth.warped_var3d(4, 4, hier="h"), "pcg"),
+    (synth.warped_var3d(4, 4, hier="p"), "pcg"),
+    (synth.warped_var3d(4, 2, hier="h", smoother="jacobi"), "mg"),
+    (synth.problem(2, 8, 8, warp_amp=0.1, mu_b=1e3, hier="p"), "pcg"),
+]
+
+
+@pytest.mark.parametrize("prob,mode", SOLVE_CASES, ids=lambda c: str(c)[:60])
+def test_solve_matches_oracle(hmg, prob, mode):
+    P = hmg.Problem(prob)
+    H = multigrid.Hierarchy(prob)
+    d = H.fine.disc
+    N = d.N
+    f = synth.nodal_field(9, N)
+    b = _z(N)
+    P.rhs(_t(f), b)
+    u = _z(N)
+    a0 = P.fine_applies()
+    st, it, hist = P.solve(mode, b, u, rtol=1e-8, maxit=300)
+    applies = P.fine_applies() - a0
+    torch.cuda.synchronize()
+    b_ref = d.rhs(f)
+    solve = H.solve_mg if mode == "mg" else H.solve_pcg
+    u_ref, it_ref, hist_ref, ok = solve(b_ref)
+    assert st == 0 and ok
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    u_gpu = u.cpu().numpy()[d.interior]
+    res = np.linalg.norm(b_ref - H.fine.A @ u_gpu) / np.linalg.norm(b_ref)
+    assert res <= 1e-8
+    if it == it_ref:                          # same iteration path: same iterate up to rounding
+        assert _rel(u_gpu, u_ref) < 1e-8
+    # residual histories agree while well above rounding
+    k = min(len(hist), len(hist_ref))
+    sel = hist_ref[:k] > 1e-6 * hist_ref[0]
+    assert np.allclose(hist[:k][sel], hist_ref[:k][sel], rtol=1e-6)
+    # cost model: 1 residual + nu_pre + nu_post smoothing applies per iteration on the finest
+    # level (the first smoothing step from a zero guess needs none): Sec. 4.3
+    nu = prob["nu_pre"] + prob["nu_post"]
+    assert applies == (it * (1 + nu) if mode == "mg" else nu + it * 1 + (it - 1) * nu)
+    P.close()
+
+
+def test_mms_solution_accuracy_2d(hmg):
+    # C1: u = sin(pi x) sin(pi y), f = 2 pi^2 sin sin, 8x8 Q4, h-MG V(2,2) Chebyshev solver
+    prob = synth.mms2d_poisson(8, 4)
+    P = hmg.Problem(prob)
+    N = P.ndof(0)
+    xyz = _z(2 * N)
+    P.node_coords(0, xyz)
+    X = xyz.cpu().numpy().reshape(2, N)
+    f = 2 * np.pi ** 2 * np.sin(np.pi * X[0]) * np.sin(np.pi * X[1])
+    b = _z(N)
+    P.rhs(_t(f), b)
+    u = _z(N)
+    st, it, hist = P.solve("mg", b, u, rtol=1e-8, maxit=100)
+    assert st == 0
+    err = np.abs(u.cpu().numpy() - np.sin(np.pi * X[0]) * np.sin(np.pi * X[1])).max()
+    assert err < 1e-5, err
+    P.close()
+
+
+def test_invalid_descriptors_are_rejected(hmg):
+    with pytest.raises(hmg.HmgError):
+        hmg.Problem(synth.problem(3, 3, 2, n_hlevels=2))       # odd mesh cannot be halved
+    with pytest.raises(hmg.HmgError):
+        hmg.Problem(synth.problem(3, 2, 17))                   # order out of range
+    with pytest.raises(hmg.HmgError):
+        hmg.Problem(synth.problem(2, 4, 2, warp_amp=0.5))      # folded map
