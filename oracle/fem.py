@@ -205,36 +205,55 @@ class Discretization:
         form used at sizes where A cannot be assembled."""
         x_full = np.asarray(x_full, dtype=np.float64).copy()
         x_full[self.boundary] = 0.0
-        out = np.zeros(len(rows))
+        return self._weak_rows(rows, x_full)
+
+    def diag_rows(self, rows):
+        """A_ii = a(phi_i, phi_i) for selected global nodes (the weak form with u_h = phi_i)."""
+        return self._weak_rows(rows, None)
+
+    def _elements_of_node(self, g):
         p, d = self.p, self.dim
+        I = [self.node_axis_index[ax][g] for ax in range(d)]
+        cand = []
+        for ax in range(d):
+            cand.append([e for e in (I[ax] // p - 1, I[ax] // p)
+                         if 0 <= e < self.E[ax] and e * p <= I[ax] <= e * p + p])
+        elems = []
+        for combo in np.array(np.meshgrid(*cand, indexing="ij")).reshape(d, -1).T:
+            lin, stride = 0, 1
+            for ax in range(d):
+                lin += int(combo[ax]) * stride
+                stride *= self.E[ax]
+            elems.append(lin)
+        return np.array(elems)
+
+    def _weak_rows(self, rows, x_full):
+        out = np.zeros(len(rows))
+        d = self.dim
         tables = self.basis_tables()
         Phi, dPhi, W = tables
         ref = np.stack(dPhi, axis=-1)                                  # (q, a, k)
+        cache = {}
+
+        def element(e):
+            if e not in cache:
+                xq, J, detJ = self.element_geometry([e], tables)
+                Jinv = np.linalg.inv(J[0])
+                c = W * np.abs(detJ[0]) * self.mu(xq[0])
+                gl = self.element_nodes([e])[0]
+                gu = None
+                if x_full is not None:
+                    gu_ref = np.stack([dPhi[m] @ x_full[gl] for m in range(d)], axis=-1)
+                    gu = np.einsum("qki,qk->qi", Jinv, gu_ref)
+                cache[e] = (Jinv, c, gl, gu)
+            return cache[e]
+
         for r_i, g in enumerate(rows):
             if self.boundary[g]:
                 continue
-            I = [self.node_axis_index[ax][g] for ax in range(d)]
-            cand = []
-            for ax in range(d):
-                cand.append([e for e in (I[ax] // p - 1, I[ax] // p)
-                             if 0 <= e < self.E[ax] and e * p <= I[ax] <= e * p + p])
-            elems = []
-            for combo in np.array(np.meshgrid(*cand, indexing="ij")).reshape(d, -1).T:
-                lin, stride = 0, 1
-                for ax in range(d):
-                    lin += int(combo[ax]) * stride
-                    stride *= self.E[ax]
-                elems.append(lin)
-            elems = np.array(elems)
-            xq, J, detJ = self.element_geometry(elems, tables)
-            Jinv = np.linalg.inv(J)
-            c = W[None, :] * np.abs(detJ) * self.mu(xq.reshape(-1, d)).reshape(detJ.shape)
-            gl = self.element_nodes(elems)
-            for k in range(len(elems)):
-                a = int(np.flatnonzero(gl[k] == g)[0])
-                xe = x_full[gl[k]]
-                gu_ref = np.stack([dPhi[m] @ xe for m in range(d)], axis=-1)      # (q, k)
-                gu = np.einsum("qki,qk->qi", Jinv[k], gu_ref)
-                gphi = np.einsum("qki,qk->qi", Jinv[k], ref[:, a, :])
-                out[r_i] += np.sum(c[k] * np.sum(gu * gphi, axis=1))
+            for e in self._elements_of_node(g):
+                Jinv, c, gl, gu = element(int(e))
+                a = int(np.flatnonzero(gl == g)[0])
+                gphi = np.einsum("qki,qk->qi", Jinv, ref[:, a, :])
+                out[r_i] += np.sum(c * np.sum((gphi if gu is None else gu) * gphi, axis=1))
         return out

@@ -66,6 +66,7 @@ void set_error(const std::string& msg);
 
 // Number of kernels this library has launched (all threads); read by hmg_launch_count().
 long long add_launches(long long n);
+cudaError_t ensure_smem_ptr(const void* kernel, size_t bytes);
 inline cudaError_t counted(cudaError_t e, long long n = 1) {
   if (e == cudaSuccess) add_launches(n);
   return e;

@@ -59,17 +59,12 @@ GeoTab<N> make_geotab(const Basis1D& b) {
   return t;
 }
 
-// Opt a kernel into more than 48 KB of dynamic shared memory (once per device).
+// Opt a kernel into more than 48 KB of dynamic shared memory (once per kernel and device).
+cudaError_t ensure_smem_ptr(const void* kernel, size_t bytes);
 template <typename K>
 cudaError_t ensure_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
-  static unsigned done_mask = 0;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 32 && (done_mask >> dev) & 1u) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024));
-  if (e == cudaSuccess && dev < 32) done_mask |= 1u << dev;
-  return e;
+  return ensure_smem_ptr((const void*)kernel, bytes);
 }
 
 // Elements per block: fill about 64 KB of shared memory, at least one element.

@@ -362,50 +362,72 @@ k_mass(const double* __restrict__ f, double* __restrict__ b, const double* __res
 }
 
 // ---------------------------------------------------------------------------------------
-// Dense interior operator of a (small, coarsest) level: one block per element, one thread
-// per entry (a,b): K_ab = sum_q sum_ij G_ij(q) dphi_a/dxi_i(q) dphi_b/dxi_j(q), added into
-// A[ia*nI + ib] for interior nodes (interior numbering, x fastest).
+// Dense interior operator of a (small, coarsest) level: every tile of a block is one
+// (element e, local column b) pair; the element operator is applied to the unit vector
+// e_b by the same sum-factorized phases as k_apply (column b of K_e), and K_e[a][b] is
+// added into A[ia*nI + ib] for interior a and b (interior numbering, x fastest).
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N>
-__global__ void k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
-                             const __grid_constant__ GeoTab<N> tab, const long long nI) {
+__global__ void __launch_bounds__(256)
+k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
+             const __grid_constant__ Tab<N, double> tab, const long long nI, const int epb) {
   constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
-  const long long e = blockIdx.x;
-  const double* Ge = G + e * NC * NP;
-  for (int t = threadIdx.x; t < NP * NP; t += blockDim.x) {
-    const int a = t / NP, b = t - a * NP;
-    bool bda, bdb;
-    const long long ga = elem_node<DIM, N>(m, e, a, bda);
-    const long long gb = elem_node<DIM, N>(m, e, b, bdb);
-    if (bda || bdb) continue;
-    const int ai[3] = {a % N, (a / N) % N, a / (N * N)};
-    const int bi[3] = {b % N, (b / N) % N, b / (N * N)};
-    double s = 0.0;
-    for (int q = 0; q < NP; ++q) {
-      const int qi[3] = {q % N, (q / N) % N, q / (N * N)};
-      double da[3], db[3];  // reference gradients of phi_a, phi_b at Gauss point q
-      for (int i = 0; i < DIM; ++i) {
-        double pa = 1.0, pb = 1.0;
-        for (int d = 0; d < DIM; ++d) {
-          const double* T1 = (d == i) ? tab.Bd : tab.B;
-          pa *= T1[qi[d] * N + ai[d]];
-          pb *= T1[qi[d] * N + bi[d]];
-        }
-        da[i] = pa;
-        db[i] = pb;
-      }
-      const double* g = Ge + q;
-      if (DIM == 3) {
-        const double g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
-        s += da[0] * (g00 * db[0] + g01 * db[1] + g02 * db[2]) +
-             da[1] * (g01 * db[0] + g11 * db[1] + g12 * db[2]) +
-             da[2] * (g02 * db[0] + g12 * db[1] + g22 * db[2]);
-      } else {
-        const double g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
-        s += da[0] * (g00 * db[0] + g01 * db[1]) + da[1] * (g01 * db[0] + g11 * db[1]);
-      }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* U = reinterpret_cast<double*>(smem_raw);
+  double* V = U + epb * NP;
+  const long long t0 = (long long)blockIdx.x * epb;
+  const long long ntiles = m.nelem * NP;
+  const int ne = (int)min((long long)epb, ntiles - t0);
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    const int b = (int)((t0 + e) % NP);
+    U[t] = (a == b) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int d = 0; d < DIM; ++d) {
+    contract<DIM, N, double, false, false>(U, U, tab.B, d, ne);
+    __syncthreads();
+  }
+  for (int d = 0; d < DIM; ++d) contract<DIM, N, double, false, false>(U, V + d * epb * NP, tab.D, d, ne);
+  __syncthreads();
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, q = t - e * NP;
+    const long long el = (t0 + e) / NP;
+    const double* g = G + el * NC * NP + q;
+    if (DIM == 3) {
+      const double u0 = V[t], u1 = V[epb * NP + t], u2 = V[2 * epb * NP + t];
+      const double g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
+      V[t] = g00 * u0 + g01 * u1 + g02 * u2;
+      V[epb * NP + t] = g01 * u0 + g11 * u1 + g12 * u2;
+      V[2 * epb * NP + t] = g02 * u0 + g12 * u1 + g22 * u2;
+    } else {
+      const double u0 = V[t], u1 = V[epb * NP + t];
+      const double g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
+      V[t] = g00 * u0 + g01 * u1;
+      V[epb * NP + t] = g01 * u0 + g11 * u1;
     }
-    atomicAdd(A + interior_index<DIM>(m, ga) * nI + interior_index<DIM>(m, gb), s);
+  }
+  __syncthreads();
+  contract<DIM, N, double, true, false>(V, U, tab.D, 0, ne);
+  __syncthreads();
+  contract<DIM, N, double, true, true>(V + epb * NP, U, tab.D, 1, ne);
+  __syncthreads();
+  if (DIM == 3) {
+    contract<DIM, N, double, true, true>(V + 2 * epb * NP, U, tab.D, 2, ne);
+    __syncthreads();
+  }
+  for (int d = 0; d < DIM; ++d) {
+    contract<DIM, N, double, true, false>(U, U, tab.B, d, ne);
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
+    const int e = t / NP, a = t - e * NP;
+    const long long el = (t0 + e) / NP;
+    const int b = (int)((t0 + e) % NP);
+    bool bda, bdb;
+    const long long ga = elem_node<DIM, N>(m, el, a, bda);
+    const long long gb = elem_node<DIM, N>(m, el, b, bdb);
+    if (!bda && !bdb) atomicAdd(A + interior_index<DIM>(m, ga) * nI + interior_index<DIM>(m, gb), U[t]);
   }
 }
 

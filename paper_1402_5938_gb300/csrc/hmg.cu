@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <set>
 #include <new>
 #include <string>
 #include <vector>
@@ -25,6 +27,21 @@ namespace {
 std::atomic<long long> g_launches{0};
 }
 long long add_launches(long long n) { return g_launches.fetch_add(n) + n; }
+
+namespace {
+std::mutex g_smem_mu;
+std::set<std::pair<const void*, int>> g_smem_done;
+}
+cudaError_t ensure_smem_ptr(const void* kernel, size_t bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  if (g_smem_done.count({kernel, dev})) return cudaSuccess;
+  (void)bytes;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) g_smem_done.insert({kernel, dev});
+  return e;
+}
 
 struct Level {
   Mesh m{};

@@ -67,7 +67,14 @@ cudaError_t dense_dim(const Mesh& m, const Basis1D& b, const double* G, double* 
                       cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
-    k_elem_dense<DIM, N><<<(unsigned)m.nelem, 256, 0, s>>>(G, A, m, make_geotab<N>(b), nI);
+    constexpr int NP = Sh<DIM, N>::NP;
+    const size_t per = (size_t)(1 + DIM) * NP * sizeof(double);
+    const int epb = epb_for(per);
+    auto k = k_elem_dense<DIM, N>;
+    cudaError_t e = ensure_smem(k, per * epb);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (m.nelem * NP + epb - 1) / epb;
+    k<<<(unsigned)blocks, 256, per * epb, s>>>(G, A, m, make_tab<N, double>(b), nI, epb);
     return counted(cudaGetLastError());
   });
 }
