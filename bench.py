@@ -32,6 +32,9 @@ WORKLOAD = "3D warped var-coef Q4 16^3 (65^3=274,625 DOF), mu=1+1e3*sum cos^2(2 
 # FP64 peak of one GB300: 152 SMs x 2.07 GHz x 4 FP64 flops/clock/SM (2 FMA lanes) = 1.259 TFLOP/s
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply64<3,n> launch on this workload,
+# from the ncu capture summarized in profiles/apply64_fp64_q4_16cube.md (n = p + 1)
+APPLY_TRAFFIC = {5: 28.736768e6}
 
 
 def workload(hier):
@@ -273,8 +276,8 @@ def run_gpu(args):
             "fine_applies_per_solve": applies, "apply_gdofs": N / (apply_ms * 1e-3) / 1e9,
             "apply_ms": apply_ms,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                         "kernel": f"k_apply<3,{n},double>",
+                         "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": APPLY_TRAFFIC.get(n),
+                         "kernel": f"k_apply64<3,{n}>",
                          "note": "FP64 pipe; peak = 152 SM x 2.07 GHz x 4 flop/clk (nominal); "
                                  "algorithmic flops 24n^4+15n^3 per element"},
             "cpu_baseline": cpu,
@@ -289,6 +292,28 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_apply(args):
+    """Small fixed launch sequence for ncu: build the workload's hierarchy, then two
+    hmg_apply calls on each of the three finest levels (after the setup's Arnoldi applies)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1402_5938_gb300 import Problem
+    P = Problem(workload(args.hier))
+    for lev in range(min(3, P.nlevels())):
+        N = P.ndof(lev)
+        x = torch.from_numpy(synth.uniform_pm1(7, N)).cuda()
+        y = torch.zeros_like(x)
+        for _ in range(2):
+            P.apply(lev, x, y)
+    torch.cuda.synchronize()
+    P.close()
+    print("profile-apply ok")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,7 +321,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--hier", choices=["h", "p"], default="p")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
     args = ap.parse_args()
+    if args.profile_apply:
+        return run_profile_apply(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -171,6 +171,156 @@ k_apply(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ G, con
 }
 
 // ---------------------------------------------------------------------------------------
+// FP64 apply, y += alpha * A x. On GB300 a warp-wide DFMA occupies the SM's FP64 pipe
+// for ~16 cycles while shared-memory loads and integer work issue elsewhere, so this
+// variant optimizes for full warps and balanced SMs rather than for few loads: one
+// small thread block per group of NEG elements (no block-wide coupling between groups),
+// one thread per output point in every contraction (so NEG*N^d work items fill warps
+// for any N), tables and tiles in shared memory, per-element base offsets so the
+// gather/scatter use 32-bit local index arithmetic.
+// Buffers (4 per element tile): cur/nxt ping-pong for the B and B^T passes, and the
+// reference gradient (V0 in the free ping-pong buffer, V1, V2).
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+struct Apply64Cfg {
+  static constexpr int NP = Sh<DIM, N>::NP;
+  static constexpr int NEG = NP >= 100 ? 1 : (NP == 64 ? 2 : (NP == 27 ? 8 : (NP >= 16 ? 4 : 8)));
+  static constexpr int W = NEG * NP;
+  static constexpr int GT = W <= 512 ? 32 : (W <= 1000 ? 64 : (W <= 2200 ? 128 : (W <= 3400 ? 256 : 512)));
+  static constexpr size_t smem = (size_t)(2 * N * N + (DIM + 1) * W) * sizeof(double) + NEG * 16;
+};
+
+// sum_m M(idx, m) src[base + m*stride]  (TRN: M[m*N + idx], else M[idx*N + m])
+template <int N, bool TRN>
+__device__ __forceinline__ double pt_dot(const double* __restrict__ M, const double* src, int idx, int base,
+                                         int stride) {
+  double s = (TRN ? M[idx] : M[idx * N]) * src[base];
+#pragma unroll
+  for (int m = 1; m < N; ++m) s = fma(TRN ? M[m * N + idx] : M[idx * N + m], src[base + m * stride], s);
+  return s;
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(Apply64Cfg<DIM, N>::GT)
+k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ G, const Mesh m,
+          const __grid_constant__ Tab<N, double> tab, const double alpha) {
+  using C = Apply64Cfg<DIM, N>;
+  constexpr int NP = C::NP, NEG = C::NEG, W = C::W, NC = Sh<DIM, N>::NC;
+  constexpr int S1 = N, S2 = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sB = reinterpret_cast<double*>(smem_raw);
+  double* sD = sB + N * N;
+  double* T0 = sD + N * N;
+  double* T1 = T0 + W;
+  double* V1 = T1 + W;
+  double* V2 = V1 + W;  // 3D only
+  long long* ebase = reinterpret_cast<long long*>(T0 + (DIM + 1) * W);
+  int* eflag = reinterpret_cast<int*>(ebase + NEG);
+  const long long e0 = (long long)blockIdx.x * NEG;
+  const int ne = (int)min((long long)NEG, m.nelem - e0);
+  const int nt = ne * NP;
+  for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
+    sB[t] = tab.B[t];
+    sD[t] = tab.D[t];
+  }
+  if (threadIdx.x < ne) {
+    const long long e = e0 + threadIdx.x;
+    const int ex = (int)(e % m.E[0]);
+    const long long r = e / m.E[0];
+    const int ey = (int)(r % m.E[1]);
+    const int ez = (int)(r / m.E[1]);
+    ebase[threadIdx.x] = ((long long)ez * m.p * m.Nn[1] + (long long)ey * m.p) * m.Nn[0] + (long long)ex * m.p;
+    int f = (ex == 0) | ((ex == m.E[0] - 1) << 1) | ((ey == 0) << 2) | ((ey == m.E[1] - 1) << 3);
+    if (DIM == 3) f |= ((ez == 0) << 4) | ((ez == m.E[2] - 1) << 5);
+    eflag[threadIdx.x] = f;
+  }
+  __syncthreads();
+  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
+  auto node = [&](int t, bool& bd) -> long long {
+    const int e = t / NP, a = t - (t / NP) * NP;
+    const int i = a % N, j = (a / N) % N, k = DIM == 3 ? a / (N * N) : 0;
+    const int f = eflag[e];
+    bd = ((i == 0) & (f & 1)) | ((i == N - 1) & ((f >> 1) & 1)) | ((j == 0) & ((f >> 2) & 1)) |
+         ((j == N - 1) & ((f >> 3) & 1));
+    if (DIM == 3) bd |= ((k == 0) & ((f >> 4) & 1)) | ((k == N - 1) & ((f >> 5) & 1));
+    return ebase[e] + (long long)k * nxy + (long long)j * nx + i;
+  };
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    bool bd;
+    const long long g = node(t, bd);
+    T0[t] = bd ? 0.0 : x[g];
+  }
+  __syncthreads();
+  double* cur = T0;
+  double* nxt = T1;
+  // interpolation to the Gauss points, one direction at a time
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? S1 : S2);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      const int a = t % NP;
+      const int idx = d == 0 ? a % N : (d == 1 ? (a / N) % N : a / (N * N));
+      nxt[t] = pt_dot<N, false>(sB, cur, idx, t - idx * st, st);
+    }
+    __syncthreads();
+    double* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  // collocated reference gradient and the pointwise geometric factor
+  double* V0 = nxt;
+  const double* Gb = G + e0 * NC * NP;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int a = t % NP;
+    const int i = a % N, j = (a / N) % N;
+    const double* g = Gb + t / NP * NC * NP + a;
+    if (DIM == 3) {
+      const int k = a / (N * N);
+      const double g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
+      const double u0 = pt_dot<N, false>(sD, cur, i, t - i, 1);
+      const double u1 = pt_dot<N, false>(sD, cur, j, t - j * S1, S1);
+      const double u2 = pt_dot<N, false>(sD, cur, k, t - k * S2, S2);
+      V0[t] = g00 * u0 + g01 * u1 + g02 * u2;
+      V1[t] = g01 * u0 + g11 * u1 + g12 * u2;
+      V2[t] = g02 * u0 + g12 * u1 + g22 * u2;
+    } else {
+      const double g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
+      const double u0 = pt_dot<N, false>(sD, cur, i, t - i, 1);
+      const double u1 = pt_dot<N, false>(sD, cur, j, t - j * S1, S1);
+      V0[t] = g00 * u0 + g01 * u1;
+      V1[t] = g01 * u0 + g11 * u1;
+    }
+  }
+  __syncthreads();
+  // transposed derivative, summed over directions, into cur
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int a = t % NP;
+    const int i = a % N, j = (a / N) % N;
+    double s = pt_dot<N, true>(sD, V0, i, t - i, 1) + pt_dot<N, true>(sD, V1, j, t - j * S1, S1);
+    if (DIM == 3) {
+      const int k = a / (N * N);
+      s += pt_dot<N, true>(sD, V2, k, t - k * S2, S2);
+    }
+    cur[t] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const int st = d == 0 ? 1 : (d == 1 ? S1 : S2);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+      const int a = t % NP;
+      const int idx = d == 0 ? a % N : (d == 1 ? (a / N) % N : a / (N * N));
+      nxt[t] = pt_dot<N, true>(sB, cur, idx, t - idx * st, st);
+    }
+    __syncthreads();
+    double* tmp = cur; cur = nxt; nxt = tmp;
+  }
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    bool bd;
+    const long long g = node(t, bd);
+    if (!bd) atomicAdd(y + g, alpha * cur[t]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Geometry, stage 1: node coordinates x = X + amp prod sin(pi X) of every element node,
 // interpolated to the Gauss points (x_q) and differentiated (dx_c/dxi_d), written to
 // J[e][c*(DIM+1) + s][NP] with s = 0 for x_q and s = 1+d for dx_c/dxi_d.

@@ -27,10 +27,25 @@ cudaError_t apply_dim(const Mesh& m, const Basis1D& b, const T* x, T* y, const T
 
 }  // namespace
 
+template <int DIM>
+cudaError_t apply64_dim(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* G,
+                        double alpha, cudaStream_t s) {
+  return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
+    constexpr int N = decltype(nc)::value;
+    using C = Apply64Cfg<DIM, N>;
+    auto kern = k_apply64<DIM, N>;
+    cudaError_t e = ensure_smem(kern, C::smem);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (m.nelem + C::NEG - 1) / C::NEG;
+    if (blocks == 0) return cudaSuccess;
+    kern<<<(unsigned)blocks, C::GT, C::smem, s>>>(x, y, G, m, make_tab<N, double>(b), alpha);
+    return counted(cudaGetLastError());
+  });
+}
+
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, cudaStream_t s) {
-  return m.dim == 3 ? apply_dim<3, double>(m, b, x, y, G, alpha, s)
-                    : apply_dim<2, double>(m, b, x, y, G, alpha, s);
+  return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, s) : apply64_dim<2>(m, b, x, y, G, alpha, s);
 }
 
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
