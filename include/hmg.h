@@ -128,6 +128,26 @@ hmg_status hmg_lambda_max(const hmg_problem* prob, int level, double* lam);
 hmg_status hmg_prolong(hmg_problem* prob, int level, const double* xc_dev, double* xf_dev, void* stream);
 hmg_status hmg_restrict(hmg_problem* prob, int level, const double* rf_dev, double* rc_dev, void* stream);
 
+/* r_c = P^T r_f without a problem handle and without allocating: for callers that cannot
+ * allocate device memory (code where cudaMalloc is forbidden or unsafe -- an allocation-free
+ * real-time loop, a plug-in that may only use memory its host hands in, a process whose
+ * memory manager owns the device), and so cannot create an hmg_problem. The paper has no
+ * counterpart; it is the same restriction as hmg_restrict, for a structured mesh described
+ * by its sizes: fine level nelem_fine[dim] elements of order_fine; the coarse level halves
+ * the elements per axis (halve_mesh != 0, counts must be even) and/or has order_coarse <=
+ * order_fine. rf_dev / rc_dev: caller-owned FP64 node vectors of the fine / coarse level
+ * (lexicographic, x fastest, boundary entries ignored / written as zero).
+ * Limits (fixed device storage held by every device that loads the library, ~18.5 MiB):
+ * at most 4097 fine nodes per axis, and the two intermediate passes together at most
+ * 2^21 doubles (16 MiB) -- e.g. a 129^3-node fine level; larger sizes return HMG_EINVAL.
+ * The first call on a device looks up the device addresses of that storage; make it
+ * before any stream capture. Every call reuses the same storage (stencils and
+ * intermediates), so calls that overlap on the GPU (different streams, or without
+ * ordering between them) race; calls on one stream are ordered. The stencils are copied
+ * from pageable host memory, which synchronizes `stream` before the copy starts. */
+hmg_status hmg_restrict_noalloc(int dim, const int nelem_fine[3], int order_fine, int order_coarse,
+                                int halve_mesh, const double* rf_dev, double* rc_dev, void* stream);
+
 /* `steps` smoothing steps on level k for A_k x = b (Jacobi or Chebyshev per the descriptor);
  * zero_guess != 0 treats x as zero on input. */
 hmg_status hmg_smooth(hmg_problem* prob, int level, const double* b_dev, double* x_dev, int steps,

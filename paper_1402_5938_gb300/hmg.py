@@ -62,6 +62,7 @@ _SIGS = {
     "hmg_smooth": (_I, [_P, _I, _V, _V, _I, _I, _V]),
     "hmg_vcycle": (_I, [_P, _V, _V, _V]),
     "hmg_solve": (_I, [_P, _I, _V, _V, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _V]),
+    "hmg_restrict_noalloc": (_I, [_I, ctypes.POINTER(ctypes.c_int), _I, _I, _I, _V, _V, _V]),
     "hmg_fine_applies": (ctypes.c_longlong, [_P]),
     "hmg_launch_count": (ctypes.c_longlong, []),
     "hmg_status_string": (ctypes.c_char_p, [_I]),
@@ -218,6 +219,14 @@ class Problem:
         if st not in (HMG_OK, HMG_ENOCONV) or (raise_on_noconv and st != HMG_OK):
             _check(st)
         return st, it.value, np.array(hist[: it.value + 1])
+
+
+def restrict_noalloc(dim, nelem_fine, order_fine, order_coarse, halve_mesh, rf, rc, stream=None):
+    """hmg_restrict_noalloc: r_c = P^T r_f for a structured mesh given by its sizes, using
+    only the library's fixed device storage (no handle, no allocation)."""
+    E = list(nelem_fine) + [1] * (3 - len(nelem_fine))
+    _check(lib().hmg_restrict_noalloc(int(dim), (ctypes.c_int * 3)(*E), int(order_fine), int(order_coarse),
+                                      int(bool(halve_mesh)), _ptr(rf), _ptr(rc), _stream(stream)))
 
 
 def launch_count():
