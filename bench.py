@@ -292,6 +292,66 @@ def run_gpu(args):
     return 0
 
 
+def run_sweep(args):
+    """Order sweep at ~2M DOF (129^3 nodes; (64^3,2), (32^3,4), (16^3,8), (8^3,16)), same warp and
+    coefficient: per order the FP64 and FP32 apply times, and FP64 vs mixed-precision (FP32
+    V-cycle) PCG + p-MG time to 1e-8, iterations, and the mixed solution's relative difference
+    from the FP64 one. One JSON line per order (not the benchmark line)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1402_5938_gb300 import Problem
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b_.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b_))
+        return statistics.median(ts), out
+
+    for E, p in [(64, 2), (32, 4), (16, 8), (8, 16)]:
+        prob = synth.warped_var3d(E, p, hier="p")
+        P64 = Problem(prob)
+        P32 = Problem(dict(prob, smooth_prec="fp32"))
+        N = P64.ndof(0)
+        f = torch.from_numpy(synth.nodal_field(synth.SEED_PSWEEP3D, N)).to(dev)
+        b = torch.zeros(N, dtype=torch.float64, device=dev)
+        P64.rhs(f, b)
+        x, y = torch.zeros_like(b), torch.zeros_like(b)
+        x32, y32 = torch.zeros(N, dtype=torch.float32, device=dev), torch.zeros(N, dtype=torch.float32, device=dev)
+        t64, _ = timed(lambda: P64.apply(0, b, y), 10)
+        t32, _ = timed(lambda: P32.apply_f32(0, x32, y32), 10)
+        u64, u32 = torch.zeros_like(b), torch.zeros_like(b)
+        s64, (_, it64, h64) = timed(lambda: P64.solve("pcg", b, u64, rtol=1e-8, maxit=500), 3)
+        s32, (_, it32, h32) = timed(lambda: P32.solve("pcg", b, u32, rtol=1e-8, maxit=500), 3)
+        P64.apply(0, u32, y)
+        res32 = float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
+        diff = float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64))
+        n = p + 1
+        flops = E ** 3 * (24 * n ** 4 + 15 * n ** 3)
+        print(json.dumps({
+            "sweep": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_tflops": flops / t64 / 1e9,
+            "apply_fp64_frac_of_fp64_peak": flops / t64 / 1e9 / FP64_PEAK_TFLOPS,
+            "apply_fp32_ms": t32, "apply_fp32_gdofs": N / t32 / 1e6,
+            "apply_fp32_hbm_gbs": (E ** 3 * 24 * n ** 3 + 8 * N) / t32 / 1e6,
+            "pcg_fp64_ms": s64, "pcg_fp64_iters": it64, "pcg_mixed_ms": s32, "pcg_mixed_iters": it32,
+            "mixed_speedup": s64 / s32, "mixed_final_rel_residual_fp64": res32,
+            "mixed_vs_fp64_solution_rel_diff": diff,
+            "setup_bytes_fp64": P64.device_bytes(), "setup_bytes_mixed": P32.device_bytes()}), flush=True)
+        P64.close()
+        P32.close()
+    return 0
+
+
 def run_profile_apply(args):
     """Small fixed launch sequence for ncu: build the workload's hierarchy, then two
     hmg_apply calls on each of the three finest levels (after the setup's Arnoldi applies)."""
@@ -322,7 +382,10 @@ def main():
     ap.add_argument("--hier", choices=["h", "p"], default="p")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
+    ap.add_argument("--sweep", action="store_true", help="order sweep at ~2M DOF, FP64 vs mixed precision")
     args = ap.parse_args()
+    if args.sweep:
+        return run_sweep(args)
     if args.profile_apply:
         return run_profile_apply(args)
     if args.impl == "reference":

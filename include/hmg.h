@@ -117,6 +117,10 @@ hmg_status hmg_rhs(hmg_problem* prob, const double* f_nodal_dev, double* b_dev, 
  * discussion; (A_k)_ij = a(phi_i, phi_j), Sec. 2.1), Dirichlet nodes masked. */
 hmg_status hmg_apply(hmg_problem* prob, int level, const double* x_dev, double* y_dev, void* stream);
 
+/* FP32 variant of hmg_apply (FP32 geometric factors and vectors, FP32 arithmetic): the
+ * operator of the mixed-precision V-cycle. Needs smooth_prec = HMG_PREC_FP32 at setup. */
+hmg_status hmg_apply_f32(hmg_problem* prob, int level, const float* x_dev, float* y_dev, void* stream);
+
 /* D^-1 of level k (inverse diagonal of A_k; 0 on boundary nodes), Sec. 3.2.1. */
 hmg_status hmg_diag_inv(hmg_problem* prob, int level, double* dinv_dev, void* stream);
 

@@ -678,6 +678,14 @@ hmg_status hmg_apply(hmg_problem* p, int level, const double* x, double* y, void
   return apply_level(p->impl, level, x, y, 1.0, s);
 }
 
+hmg_status hmg_apply_f32(hmg_problem* p, int level, const float* x, float* y, void* stream) {
+  if (!level_ok(p, level) || !x || !y) { set_error("null argument"); return HMG_EINVAL; }
+  if (!p->impl.L[level].G32) { set_error("the FP32 operator exists only for smooth_prec = HMG_PREC_FP32"); return HMG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  TRY(cudaMemsetAsync(y, 0, p->impl.L[level].m.N * sizeof(float), s));
+  return apply_level(p->impl, level, x, y, 1.0f, s);
+}
+
 hmg_status hmg_diag_inv(hmg_problem* p, int level, double* dinv, void* stream) {
   if (!level_ok(p, level) || !dinv) { set_error("null argument"); return HMG_EINVAL; }
   Level& l = p->impl.L[level];

@@ -1,4 +1,6 @@
 // Instantiation and launch of the operator-apply kernels (FP64 and FP32).
+#include <algorithm>
+
 #include "dispatch.cuh"
 #include "ops.cuh"
 
@@ -13,7 +15,10 @@ cudaError_t apply_dim(const Mesh& m, const Basis1D& b, const T* x, T* y, const T
     constexpr int N = decltype(nc)::value;
     constexpr int NP = Sh<DIM, N>::NP;
     const size_t per = (size_t)(1 + DIM) * NP * sizeof(T);
-    const int epb = epb_for(per);
+    // shared-memory cap, then small enough tiles for >= 4 blocks per SM on the 152 SMs
+    int epb = epb_for(per);
+    const long long want = std::max(1LL, m.nelem / (152LL * 4));
+    if (epb > want) epb = (int)want;
     const size_t smem = per * epb;
     auto kern = k_apply<DIM, N, T>;
     cudaError_t e = ensure_smem(kern, smem);

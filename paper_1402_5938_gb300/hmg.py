@@ -55,6 +55,7 @@ _SIGS = {
     "hmg_node_coords": (_I, [_P, _I, _V, _V]),
     "hmg_rhs": (_I, [_P, _V, _V, _V]),
     "hmg_apply": (_I, [_P, _I, _V, _V, _V]),
+    "hmg_apply_f32": (_I, [_P, _I, _V, _V, _V]),
     "hmg_diag_inv": (_I, [_P, _I, _V, _V]),
     "hmg_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "hmg_prolong": (_I, [_P, _I, _V, _V, _V]),
@@ -100,10 +101,10 @@ def _stream(stream):
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _ptr(t, n=None):
+def _ptr(t, n=None, dtype=None):
     import torch
-    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if not (t.is_cuda and t.dtype == (dtype or torch.float64) and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous {dtype or torch.float64} CUDA tensor")
     if n is not None and t.numel() < n:
         raise ValueError(f"tensor has {t.numel()} entries, the level needs {n}")
     return ctypes.c_void_p(t.data_ptr())
@@ -183,6 +184,12 @@ class Problem:
     def apply(self, level, x, y, stream=None):
         n = self.ndof(level)
         _check(lib().hmg_apply(self.h, level, _ptr(x, n), _ptr(y, n), _stream(stream)))
+
+    def apply_f32(self, level, x, y, stream=None):
+        import torch
+        n = self.ndof(level)
+        _check(lib().hmg_apply_f32(self.h, level, _ptr(x, n, torch.float32), _ptr(y, n, torch.float32),
+                                   _stream(stream)))
 
     def diag_inv(self, level, out, stream=None):
         _check(lib().hmg_diag_inv(self.h, level, _ptr(out, self.ndof(level)), _stream(stream)))
