@@ -353,21 +353,28 @@ def run_sweep(args):
 
 
 def run_profile_apply(args):
-    """Small fixed launch sequence for ncu: build the workload's hierarchy, then two
-    hmg_apply calls on each of the three finest levels (after the setup's Arnoldi applies)."""
+    """Small fixed launch sequence for ncu: build the hierarchy of the warped var-coef problem
+    (--mesh elements per axis, --order p, p-multigrid), then two applies on each of the three
+    finest levels (FP64 hmg_apply, or hmg_apply_f32 with --prec fp32) after setup's applies."""
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     import synth
     from paper_1402_5938_gb300 import Problem
-    P = Problem(workload(args.hier))
+    prob = synth.warped_var3d(args.mesh, args.order, hier=args.hier)
+    if args.prec == "fp32":
+        prob = dict(prob, smooth_prec="fp32")
+    P = Problem(prob)
     for lev in range(min(3, P.nlevels())):
         N = P.ndof(lev)
         x = torch.from_numpy(synth.uniform_pm1(7, N)).cuda()
         y = torch.zeros_like(x)
         for _ in range(2):
-            P.apply(lev, x, y)
+            if args.prec == "fp32":
+                P.apply_f32(lev, x.float(), y.float())
+            else:
+                P.apply(lev, x, y)
     torch.cuda.synchronize()
     P.close()
     print("profile-apply ok")
@@ -383,6 +390,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
     ap.add_argument("--sweep", action="store_true", help="order sweep at ~2M DOF, FP64 vs mixed precision")
+    ap.add_argument("--mesh", type=int, default=16, help="--profile-apply: elements per axis")
+    ap.add_argument("--order", type=int, default=4, help="--profile-apply: polynomial order")
+    ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="--profile-apply: precision")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)

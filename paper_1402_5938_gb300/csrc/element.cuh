@@ -11,6 +11,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace hmg {
 
@@ -71,6 +72,30 @@ __device__ __forceinline__ long long interior_index(const Mesh& m, long long g) 
   return (r - 1) * (m.Nn[0] - 2) + (I - 1);
 }
 
+// Per-element gather/scatter data computed once per element tile: the global node number of
+// local node (0,0,0) and six boundary-face bits (x0, x1, y0, y1, z0, z1).
+__device__ __forceinline__ void elem_base(const Mesh& m, long long e, long long* base, int* flags) {
+  const int ex = (int)(e % m.E[0]);
+  const long long r = e / m.E[0];
+  const int ey = (int)(r % m.E[1]);
+  const int ez = (int)(r / m.E[1]);
+  *base = ((long long)ez * m.p * m.Nn[1] + (long long)ey * m.p) * m.Nn[0] + (long long)ex * m.p;
+  int f = (ex == 0) | ((ex == m.E[0] - 1) << 1) | ((ey == 0) << 2) | ((ey == m.E[1] - 1) << 3);
+  if (m.dim == 3) f |= ((ez == 0) << 4) | ((ez == m.E[2] - 1) << 5);
+  *flags = f;
+}
+
+// Global node of local point a of an element with the given base/flags (32-bit local math).
+template <int DIM, int N>
+__device__ __forceinline__ long long local_node(int a, long long base, int f, long long nx, long long nxy,
+                                                bool& bd) {
+  const int i = a % N, j = (a / N) % N, k = DIM == 3 ? a / (N * N) : 0;
+  bd = ((i == 0) & (f & 1)) | ((i == N - 1) & ((f >> 1) & 1)) | ((j == 0) & ((f >> 2) & 1)) |
+       ((j == N - 1) & ((f >> 3) & 1));
+  if (DIM == 3) bd |= ((k == 0) & ((f >> 4) & 1)) | ((k == N - 1) & ((f >> 5) & 1));
+  return base + (long long)k * nxy + (long long)j * nx + i;
+}
+
 // dst (=, or += if ACC) table contraction of src along `dir` for the `ne` tiles of the block.
 //   TRN = false: out[i] = sum_m M[i*N+m] in[m]   (nodes -> Gauss points)
 //   TRN = true : out[i] = sum_m M[m*N+i] in[m]   (transpose, Gauss points -> nodes)
@@ -99,74 +124,158 @@ __device__ __forceinline__ void contract(const T* src, T* dst, const T* M, int d
 }
 
 // ---------------------------------------------------------------------------------------
-// y += alpha * A x on one level: gather, interpolate to Gauss points (B), collocated
-// reference gradient (D), pointwise G (mu w detJ J^-1 J^-T), transpose, scatter-add.
-// Boundary nodes read as 0 and are never written. G layout [E][NC][NP].
-// Shared memory: (1 + DIM) * epb * NP values of T.
+// FP32 apply, y += alpha * A x, for the mixed-precision V-cycle. Here the geometric factors
+// (24 q^d bytes per element) dominate the traffic and the arithmetic is cheap, so the
+// kernel streams them: persistent blocks walk over tiles of `epb` elements, and one thread
+// per block loads each tile's contiguous G slab into shared memory with a bulk TMA copy
+// (cp.async.bulk + mbarrier), NBUF = 2 buffers deep so the next tile's factors arrive
+// while the current tile is gathered and contracted. Contractions are line-based with
+// the line in registers and table entries as uniform parameter-space operands.
+// A bulk copy must start on 16 bytes: the slab is fetched from the 16-byte boundary below
+// it (G is allocated with tail padding) and read at that offset in shared memory.
+// Waits are bounded: on timeout the block records kErrTmaTimeout in *err, waits (bounded)
+// for its other copy in flight and returns.
 // ---------------------------------------------------------------------------------------
-template <int DIM, int N, typename T>
+constexpr int kErrTmaTimeout = 1;
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+template <int DIM, int N, int NBUF>
+struct Apply32Cfg {
+  static constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+  __host__ __device__ static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+  // bytes of one G buffer: the slab plus up to 16 bytes of alignment slack
+  __host__ __device__ static size_t gslot(int epb) { return al16((size_t)epb * NC * NP * 4 + 16); }
+  // shared-memory layout; every region starts on 16 bytes:
+  // [0,128): mbarriers + flag | G buffers | U | V (DIM tiles) | element bases (8 B) | face bits (4 B)
+  __host__ __device__ static size_t off_g() { return 128; }
+  __host__ __device__ static size_t off_u(int epb) { return off_g() + NBUF * gslot(epb); }
+  __host__ __device__ static size_t off_v(int epb) { return off_u(epb) + al16((size_t)epb * NP * 4); }
+  __host__ __device__ static size_t off_base(int epb) { return off_v(epb) + al16((size_t)DIM * epb * NP * 4); }
+  __host__ __device__ static size_t off_flag(int epb) { return off_base(epb) + al16((size_t)epb * 8); }
+  __host__ __device__ static size_t smem(int epb) { return off_flag(epb) + al16((size_t)epb * 4); }
+};
+
+template <int DIM, int N, int NBUF>
 __global__ void __launch_bounds__(256)
-k_apply(const T* __restrict__ x, T* __restrict__ y, const T* __restrict__ G, const Mesh m,
-        const __grid_constant__ Tab<N, T> tab, const T alpha, const int epb) {
-  constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* U = reinterpret_cast<T*>(smem_raw);
-  T* V = U + epb * NP;
-  const long long e0 = (long long)blockIdx.x * epb;
-  const int ne = (int)min((long long)epb, m.nelem - e0);
+k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ G, const Mesh m,
+          const __grid_constant__ Tab<N, float> tab, const float alpha, const int epb, const long long ntiles,
+          int* __restrict__ err) {
+  using C = Apply32Cfg<DIM, N, NBUF>;
+  constexpr int NP = C::NP, NC = C::NC;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  int* sflag = reinterpret_cast<int*>(smem_raw + 64);
+  const size_t gslot = C::gslot(epb);
+  unsigned char* gbuf = smem_raw + C::off_g();
+  float* U = reinterpret_cast<float*>(smem_raw + C::off_u(epb));
+  float* V = reinterpret_cast<float*>(smem_raw + C::off_v(epb));
+  long long* ebase = reinterpret_cast<long long*>(smem_raw + C::off_base(epb));
+  int* eflag = reinterpret_cast<int*>(smem_raw + C::off_flag(epb));
+  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
 
-  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
-    const int e = t / NP, a = t - e * NP;
-    bool bd;
-    const long long g = elem_node<DIM, N>(m, e0 + e, a, bd);
-    U[t] = bd ? T(0) : x[g];
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
+    mbar_init_fence();
   }
   __syncthreads();
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    contract<DIM, N, T, false, false>(U, U, tab.B, d, ne);
+
+  // byte offset of tile t's slab above the 16-byte boundary it is fetched from
+  auto slab = [&](long long t, const char** src, uint32_t* bytes) -> int {
+    const long long e0 = t * epb;
+    const long long ne = min((long long)epb, m.nelem - e0);
+    const char* p = reinterpret_cast<const char*>(G + e0 * NC * NP);
+    const int off = (int)(reinterpret_cast<uintptr_t>(p) & 15);
+    *src = p - off;
+    *bytes = (uint32_t)((ne * NC * NP * 4 + off + 15) & ~15LL);
+    return off;
+  };
+  auto issue = [&](long long t, int b) {
+    const char* src;
+    uint32_t bytes;
+    slab(t, &src, &bytes);
+    fence_proxy_async_smem();
+    bulk_g2s(gbuf + b * gslot, src, bytes, &bar[b]);
+  };
+
+  uint32_t phase[NBUF > 1 ? NBUF : 1] = {};
+  long long t = blockIdx.x;
+  if (threadIdx.x == 0 && t < ntiles) issue(t, 0);
+  for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
+    const int b = NBUF > 1 ? (k & 1) : 0;
+    const long long tn = t + gridDim.x;
+    if (NBUF > 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, b ^ 1);
+    const long long e0 = t * epb;
+    const int ne = (int)min((long long)epb, m.nelem - e0);
+    if (threadIdx.x < ne) elem_base(m, e0 + threadIdx.x, &ebase[threadIdx.x], &eflag[threadIdx.x]);
     __syncthreads();
-  }
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) contract<DIM, N, T, false, false>(U, V + d * epb * NP, tab.D, d, ne);
-  __syncthreads();
-
-  const T* Gb = G + e0 * NC * NP;
-  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
-    const int e = t / NP, q = t - e * NP;
-    const T* g = Gb + (long long)e * NC * NP + q;
-    if (DIM == 3) {
-      const T u0 = V[t], u1 = V[epb * NP + t], u2 = V[2 * epb * NP + t];
-      const T g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
-      V[t] = g00 * u0 + g01 * u1 + g02 * u2;
-      V[epb * NP + t] = g01 * u0 + g11 * u1 + g12 * u2;
-      V[2 * epb * NP + t] = g02 * u0 + g12 * u1 + g22 * u2;
-    } else {
-      const T u0 = V[t], u1 = V[epb * NP + t];
-      const T g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
-      V[t] = g00 * u0 + g01 * u1;
-      V[epb * NP + t] = g01 * u0 + g11 * u1;
+    for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
+      const int e = i / NP, a = i - e * NP;
+      bool bd;
+      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
+      U[i] = bd ? 0.0f : x[g];
     }
-  }
-  __syncthreads();
-  contract<DIM, N, T, true, false>(V, U, tab.D, 0, ne);
-  __syncthreads();
-  contract<DIM, N, T, true, true>(V + epb * NP, U, tab.D, 1, ne);
-  __syncthreads();
-  if (DIM == 3) {
-    contract<DIM, N, T, true, true>(V + 2 * epb * NP, U, tab.D, 2, ne);
     __syncthreads();
-  }
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    contract<DIM, N, T, true, false>(U, U, tab.B, d, ne);
+    for (int d = 0; d < DIM; ++d) {
+      contract<DIM, N, float, false, false>(U, U, tab.B, d, ne);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) contract<DIM, N, float, false, false>(U, V + d * epb * NP, tab.D, d, ne);
+    // this tile's factors: thread 0 polls with a limit, then everyone observes the phase
+    if (threadIdx.x == 0) *sflag = mbar_wait(&bar[b], phase[b], kWaitPolls) ? 0 : 1;
     __syncthreads();
-  }
-  for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
-    const int e = t / NP, a = t - e * NP;
-    bool bd;
-    const long long g = elem_node<DIM, N>(m, e0 + e, a, bd);
-    if (!bd) atomicAdd(y + g, alpha * U[t]);
+    if (*sflag) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, kErrTmaTimeout);
+        if (NBUF > 1 && tn < ntiles) mbar_wait(&bar[b ^ 1], phase[b ^ 1], kWaitPolls);
+      }
+      return;
+    }
+    mbar_wait(&bar[b], phase[b], kWaitPolls);
+    phase[b] ^= 1;
+    const char* src;
+    uint32_t bytes;
+    const int off = slab(t, &src, &bytes);
+    const float* Gt = reinterpret_cast<const float*>(gbuf + b * gslot + off);
+    for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
+      const int e = i / NP, q = i - e * NP;
+      const float* g = Gt + e * NC * NP + q;
+      if (DIM == 3) {
+        const float u0 = V[i], u1 = V[epb * NP + i], u2 = V[2 * epb * NP + i];
+        const float g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
+        V[i] = g00 * u0 + g01 * u1 + g02 * u2;
+        V[epb * NP + i] = g01 * u0 + g11 * u1 + g12 * u2;
+        V[2 * epb * NP + i] = g02 * u0 + g12 * u1 + g22 * u2;
+      } else {
+        const float u0 = V[i], u1 = V[epb * NP + i];
+        const float g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
+        V[i] = g00 * u0 + g01 * u1;
+        V[epb * NP + i] = g01 * u0 + g11 * u1;
+      }
+    }
+    __syncthreads();
+    if (NBUF == 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, 0);  // the single buffer is free
+    contract<DIM, N, float, true, false>(V, U, tab.D, 0, ne);
+    __syncthreads();
+    contract<DIM, N, float, true, true>(V + epb * NP, U, tab.D, 1, ne);
+    __syncthreads();
+    if (DIM == 3) {
+      contract<DIM, N, float, true, true>(V + 2 * epb * NP, U, tab.D, 2, ne);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      contract<DIM, N, float, true, false>(U, U, tab.B, d, ne);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
+      const int e = i / NP, a = i - e * NP;
+      bool bd;
+      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
+      if (!bd) atomicAdd(y + g, alpha * U[i]);
+    }
+    __syncthreads();
   }
 }
 

@@ -65,6 +65,7 @@ struct ProblemImpl {
   int device = 0;
   std::vector<Level> L;
   double* S = nullptr;        // device scalars
+  int* err = nullptr;         // device error flag written by bounded waits in kernels
   double* partial = nullptr;  // reduction partials
   double* hostS = nullptr;    // pinned host copy of a scalar
   void* t1 = nullptr;         // transfer intermediates
@@ -260,7 +261,7 @@ hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0) P.fine_applies++;
-  TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, s));
+  TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s));
   return HMG_OK;
 }
 
@@ -505,6 +506,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
     for (int a = 0; a < D.dim; ++a) { rd[a] = c.Nn[a]; max_tbuf = std::max(max_tbuf, (size_t)(rd[0] * rd[1] * rd[2])); }
   }
   TRY(P.alloc((void**)&P.S, 64 * sizeof(double)));
+  TRY(P.alloc((void**)&P.err, sizeof(int)));
   TRY(P.alloc((void**)&P.partial, kRedBlocks * sizeof(double)));
   TRY(cudaMallocHost((void**)&P.hostS, 16 * sizeof(double)));
   TRY(P.alloc(&P.t1, max_tbuf * sizeof(double)));
@@ -543,7 +545,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       TRY(dinv_from_diag(l.r, l.dinv, n, s));
       TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));
       if (mixed) {
-        TRY(P.alloc((void**)&l.G32, gsz * nc_of(D.dim) * sizeof(float)));
+        TRY(P.alloc((void**)&l.G32, gsz * nc_of(D.dim) * sizeof(float) + 256));  // TMA tail padding
         TRY(P.alloc((void**)&l.dinv32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.b32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.x32, n * sizeof(float)));
@@ -741,8 +743,34 @@ hmg_status hmg_vcycle(hmg_problem* p, const double* r, double* z, void* stream) 
   return precondition(P, P.pr, z, s);
 }
 
+static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit,
+                             int* iters, double* res_hist, void* stream);
+
+// Reads (and clears) the device error flag set by bounded waits inside kernels.
+static hmg_status device_error(ProblemImpl& P, cudaStream_t s) {
+  int h = 0;
+  TRY(cudaMemcpyAsync(&h, P.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (h != 0) {
+    TRY(cudaMemsetAsync(P.err, 0, sizeof(int), s));
+    set_error("a bounded wait inside a kernel gave up (error code " + std::to_string(h) + ")");
+    return HMG_ETIMEOUT;
+  }
+  return HMG_OK;
+}
+
 hmg_status hmg_solve(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit, int* iters,
                      double* res_hist, void* stream) {
+  hmg_status st = solve_impl(p, mode, b, u, rtol, maxit, iters, res_hist, stream);
+  if (p && (st == HMG_OK || st == HMG_ENOCONV || st == HMG_ENAN)) {
+    hmg_status de = device_error(p->impl, (cudaStream_t)stream);
+    if (de != HMG_OK) return de;
+  }
+  return st;
+}
+
+static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit,
+                             int* iters, double* res_hist, void* stream) {
   if (!level_ok(p, 0) || !b || !u || maxit < 0 || !(rtol >= 0.0)) { set_error("bad argument"); return HMG_EINVAL; }
   if (mode != HMG_MODE_MG && mode != HMG_MODE_PCG) { set_error("bad mode"); return HMG_EINVAL; }
   ProblemImpl& P = p->impl;

@@ -6,11 +6,13 @@
 
 namespace hmg {
 
-// y += alpha * A x (FP64 or FP32 data; G in the same precision).
+// y += alpha * A x (FP64 or FP32 data; G in the same precision). The FP32 kernel stages G
+// with bulk TMA copies and needs G allocated with >= 16 bytes of tail padding; a timed-out
+// wait sets *err (device int) to a nonzero code.
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, cudaStream_t s);
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
-                             const float* G, float alpha, cudaStream_t s);
+                             const float* G, float alpha, int* err, cudaStream_t s);
 
 // Geometry: stage buffer J [E][dim*(dim+1)][NP], then G [E][NC][NP] and wdetJ [E][NP].
 // *bad (device int) is set to 1 where det J <= 0.
@@ -26,7 +28,5 @@ cudaError_t launch_mass(const Mesh& m, const Basis1D& b, const double* f, double
 cudaError_t launch_elem_dense(const Mesh& m, const Basis1D& b, const double* G, double* A,
                               long long nI, cudaStream_t s);
 
-// Elements per block and dynamic shared memory of the apply kernel.
-int apply_epb(int dim, int n, size_t elem_bytes);
 
 }  // namespace hmg

@@ -1,5 +1,8 @@
 // Instantiation and launch of the operator-apply kernels (FP64 and FP32).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "dispatch.cuh"
 #include "ops.cuh"
@@ -8,24 +11,56 @@ namespace hmg {
 
 namespace {
 
-template <int DIM, typename T>
-cudaError_t apply_dim(const Mesh& m, const Basis1D& b, const T* x, T* y, const T* G, T alpha,
-                      cudaStream_t s) {
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// resident blocks per SM of (kernel, dynamic shared memory), queried once
+int blocks_per_sm(const void* kernel, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(kernel, threads, smem, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nb = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+  cache[key] = nb;
+  return nb;
+}
+
+template <int DIM>
+cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* y, const float* G, float alpha,
+                        int* err, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
-    constexpr int NP = Sh<DIM, N>::NP;
-    const size_t per = (size_t)(1 + DIM) * NP * sizeof(T);
-    // shared-memory cap, then small enough tiles for >= 4 blocks per SM on the 152 SMs
-    int epb = epb_for(per);
-    const long long want = std::max(1LL, m.nelem / (152LL * 4));
+    constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+    constexpr int NBUF = (DIM == 2 || NP <= 3200) ? 2 : 1;
+    using C = Apply32Cfg<DIM, N, NBUF>;
+    const size_t per = (size_t)(NBUF * NC + 1 + DIM) * NP * 4;
+    int epb = (int)std::max<size_t>(1, (64 * 1024) / per);
+    const long long want = std::max(1LL, m.nelem / (2LL * sm_count()));
     if (epb > want) epb = (int)want;
-    const size_t smem = per * epb;
-    auto kern = k_apply<DIM, N, T>;
+    if (epb > 64) epb = 64;
+    const size_t smem = C::smem(epb);
+    auto kern = k_apply32<DIM, N, NBUF>;
     cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    const long long blocks = (m.nelem + epb - 1) / epb;
-    if (blocks == 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, 256, smem, s>>>(x, y, G, m, make_tab<N, T>(b), alpha, epb);
+    const long long ntiles = (m.nelem + epb - 1) / epb;
+    if (ntiles == 0) return cudaSuccess;
+    const long long grid = std::min<long long>(ntiles, (long long)sm_count() * blocks_per_sm((const void*)kern, 256, smem));
+    kern<<<(unsigned)grid, 256, smem, s>>>(x, y, G, m, make_tab<N, float>(b), alpha, epb, ntiles, err);
     return counted(cudaGetLastError());
   });
 }
@@ -54,9 +89,8 @@ cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, d
 }
 
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
-                             const float* G, float alpha, cudaStream_t s) {
-  return m.dim == 3 ? apply_dim<3, float>(m, b, x, y, G, alpha, s)
-                    : apply_dim<2, float>(m, b, x, y, G, alpha, s);
+                             const float* G, float alpha, int* err, cudaStream_t s) {
+  return m.dim == 3 ? apply32_dim<3>(m, b, x, y, G, alpha, err, s) : apply32_dim<2>(m, b, x, y, G, alpha, err, s);
 }
 
 }  // namespace hmg
