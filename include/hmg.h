@@ -67,6 +67,9 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1 } hmg_prec;
  *                        0 selects 0x1402593800000000.
  *   smooth_prec        : HMG_PREC_FP64, or HMG_PREC_FP32 for the V-cycle's smoother, residual and
  *                        transfer work below the FP64 fine residual / PCG / coarsest solve.
+ *   solve_graph        : 1 (default): hmg_solve runs each solve as one instantiated CUDA graph with
+ *                        a device-side loop (no host round trip per iteration); 0: host-driven loop
+ *                        that reads the residual norm back every iteration. Same results.
  */
 typedef struct hmg_desc {
   int dim;
@@ -84,6 +87,7 @@ typedef struct hmg_desc {
   double cheb_safety;
   unsigned long long arnoldi_seed;
   int smooth_prec;
+  int solve_graph;
 } hmg_desc;
 
 typedef struct hmg_problem hmg_problem;
@@ -167,6 +171,16 @@ hmg_status hmg_vcycle(hmg_problem* prob, const double* r_dev, double* z_dev, voi
  * maxit is reached, HMG_ENAN on a non-finite residual. Synchronizes `stream`. */
 hmg_status hmg_solve(hmg_problem* prob, int mode, const double* b_dev, double* u_dev, double rtol,
                      int maxit, int* iters, double* res_hist, void* stream);
+
+/* n independent solves (different meshes, orders and coefficients allowed) as one call: every
+ * problem's solve is the same device-side graph as hmg_solve's, launched concurrently on a pool
+ * of streams forked from and joined back to `stream`, which is synchronized on return.
+ * b[i], u[i]: problem i's vectors; iters[i], res_hist[i] (host, >= maxit+1 doubles) and
+ * status[i] may be NULL. Returns HMG_OK if every solve converged, else the first failing
+ * status. A handle may appear only once per call. (Batched form of Sec. 4.3 / Algorithm 1.) */
+hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const double* const* b_dev,
+                             double* const* u_dev, double rtol, int maxit, int* iters, double* const* res_hist,
+                             int* status, void* stream);
 
 /* Number of finest-level operator applies issued since setup (cost-model accounting,
  * Sec. 4.2/4.3: 7 per V(3,3) cycle). */

@@ -74,6 +74,19 @@ struct ProblemImpl {
   std::vector<void*> dev_allocs;
   size_t bytes = 0;
   long long fine_applies = 0;
+  // graph solves: one instantiated graph per mode (MG, PCG) with a device-side WHILE loop
+  double* gb = nullptr;       // masked right-hand side
+  double* gu = nullptr;       // solution
+  int* ctrl = nullptr;        // iteration, status, maxit, history capacity
+  double* hist = nullptr;     // residual history (capacity hist_cap + 1)
+  int hist_cap = 0;
+  int* host_ctrl = nullptr;   // pinned
+  double* host_hist = nullptr;  // pinned
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  long long gkern[2][3] = {};  // kernel nodes per graph section: prologue, loop body (part 1), PCG part 2
+  bool capturing = false;
 
   cudaError_t alloc(void** p, size_t nbytes) {
     *p = nullptr;
@@ -85,8 +98,16 @@ struct ProblemImpl {
     return cudaMemset(*p, 0, nbytes);
   }
   ~ProblemImpl() {
+    for (int m = 0; m < 2; ++m) {
+      if (gexec[m]) cudaGraphExecDestroy(gexec[m]);
+      if (graph[m]) cudaGraphDestroy(graph[m]);
+    }
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : dev_allocs) cudaFree(p);
+    if (hist) cudaFree(hist);
     if (hostS) cudaFreeHost(hostS);
+    if (host_ctrl) cudaFreeHost(host_ctrl);
+    if (host_hist) cudaFreeHost(host_hist);
   }
 };
 
@@ -254,13 +275,13 @@ template <> struct Acc<float> {
 
 hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double alpha, cudaStream_t s) {
   Level& l = P.L[k];
-  if (k == 0) P.fine_applies++;
+  if (k == 0 && !P.capturing) P.fine_applies++;
   TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, s));
   return HMG_OK;
 }
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
   Level& l = P.L[k];
-  if (k == 0) P.fine_applies++;
+  if (k == 0 && !P.capturing) P.fine_applies++;
   TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s));
   return HMG_OK;
 }
@@ -516,6 +537,10 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   TRY(P.alloc((void**)&P.pz, N0 * sizeof(double)));
   TRY(P.alloc((void**)&P.pp, N0 * sizeof(double)));
   TRY(P.alloc((void**)&P.ph, N0 * sizeof(double)));
+  TRY(P.alloc((void**)&P.gb, N0 * sizeof(double)));
+  TRY(P.alloc((void**)&P.gu, N0 * sizeof(double)));
+  TRY(P.alloc((void**)&P.ctrl, 4 * sizeof(int)));
+  TRY(cudaMallocHost((void**)&P.host_ctrl, 4 * sizeof(int)));
 
   double* Jstage = nullptr;
   int* bad = nullptr;
@@ -568,6 +593,179 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   return st;
 }
 
+// ---- graph solves -----------------------------------------------------------------------
+
+// finest-level applies of one V-cycle from a zero guess (the first pre-smoothing step needs none)
+long long vcycle_fine_applies(const ProblemImpl& P) {
+  if (P.L.size() < 2) return 0;
+  const hmg_desc& D = P.desc;
+  return (D.nu_pre >= 1 ? D.nu_pre - 1 : 0) + 1 + D.nu_post;
+}
+
+// Capture the work `fn` enqueues on s into graph g (appended after nothing: g is empty or a
+// body graph); *leaves receives the capture's final dependency set.
+template <typename F>
+hmg_status capture_into(cudaGraph_t g, cudaStream_t s, F&& fn, std::vector<cudaGraphNode_t>* leaves) {
+  TRY(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  hmg_status st = fn();
+  if (st == HMG_OK && leaves) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &d, nullptr, &nd);
+    if (e == cudaSuccess) leaves->assign(d, d + nd);
+    else st = HMG_EDEVICE;
+  }
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &out);
+  if (st != HMG_OK) return st;
+  TRY(e);
+  return HMG_OK;
+}
+
+hmg_status add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
+                           cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  TRY(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &prm));
+  *body = prm.conditional.phGraph_out[0];
+  return HMG_OK;
+}
+
+// One solve of mode `mode` as a graph: prologue, then WHILE(hw){ iteration }. For PCG the
+// iteration is [A p, alpha, u, r, ||r||, check] then IF(hi){ z = V(r), beta, p }, so the last
+// iteration stops right after the convergence test (Algorithm 1's order).
+hmg_status build_graph(ProblemImpl& P, int mode, int cap) {
+  if (P.gexec[mode] && P.hist_cap >= cap) return HMG_OK;
+  if (P.hist_cap < cap) {
+    for (int m = 0; m < 2; ++m) {  // both graphs point at the history array
+      if (P.gexec[m]) { cudaGraphExecDestroy(P.gexec[m]); P.gexec[m] = nullptr; }
+      if (P.graph[m]) { cudaGraphDestroy(P.graph[m]); P.graph[m] = nullptr; }
+    }
+    if (P.hist) { TRY(cudaFree(P.hist)); P.hist = nullptr; }
+    if (P.host_hist) { TRY(cudaFreeHost(P.host_hist)); P.host_hist = nullptr; }
+    TRY(cudaMalloc((void**)&P.hist, (cap + 1) * sizeof(double)));
+    TRY(cudaMallocHost((void**)&P.host_hist, (cap + 1) * sizeof(double)));
+    P.hist_cap = cap;
+  }
+  if (!P.cap_stream) TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = P.cap_stream;
+  const long long n = P.L[0].m.N;
+  cudaGraph_t g = nullptr;
+  TRY(cudaGraphCreate(&g, 0));
+  P.capturing = true;
+  hmg_status st = [&]() -> hmg_status {
+    cudaGraphConditionalHandle hw;
+    TRY(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+    std::vector<cudaGraphNode_t> leaves;
+    double* r = P.pr;
+    double* z = P.pz;
+    long long c0 = add_launches(0);
+    CHECK(capture_into(g, s, [&]() -> hmg_status {
+      TRY(cudaMemcpyAsync(r, P.gb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      TRY(cudaMemsetAsync(P.gu, 0, n * sizeof(double), s));
+      CHECK(dot_to(P, r, r, n, FIN_STORE, S_RR0, 0, false, s));
+      TRY(start_check(P.S, P.ctrl, P.hist, hw, s));
+      if (mode == HMG_MODE_PCG) {
+        CHECK(precondition(P, r, z, s));
+        TRY(cudaMemcpyAsync(P.pp, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CHECK(dot_to(P, z, r, n, FIN_STORE, S_RHO, 0, false, s));
+      }
+      return HMG_OK;
+    }, &leaves));
+    P.gkern[mode][0] = add_launches(0) - c0;
+    c0 = add_launches(0);
+    cudaGraph_t body;
+    CHECK(add_conditional(g, leaves, hw, cudaGraphCondTypeWhile, &body));
+    if (mode == HMG_MODE_MG) {
+      CHECK(capture_into(body, s, [&]() -> hmg_status {
+        CHECK(precondition(P, r, z, s));
+        TRY(axpy(P.gu, z, n, 1.0, s));
+        TRY(cudaMemcpyAsync(r, P.gb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CHECK(apply_level(P, 0, P.gu, r, -1.0, s));
+        CHECK(dot_to(P, r, r, n, FIN_STORE, S_RR, 0, false, s));
+        TRY(step_check(P.S, P.ctrl, P.hist, hw, hw, 0, s));
+        return HMG_OK;
+      }, nullptr));
+      P.gkern[mode][1] = add_launches(0) - c0;
+    } else {
+      cudaGraphConditionalHandle hi;
+      TRY(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
+      std::vector<cudaGraphNode_t> l1;
+      CHECK(capture_into(body, s, [&]() -> hmg_status {
+        TRY(cudaMemsetAsync(P.ph, 0, n * sizeof(double), s));
+        CHECK(apply_level(P, 0, P.pp, P.ph, 1.0, s));
+        CHECK(dot_to(P, P.pp, P.ph, n, FIN_STORE, S_PH, 0, false, s));
+        TRY(pcg_update(P.gu, r, P.pp, P.ph, n, P.S, P.partial, s));
+        TRY(finish(P.partial, P.S, FIN_STORE, S_RR, 0, nullptr, s));
+        TRY(step_check(P.S, P.ctrl, P.hist, hw, hi, 1, s));
+        return HMG_OK;
+      }, &l1));
+      P.gkern[mode][1] = add_launches(0) - c0;
+      c0 = add_launches(0);
+      cudaGraph_t rest;
+      CHECK(add_conditional(body, l1, hi, cudaGraphCondTypeIf, &rest));
+      CHECK(capture_into(rest, s, [&]() -> hmg_status {
+        CHECK(precondition(P, r, z, s));
+        CHECK(dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s));
+        TRY(pcg_direction(P.pp, z, n, P.S, s));
+        return HMG_OK;
+      }, nullptr));
+      P.gkern[mode][2] = add_launches(0) - c0;
+    }
+    // capture launched nothing: take the captured kernels back out of the launch count
+    add_launches(-(P.gkern[mode][0] + P.gkern[mode][1] + P.gkern[mode][2]));
+    cudaGraphExec_t ex = nullptr;
+    TRY(cudaGraphInstantiate(&ex, g, 0));
+    P.graph[mode] = g;
+    P.gexec[mode] = ex;
+    return HMG_OK;
+  }();
+  P.capturing = false;
+  if (st != HMG_OK) cudaGraphDestroy(g);
+  return st;
+}
+
+// Enqueue one graph solve on s (no host synchronization); results land in pinned buffers.
+hmg_status graph_solve_enqueue(ProblemImpl& P, int mode, const double* b, double* u, double rtol, int maxit,
+                               cudaStream_t s) {
+  const int cap = std::max(maxit, 64);
+  CHECK(build_graph(P, mode, cap));
+  const long long n = P.L[0].m.N;
+  TRY(copy_masked(P.gb, b, P.L[0].m, s));
+  TRY(set_solve_params(P.S, P.ctrl, rtol, maxit, P.hist_cap, s));
+  TRY(cudaGraphLaunch(P.gexec[mode], s));
+  TRY(cudaMemcpyAsync(u, P.gu, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TRY(cudaMemcpyAsync(P.host_ctrl, P.ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(P.host_hist, P.hist, (maxit + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return HMG_OK;
+}
+
+// After the stream has completed: iteration count, history and status of a graph solve.
+hmg_status graph_solve_finish(ProblemImpl& P, int mode, int* iters, double* res_hist) {
+  const int it = P.host_ctrl[0];
+  const int status = P.host_ctrl[1];
+  if (iters) *iters = it;
+  if (res_hist)
+    for (int i = 0; i <= it && i <= P.hist_cap; ++i) res_hist[i] = P.host_hist[i];
+  // kernels the graph executed: prologue, `it` loop bodies, and (PCG) it-1 second halves
+  add_launches(P.gkern[mode][0] + (long long)it * P.gkern[mode][1] +
+               (it > 0 ? (long long)(it - 1) * P.gkern[mode][2] : 0));
+  const long long v = vcycle_fine_applies(P);
+  if (it > 0) P.fine_applies += mode == HMG_MODE_MG ? (long long)it * (v + 1) : v + it + (long long)(it - 1) * v;
+  else if (mode == HMG_MODE_PCG && status != ST_NAN) P.fine_applies += v;
+  switch (status) {
+    case ST_CONVERGED: return HMG_OK;
+    case ST_MAXIT: set_error("maximum number of iterations reached"); return HMG_ENOCONV;
+    case ST_NAN: set_error("non-finite residual"); return HMG_ENAN;
+    default: set_error("graph solve ended in an unexpected state"); return HMG_EDEVICE;
+  }
+}
+
 bool level_ok(const hmg_problem* p, int level) {
   if (!p || level < 0 || level >= (int)p->impl.L.size()) {
     set_error("invalid problem handle or level");
@@ -603,6 +801,7 @@ hmg_status hmg_desc_default(hmg_desc* d) {
   d->cheb_safety = 1.0;
   d->arnoldi_seed = 0;
   d->smooth_prec = HMG_PREC_FP64;
+  d->solve_graph = 1;
   return HMG_OK;
 }
 
@@ -761,7 +960,19 @@ static hmg_status device_error(ProblemImpl& P, cudaStream_t s) {
 
 hmg_status hmg_solve(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit, int* iters,
                      double* res_hist, void* stream) {
-  hmg_status st = solve_impl(p, mode, b, u, rtol, maxit, iters, res_hist, stream);
+  hmg_status st;
+  if (p && p->impl.desc.solve_graph && (mode == HMG_MODE_MG || mode == HMG_MODE_PCG) && b && u && maxit >= 0 &&
+      rtol >= 0.0) {
+    cudaStream_t s = (cudaStream_t)stream;
+    st = graph_solve_enqueue(p->impl, mode, b, u, rtol, maxit, s);
+    if (st == HMG_OK) {
+      cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) { set_error(std::string("graph solve: ") + cudaGetErrorString(e)); return HMG_EDEVICE; }
+      st = graph_solve_finish(p->impl, mode, iters, res_hist);
+    }
+  } else {
+    st = solve_impl(p, mode, b, u, rtol, maxit, iters, res_hist, stream);
+  }
   if (p && (st == HMG_OK || st == HMG_ENOCONV || st == HMG_ENAN)) {
     hmg_status de = device_error(p->impl, (cudaStream_t)stream);
     if (de != HMG_OK) return de;
@@ -832,6 +1043,63 @@ static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* 
   }
   set_error("maximum number of PCG iterations reached");
   return HMG_ENOCONV;
+}
+
+hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const double* const* b,
+                             double* const* u, double rtol, int maxit, int* iters, double* const* res_hist,
+                             int* status, void* stream) {
+  if (!probs || n < 0 || !b || !u || maxit < 0 || !(rtol >= 0.0) || (mode != HMG_MODE_MG && mode != HMG_MODE_PCG)) {
+    set_error("bad argument");
+    return HMG_EINVAL;
+  }
+  if (n == 0) return HMG_OK;
+  for (int i = 0; i < n; ++i) {
+    if (!level_ok(probs[i], 0) || !b[i] || !u[i]) { set_error("bad problem handle or vector in the batch"); return HMG_EINVAL; }
+    for (int j = 0; j < i; ++j)
+      if (probs[j] == probs[i]) { set_error("a handle appears twice in the batch"); return HMG_EINVAL; }
+  }
+  const int cap = std::max(maxit, 64);
+  for (int i = 0; i < n; ++i) CHECK(build_graph(probs[i]->impl, mode, cap));
+  // fan out over a pool of streams, join back on the caller's stream
+  static std::mutex pool_mu;
+  static std::vector<cudaStream_t> pool[64];
+  int dev = 0;
+  TRY(cudaGetDevice(&dev));
+  const int K = 16;
+  {
+    std::lock_guard<std::mutex> lk(pool_mu);
+    if (dev >= 0 && dev < 64 && pool[dev].empty())
+      for (int k = 0; k < K; ++k) {
+        cudaStream_t sk;
+        TRY(cudaStreamCreateWithFlags(&sk, cudaStreamNonBlocking));
+        pool[dev].push_back(sk);
+      }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<cudaEvent_t> ev(K + 1, nullptr);
+  for (auto& e : ev) TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  hmg_status st = [&]() -> hmg_status {
+    TRY(cudaEventRecord(ev[K], s));
+    const int used = std::min(n, K);
+    for (int k = 0; k < used; ++k) TRY(cudaStreamWaitEvent(pool[dev][k], ev[K], 0));
+    for (int i = 0; i < n; ++i) CHECK(graph_solve_enqueue(probs[i]->impl, mode, b[i], u[i], rtol, maxit, pool[dev][i % K]));
+    for (int k = 0; k < used; ++k) {
+      TRY(cudaEventRecord(ev[k], pool[dev][k]));
+      TRY(cudaStreamWaitEvent(s, ev[k], 0));
+    }
+    TRY(cudaStreamSynchronize(s));
+    return HMG_OK;
+  }();
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != HMG_OK) return st;
+  hmg_status first = HMG_OK;
+  for (int i = 0; i < n; ++i) {
+    hmg_status si = graph_solve_finish(probs[i]->impl, mode, iters ? &iters[i] : nullptr, res_hist ? res_hist[i] : nullptr);
+    if (si == HMG_OK) si = device_error(probs[i]->impl, s);
+    if (status) status[i] = si;
+    if (first == HMG_OK && si != HMG_OK) first = si;
+  }
+  return first;
 }
 
 long long hmg_fine_applies(const hmg_problem* p) { return p ? p->impl.fine_applies : 0; }

@@ -199,6 +199,39 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, lon
     y[i] = fma(a, x[i], y[i]);
 }
 
+__global__ void k_set_params(double* S, int* ctrl, double rtol, int maxit, int cap) {
+  S[S_RTOL] = rtol;
+  ctrl[0] = 0;
+  ctrl[1] = ST_RUNNING;
+  ctrl[2] = maxit;
+  ctrl[3] = cap;
+}
+
+__global__ void k_start_check(const double* S, int* ctrl, double* hist, cudaGraphConditionalHandle hw) {
+  const double r0 = sqrt(S[S_RR0]);
+  hist[0] = r0;
+  int cont = 0;
+  if (!isfinite(r0)) ctrl[1] = ST_NAN;
+  else if (r0 == 0.0) ctrl[1] = ST_CONVERGED;
+  else if (ctrl[2] <= 0) ctrl[1] = ST_MAXIT;
+  else cont = 1;
+  cudaGraphSetConditional(hw, cont);
+}
+
+__global__ void k_step_check(const double* S, int* ctrl, double* hist, cudaGraphConditionalHandle hw,
+                             cudaGraphConditionalHandle hi, int has_if) {
+  const int it = ++ctrl[0];
+  const double r = sqrt(S[S_RR]);
+  if (it <= ctrl[3]) hist[it] = r;
+  int cont = 0;
+  if (!isfinite(r)) ctrl[1] = ST_NAN;
+  else if (r <= S[S_RTOL] * sqrt(S[S_RR0])) ctrl[1] = ST_CONVERGED;
+  else if (it >= ctrl[2]) ctrl[1] = ST_MAXIT;
+  else cont = 1;
+  cudaGraphSetConditional(hw, cont);
+  if (has_if) cudaGraphSetConditional(hi, cont);
+}
+
 struct Gll {
   double r[kMaxN];
 };
@@ -398,6 +431,19 @@ cudaError_t div_dev(double* y, const double* x, long long n, const double* den, 
 }
 cudaError_t copy_scalar(double* dst, const double* src, cudaStream_t s) {
   k_copy_scalar<<<1, 1, 0, s>>>(dst, src);
+  return counted(cudaGetLastError());
+}
+cudaError_t set_solve_params(double* S, int* ctrl, double rtol, int maxit, int cap, cudaStream_t s) {
+  k_set_params<<<1, 1, 0, s>>>(S, ctrl, rtol, maxit, cap);
+  return counted(cudaGetLastError());
+}
+cudaError_t start_check(const double* S, int* ctrl, double* hist, cudaGraphConditionalHandle hw, cudaStream_t s) {
+  k_start_check<<<1, 1, 0, s>>>(S, ctrl, hist, hw);
+  return counted(cudaGetLastError());
+}
+cudaError_t step_check(const double* S, int* ctrl, double* hist, cudaGraphConditionalHandle hw,
+                       cudaGraphConditionalHandle hi, int has_if, cudaStream_t s) {
+  k_step_check<<<1, 1, 0, s>>>(S, ctrl, hist, hw, hi, has_if);
   return counted(cudaGetLastError());
 }
 cudaError_t axpy(double* y, const double* x, long long n, double a, cudaStream_t s) {

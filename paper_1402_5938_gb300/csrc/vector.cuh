@@ -14,8 +14,13 @@ enum Scalar : int {
   S_BETA = 3,   // PCG beta
   S_TMP = 4,    // scratch scalar (Arnoldi h_ij, norms)
   S_RR0 = 5,    // ||r_0||^2
+  S_RTOL = 6,   // relative tolerance of a graph solve
   S_COUNT = 8
 };
+
+// Device-side solve control of a graph solve: ctrl[0] iteration, ctrl[1] status, ctrl[2] maxit,
+// ctrl[3] capacity of the residual-history array.
+enum SolveStatus : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_NAN = 3 };
 
 enum FinishOp : int { FIN_STORE = 0, FIN_SQRT = 1, FIN_RHO_BETA = 2 };
 
@@ -84,5 +89,12 @@ cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const l
                          long long nI, cudaStream_t s);
 cudaError_t coarse_solve_f32(const double* Ainv, const float* b, float* x, const long long* gmap,
                              long long nI, cudaStream_t s);
+
+// graph-solve control kernels (single thread): parameters, start check, per-iteration check.
+// The checks set the WHILE condition `hw` (and the IF condition `hi` if has_if) to "continue".
+cudaError_t set_solve_params(double* S, int* ctrl, double rtol, int maxit, int cap, cudaStream_t s);
+cudaError_t start_check(const double* S, int* ctrl, double* hist, cudaGraphConditionalHandle hw, cudaStream_t s);
+cudaError_t step_check(const double* S, int* ctrl, double* hist, cudaGraphConditionalHandle hw,
+                       cudaGraphConditionalHandle hi, int has_if, cudaStream_t s);
 
 }  // namespace hmg

@@ -35,7 +35,7 @@ class Desc(ctypes.Structure):
         ("smoother", ctypes.c_int), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
         ("omega", ctypes.c_double), ("arnoldi_iters", ctypes.c_int),
         ("cheb_lo_frac", ctypes.c_double), ("cheb_safety", ctypes.c_double),
-        ("arnoldi_seed", ctypes.c_ulonglong), ("smooth_prec", ctypes.c_int),
+        ("arnoldi_seed", ctypes.c_ulonglong), ("smooth_prec", ctypes.c_int), ("solve_graph", ctypes.c_int),
     ]
 
 
@@ -64,6 +64,8 @@ _SIGS = {
     "hmg_vcycle": (_I, [_P, _V, _V, _V]),
     "hmg_solve": (_I, [_P, _I, _V, _V, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _V]),
     "hmg_restrict_noalloc": (_I, [_I, ctypes.POINTER(ctypes.c_int), _I, _I, _I, _V, _V, _V]),
+    "hmg_solve_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_V), ctypes.POINTER(_V), _D, _I,
+                               ctypes.POINTER(_I), ctypes.POINTER(ctypes.POINTER(_D)), ctypes.POINTER(_I), _V]),
     "hmg_fine_applies": (ctypes.c_longlong, [_P]),
     "hmg_launch_count": (ctypes.c_longlong, []),
     "hmg_status_string": (ctypes.c_char_p, [_I]),
@@ -130,6 +132,7 @@ def make_desc(prob: dict) -> Desc:
     d.cheb_safety = prob.get("cheb_safety", 1.0)
     d.arnoldi_seed = prob.get("arnoldi_seed", 0)
     d.smooth_prec = PREC[prob.get("smooth_prec", "fp64")]
+    d.solve_graph = int(prob.get("solve_graph", 1))
     return d
 
 
@@ -226,6 +229,22 @@ class Problem:
         if st not in (HMG_OK, HMG_ENOCONV) or (raise_on_noconv and st != HMG_OK):
             _check(st)
         return st, it.value, np.array(hist[: it.value + 1])
+
+
+def solve_batched(problems, mode, bs, us, rtol=1e-8, maxit=1000, stream=None):
+    """hmg_solve_batched: returns (statuses, iterations, histories) for the n problems."""
+    n = len(problems)
+    H = (_P * n)(*[p.h for p in problems])
+    B = (_V * n)(*[_ptr(b, p.ndof(0)) for p, b in zip(problems, bs)])
+    U = (_V * n)(*[_ptr(u, p.ndof(0)) for p, u in zip(problems, us)])
+    its = (_I * n)()
+    sts = (_I * n)()
+    hists = [(_D * (maxit + 1))() for _ in range(n)]
+    HP = (ctypes.POINTER(_D) * n)(*[ctypes.cast(h, ctypes.POINTER(_D)) for h in hists])
+    st = lib().hmg_solve_batched(H, n, MODE[mode], B, U, float(rtol), int(maxit), its, HP, sts, _stream(stream))
+    if st not in (HMG_OK, HMG_ENOCONV):
+        _check(st)
+    return list(sts), list(its), [np.array(h[: its[i] + 1]) for i, h in enumerate(hists)]
 
 
 def restrict_noalloc(dim, nelem_fine, order_fine, order_coarse, halve_mesh, rf, rc, stream=None):

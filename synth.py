@@ -79,3 +79,19 @@ def warped_var3d(nelem=16, order=4, hier="h", **kw):
 # Seeds of the nodal right-hand sides for the 3D workloads.
 SEED_WARPED_VAR3D = 2
 SEED_PSWEEP3D = 3
+
+
+def batched_problem(i, base_seed=4_000_000):
+    """Solve i of the batched workload (parameters drawn from SplitMix64 with seed base+i):
+    3D warped cube, elements per axis E in 2..12, order p in {2,4,6,8}, coefficient contrast
+    10^k with k in 0..4: mu = 1 + (10^k - 1)/3 sum_i cos^2(2 pi x_i) (max/min = 10^k), p-multigrid
+    down to p = 1 on the same mesh (whose dense coarsest system then has at most 11^3 unknowns),
+    V(3,3) Chebyshev, FP32 V-cycle inside FP64 PCG. Returns (problem, rhs seed)."""
+    z = splitmix64(base_seed + i, 3)
+    E = 2 + int(z[0] % np.uint64(11))
+    p = (2, 4, 6, 8)[int(z[1] % np.uint64(4))]
+    k = int(z[2] % np.uint64(5))
+    prob = problem(3, E, p, warp_amp=0.1, mu_a=1.0, mu_b=(10.0 ** k - 1.0) / 3.0, mu_k=2.0, hier="p",
+                   n_hlevels=1, smoother="cheb", nu_pre=3, nu_post=3)
+    prob["smooth_prec"] = "fp32"
+    return prob, base_seed + i

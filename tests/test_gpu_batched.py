@@ -1,0 +1,108 @@
+"""Device-side graph solves and batched solves.
+
+* The graph solve (one CUDA graph per solve with a device-side WHILE loop) gives the same
+  iteration counts and residual histories as the host-driven loop.
+* hmg_solve_batched on uneven problems (batched-workload recipe: E in 2..12, p in {2,4,6,8},
+  contrast 10^k, FP32 V-cycle in FP64 PCG) gives, for every problem, the same result as
+  solving it alone: same iteration count, solutions equal to 1e-8 relative (the two runs
+  differ only in the rounding order of the atomic scatter, which the FP32 V-cycle shows)."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def hmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1402_5938_gb300 as pkg
+    return pkg
+
+
+CASES = [
+    (synth.warped_var3d(4, 4, hier="h"), "pcg"),
+    (synth.warped_var3d(4, 4, hier="p"), "mg"),
+    (dict(synth.warped_var3d(4, 4, hier="p"), smooth_prec="fp32"), "pcg"),
+    (synth.mms2d_poisson(8, 4), "mg"),
+]
+
+
+@pytest.mark.parametrize("prob,mode", CASES, ids=lambda c: str(c)[:50])
+def test_graph_solve_equals_host_loop(hmg, prob, mode):
+    Pg = hmg.Problem(dict(prob, solve_graph=1))
+    Ph = hmg.Problem(dict(prob, solve_graph=0))
+    N = Pg.ndof(0)
+    f = torch.from_numpy(synth.nodal_field(9, N)).to(DEV)
+    b = torch.zeros(N, dtype=torch.float64, device=DEV)
+    Pg.rhs(f, b)
+    ug, uh = torch.zeros_like(b), torch.zeros_like(b)
+    a0g, a0h = Pg.fine_applies(), Ph.fine_applies()
+    for rep in range(2):                                   # second call replays the same graph
+        stg, itg, hg = Pg.solve(mode, b, ug, rtol=1e-8, maxit=200)
+    sth, ith, hh = Ph.solve(mode, b, uh, rtol=1e-8, maxit=200)
+    assert stg == 0 and sth == 0 and itg == ith
+    # FP64: runs differ only in the FP64 atomic-scatter rounding order; with an FP32 V-cycle the
+    # preconditioner's own FP32 rounding order (unit roundoff 6e-8) shows in the history
+    fp32 = prob.get("smooth_prec") == "fp32"
+    sel = hh > 1e-6 * hh[0]                  # below that the scatter rounding order dominates
+    assert np.allclose(hg[sel], hh[sel], rtol=1e-5 if fp32 else 1e-9, atol=0)
+    assert float(torch.linalg.norm(ug - uh) / torch.linalg.norm(uh)) < (1e-8 if fp32 else 1e-10)
+    assert (Pg.fine_applies() - a0g) == 2 * (Ph.fine_applies() - a0h)
+    # maxit reached: status and history still written
+    st, it, h = Pg.solve(mode, b, ug, rtol=1e-14, maxit=2)
+    assert st == hmg.hmg.HMG_ENOCONV and it == 2 and len(h) == 3
+    # zero right-hand side: converged at iteration 0
+    st, it, h = Pg.solve(mode, torch.zeros_like(b), ug, rtol=1e-8, maxit=10)
+    assert st == 0 and it == 0 and float(torch.linalg.norm(ug)) == 0.0
+    Pg.close()
+    Ph.close()
+
+
+def test_batched_equals_alone(hmg):
+    probs, bs, us = [], [], []
+    for i in range(12):
+        prob, seed = synth.batched_problem(i)
+        P = hmg.Problem(prob)
+        N = P.ndof(0)
+        f = torch.from_numpy(synth.nodal_field(seed, N)).to(DEV)
+        b = torch.zeros(N, dtype=torch.float64, device=DEV)
+        P.rhs(f, b)
+        probs.append(P)
+        bs.append(b)
+        us.append(torch.zeros_like(b))
+    sts, its, hists = hmg.solve_batched(probs, "pcg", bs, us, rtol=1e-8, maxit=300)
+    assert all(s == 0 for s in sts)
+    for P, b, u, it, h in zip(probs, bs, us, its, hists):
+        u1 = torch.zeros_like(b)
+        st1, it1, h1 = P.solve("pcg", b, u1, rtol=1e-8, maxit=300)
+        assert st1 == 0 and it1 == it
+        assert float(torch.linalg.norm(u - u1) / torch.linalg.norm(u1)) < 1e-8    # FP32 V-cycle
+        assert h[-1] <= 1e-8 * h[0]
+    for P in probs:
+        P.close()
+
+
+def test_batched_matches_oracle_counts(hmg):
+    from oracle import multigrid
+    for i in (0, 3):
+        prob, seed = synth.batched_problem(i)
+        prob64 = dict(prob, smooth_prec="fp64")
+        P = hmg.Problem(prob64)
+        N = P.ndof(0)
+        f = synth.nodal_field(seed, N)
+        b = torch.zeros(N, dtype=torch.float64, device=DEV)
+        P.rhs(torch.from_numpy(f).to(DEV), b)
+        u = torch.zeros_like(b)
+        sts, its, _ = hmg.solve_batched([P], "pcg", [b], [u], rtol=1e-8, maxit=300)
+        H = multigrid.Hierarchy(prob64)
+        _, it_ref, _, ok = H.solve_pcg(H.fine.disc.rhs(f))
+        assert sts[0] == 0 and ok and abs(its[0] - it_ref) <= 1
+        P.close()
