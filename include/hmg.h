@@ -104,6 +104,14 @@ hmg_status hmg_desc_default(hmg_desc* d);
 hmg_status hmg_setup(const hmg_desc* desc, void* stream, hmg_problem** out);
 hmg_status hmg_destroy(hmg_problem* prob);
 
+/* Node count N of the finest level a descriptor describes (0 if the descriptor is invalid). */
+size_t hmg_desc_ndof(const hmg_desc* desc);
+
+/* Device bytes hmg_setup will hold for this descriptor (resident) and its peak during setup
+ * (resident plus setup temporaries), computed without touching the device. Used for
+ * admission by memory budget. */
+hmg_status hmg_estimate_bytes(const hmg_desc* desc, size_t* resident, size_t* peak);
+
 /* Hierarchy introspection. level_info writes nelem[3], order and the node count. */
 int hmg_nlevels(const hmg_problem* prob);
 size_t hmg_ndof(const hmg_problem* prob, int level);
@@ -188,6 +196,33 @@ long long hmg_fine_applies(const hmg_problem* prob);
 
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 long long hmg_launch_count(void);
+
+/* ---- serving: continuous batching of independent solves (one GPU) ----
+ * A server owns `max_slots` worker threads with one CUDA stream each. Submitted requests queue
+ * in FIFO order; a worker starts the head request as soon as a slot is free and its peak device
+ * memory (hmg_estimate_bytes plus its vectors) fits in `hbm_budget` beside what is resident.
+ * Hierarchies stay resident after their solve, keyed by the descriptor, so a later request for
+ * the same problem skips hmg_setup; idle ones are evicted least-recently-used when an admission
+ * needs the memory. Each request is hmg_rhs + hmg_solve on the worker's stream; work of
+ * different requests overlaps on the device. The server is thread-safe. */
+typedef struct hmg_server hmg_server;
+hmg_status hmg_server_create(int device, size_t hbm_budget, int max_slots, hmg_server** out);
+/* f_host: nodal right-hand side (hmg_desc_ndof(desc) doubles, copied at submit). Returns
+ * HMG_ENOMEM if the request could never fit the budget. */
+hmg_status hmg_server_submit(hmg_server* srv, const hmg_desc* desc, const double* f_host, double rtol, int mode,
+                             int maxit, unsigned long long* ticket);
+/* HMG_EBUSY while the request is queued or running; otherwise its solve status, once (the ticket
+ * is released). u_host (hmg_desc_ndof doubles), iters, res_final (final relative residual) and
+ * latency_s (submit to completion) may be NULL. */
+hmg_status hmg_server_poll(hmg_server* srv, unsigned long long ticket, double* u_host, int* iters,
+                           double* res_final, double* latency_s);
+/* As poll, blocking up to timeout_s seconds (HMG_ETIMEOUT if still running). */
+hmg_status hmg_server_wait(hmg_server* srv, unsigned long long ticket, double timeout_s, double* u_host,
+                           int* iters, double* res_final, double* latency_s);
+hmg_status hmg_server_stats(hmg_server* srv, long long* completed, long long* cache_hits, size_t* resident_bytes,
+                            int* queued);
+/* Stops the workers after the running requests, frees every resident hierarchy. */
+hmg_status hmg_server_destroy(hmg_server* srv);
 
 const char* hmg_status_string(hmg_status s);
 const char* hmg_last_error(void);

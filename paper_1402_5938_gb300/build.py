@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ops_apply.cu", "ops_setup.cu", "vector.cu", "hmg.cu", "noalloc.cu", "host_basis.cpp"]
+SOURCES = ["ops_apply.cu", "ops_setup.cu", "vector.cu", "hmg.cu", "noalloc.cu", "host_basis.cpp", "server.cpp"]
 
 
 def _nvcc():
@@ -33,6 +33,8 @@ def _compile(src, nvcc, verbose):
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-c", path, "-o", obj]
+    if src.endswith(".cpp"):
+        cmd = [nvcc, "-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-c", path, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

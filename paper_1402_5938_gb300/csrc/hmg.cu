@@ -766,6 +766,52 @@ hmg_status graph_solve_finish(ProblemImpl& P, int mode, int* iters, double* res_
   }
 }
 
+// ---- device-memory estimate of a hierarchy (mirrors setup_impl's allocations) -------------
+hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
+  std::vector<std::pair<std::vector<int>, int>> shapes;
+  CHECK(level_shapes(D, shapes));
+  const bool mixed = D.smooth_prec == HMG_PREC_FP32;
+  std::vector<Mesh> ms;
+  for (auto& sh : shapes) ms.push_back(make_mesh(D.dim, sh.first.data(), sh.second));
+  size_t res = 0, allocs = 0, max_stage = 0, max_tbuf = 0, arnoldi = 0;
+  auto add = [&](size_t b) { res += std::max<size_t>(b, 16); ++allocs; };
+  for (size_t k = 0; k < ms.size(); ++k) {
+    const Mesh& m = ms[k];
+    const size_t gsz = (size_t)(m.nelem * np_of(m)), n = (size_t)m.N;
+    add(gsz * nc_of(D.dim) * 8); add(gsz * 8);
+    for (int v = 0; v < 5; ++v) add(n * 8);
+    if (mixed) { add(gsz * nc_of(D.dim) * 4 + 256); for (int v = 0; v < 5; ++v) add(n * 4); }
+    max_stage = std::max(max_stage, gsz * D.dim * (D.dim + 1) * 8);
+    if (D.smoother == HMG_SMOOTH_CHEB && k + 1 < ms.size())
+      arnoldi = std::max(arnoldi, (size_t)(std::min<long long>(D.arnoldi_iters, interior_count(m)) + 1) * n * 8);
+    if (k + 1 < ms.size()) {
+      const Mesh& c = ms[k + 1];
+      long long od[3] = {c.Nn[0], c.Nn[1], c.Nn[2]};
+      for (int a = 0; a < D.dim; ++a) {
+        od[a] = m.Nn[a];
+        max_tbuf = std::max(max_tbuf, (size_t)(od[0] * od[1] * od[2]));
+        const size_t nnz = (size_t)m.Nn[a] * (c.p + 1);
+        add((m.Nn[a] + 1) * 4); add(nnz * 4); add(nnz * 8); add(nnz * 4);
+        add((c.Nn[a] + 1) * 4); add(nnz * 4); add(nnz * 8); add(nnz * 4);
+      }
+      long long rd[3] = {m.Nn[0], m.Nn[1], m.Nn[2]};
+      for (int a = 0; a < D.dim; ++a) { rd[a] = c.Nn[a]; max_tbuf = std::max(max_tbuf, (size_t)(rd[0] * rd[1] * rd[2])); }
+    }
+  }
+  const long long nI = interior_count(ms.back());
+  add((size_t)nI * nI * 8); add((size_t)nI * 8);
+  const size_t N0 = (size_t)ms[0].N;
+  add(64 * 8); add(4); add(kRedBlocks * 8); add(max_tbuf * 8); add(max_tbuf * 8);
+  for (int v = 0; v < 6; ++v) add(N0 * 8);
+  add(16);
+  res += 1001 * 8;                        // residual history of graph solves (default capacity)
+  res += allocs * 512;                    // allocation granularity
+  const size_t temp = std::max(max_stage + 16, std::max(arnoldi, (size_t)nI * 16));
+  if (resident) *resident = res;
+  if (peak) *peak = res + temp;
+  return HMG_OK;
+}
+
 bool level_ok(const hmg_problem* p, int level) {
   if (!p || level < 0 || level >= (int)p->impl.L.size()) {
     set_error("invalid problem handle or level");
@@ -1100,6 +1146,18 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
     if (first == HMG_OK && si != HMG_OK) first = si;
   }
   return first;
+}
+
+size_t hmg_desc_ndof(const hmg_desc* d) {
+  if (validate(d) != HMG_OK) return 0;
+  size_t n = 1;
+  for (int a = 0; a < d->dim; ++a) n *= (size_t)d->nelem[a] * d->order + 1;
+  return n;
+}
+
+hmg_status hmg_estimate_bytes(const hmg_desc* d, size_t* resident, size_t* peak) {
+  CHECK(validate(d));
+  return estimate_bytes(*d, resident, peak);
 }
 
 long long hmg_fine_applies(const hmg_problem* p) { return p ? p->impl.fine_applies : 0; }

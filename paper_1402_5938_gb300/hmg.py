@@ -66,6 +66,17 @@ _SIGS = {
     "hmg_restrict_noalloc": (_I, [_I, ctypes.POINTER(ctypes.c_int), _I, _I, _I, _V, _V, _V]),
     "hmg_solve_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_V), ctypes.POINTER(_V), _D, _I,
                                ctypes.POINTER(_I), ctypes.POINTER(ctypes.POINTER(_D)), ctypes.POINTER(_I), _V]),
+    "hmg_desc_ndof": (ctypes.c_size_t, [ctypes.POINTER(Desc)]),
+    "hmg_estimate_bytes": (_I, [ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "hmg_server_create": (_I, [_I, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "hmg_server_submit": (_I, [_P, ctypes.POINTER(Desc), ctypes.POINTER(_D), _D, _I, _I, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "hmg_server_poll": (_I, [_P, ctypes.c_ulonglong, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                             ctypes.POINTER(_D)]),
+    "hmg_server_wait": (_I, [_P, ctypes.c_ulonglong, _D, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                             ctypes.POINTER(_D)]),
+    "hmg_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
+    "hmg_server_destroy": (_I, [_P]),
     "hmg_fine_applies": (ctypes.c_longlong, [_P]),
     "hmg_launch_count": (ctypes.c_longlong, []),
     "hmg_status_string": (ctypes.c_char_p, [_I]),
@@ -275,3 +286,65 @@ def host_hessenberg_max_real_eig(H):
                                                 ctypes.byref(out))
     _check(st)
     return out.value
+
+
+def desc_ndof(prob: dict) -> int:
+    d = make_desc(prob)
+    return lib().hmg_desc_ndof(ctypes.byref(d))
+
+
+def estimate_bytes(prob: dict):
+    """(resident, peak) device bytes of hmg_setup for this workload (no device touched)."""
+    d = make_desc(prob)
+    r, pk = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().hmg_estimate_bytes(ctypes.byref(d), ctypes.byref(r), ctypes.byref(pk)))
+    return r.value, pk.value
+
+
+class Server:
+    """hmg_server: continuous batching of independent solves (see include/hmg.h)."""
+
+    def __init__(self, device=0, hbm_budget=8 << 30, max_slots=4):
+        h = ctypes.c_void_p()
+        _check(lib().hmg_server_create(int(device), int(hbm_budget), int(max_slots), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, prob: dict, f_host, rtol=1e-8, mode="pcg", maxit=1000):
+        d = make_desc(prob)
+        f = np.ascontiguousarray(f_host, dtype=np.float64)
+        if f.size != lib().hmg_desc_ndof(ctypes.byref(d)):
+            raise ValueError("right-hand side length does not match the problem")
+        t = ctypes.c_ulonglong()
+        _check(lib().hmg_server_submit(self.h, ctypes.byref(d), f.ctypes.data_as(ctypes.POINTER(_D)), float(rtol),
+                                       MODE[mode], int(maxit), ctypes.byref(t)))
+        return t.value, f.size
+
+    def _result(self, fn, ticket, n, *extra):
+        u = np.zeros(n)
+        it, res, lat = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+        st = fn(self.h, ctypes.c_ulonglong(ticket), *extra, u.ctypes.data_as(ctypes.POINTER(_D)), ctypes.byref(it),
+                ctypes.byref(res), ctypes.byref(lat))
+        return st, u, it.value, res.value, lat.value
+
+    def poll(self, ticket, n):
+        """(status, u, iterations, final relative residual, latency s); status HMG_EBUSY if not done."""
+        return self._result(lib().hmg_server_poll, ticket, n)
+
+    def wait(self, ticket, n, timeout_s=600.0):
+        return self._result(lib().hmg_server_wait, ticket, n, ctypes.c_double(timeout_s))
+
+    def stats(self):
+        c, h, r, q = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t(), ctypes.c_int()
+        _check(lib().hmg_server_stats(self.h, ctypes.byref(c), ctypes.byref(h), ctypes.byref(r), ctypes.byref(q)))
+        return dict(completed=c.value, cache_hits=h.value, resident_bytes=r.value, queued=q.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hmg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
