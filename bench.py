@@ -352,6 +352,142 @@ def run_sweep(args):
     return 0
 
 
+def run_batched(args):
+    """Batched workload: 512 independent 3D solves (E in 2..12, p in {2,4,6,8}, contrast 10^k,
+    k in 0..4) with an FP32 V-cycle inside FP64 PCG, all through one hmg_solve_batched call, against
+    the same 512 problems solved one at a time with the plain FP64 solver. One JSON line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1402_5938_gb300 import Problem, solve_batched
+    dev = torch.device("cuda", 0)
+    n = args.batch
+    t0 = time.perf_counter()
+    mixed, fp64, bs, dofs = [], [], [], []
+    for i in range(n):
+        prob, seed = synth.batched_problem(i)
+        Pm = Problem(prob)
+        P6 = Problem(dict(prob, smooth_prec="fp64"))
+        N = Pm.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device=dev)
+        Pm.rhs(torch.from_numpy(synth.nodal_field(seed, N)).to(dev), b)
+        mixed.append(Pm)
+        fp64.append(P6)
+        bs.append(b)
+        dofs.append(N)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    us = [torch.zeros_like(b) for b in bs]
+    solve_batched(mixed, "pcg", bs, us, rtol=1e-8, maxit=500)          # builds the graphs
+    reps, tb = 3, []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sts, its, _ = solve_batched(mixed, "pcg", bs, us, rtol=1e-8, maxit=500)
+        tb.append(time.perf_counter() - t)
+    u6 = [torch.zeros_like(b) for b in bs]
+    for P, b, u in zip(fp64, bs, u6):                                   # build graphs
+        P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    its6 = []
+    for P, b, u in zip(fp64, bs, u6):
+        st, it, _ = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+        its6.append(it)
+    t_seq = time.perf_counter() - t
+    diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(us, u6))
+    r = torch.zeros_like(bs[0])
+    worst = 0.0
+    for P, b, u in zip(fp64, bs, us):
+        rr = torch.zeros_like(b)
+        P.apply(0, u, rr)
+        worst = max(worst, float(torch.linalg.norm(b - rr) / torch.linalg.norm(b)))
+    tbm = statistics.median(tb)
+    print(json.dumps({
+        "batched": f"{n} solves", "total_dof": sum(dofs), "setup_s_both_sets": setup_s,
+        "batched_mixed_s": tbm, "batched_solves_per_s": n / tbm, "batched_gdof_per_s": sum(dofs) / tbm / 1e9,
+        "fp64_one_at_a_time_s": t_seq, "fp64_solves_per_s": n / t_seq, "speedup_vs_fp64_sequential": t_seq / tbm,
+        "all_converged": all(s_ == 0 for s_ in sts), "iters_mixed_mean": statistics.mean(its),
+        "iters_fp64_mean": statistics.mean(its6), "max_rel_diff_mixed_vs_fp64": diff,
+        "worst_fp64_residual_of_mixed": worst}), flush=True)
+    for P in mixed + fp64:
+        P.close()
+    return 0
+
+
+def run_serve(args):
+    """Serving workload: Poisson arrivals (2,000/s mean) of 2D/3D solves, DOF log-uniform in
+    [1e3, 2e6], p uniform in 1..16, through the continuous-batching server (FP32 V-cycle in FP64
+    PCG); p50/p99 latency (submit to result on the host) and solves/s at the specified rate and
+    at half the measured saturated rate, against the plain FP64 path one request at a time
+    (single-server queue on the same arrivals). One JSON line."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1402_5938_gb300 import Problem, Server, desc_ndof
+    dev = torch.device("cuda", 0)
+    R = args.requests
+    reqs = [synth.serving_request(i) for i in range(R)]
+    fs = [synth.nodal_field(seed, desc_ndof(prob)) for prob, seed, _ in reqs]
+    gaps = np.array([g for _, _, g in reqs])
+
+    def serve(scale, slots):
+        srv = Server(0, 160 << 30, slots)
+        arr = np.cumsum(gaps * scale)
+        t0 = time.perf_counter()
+        tickets = []
+        for (prob, _, _), f, a in zip(reqs, fs, arr):
+            dt = t0 + a - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(prob, f, rtol=1e-8, mode="pcg", maxit=500))
+        lat, ok, done_at = [], 0, []
+        for (t, n), a in zip(tickets, arr):
+            st, u, it, res, l = srv.wait(t, n)
+            ok += int(st == 0)
+            lat.append(l)
+            done_at.append(a + l)
+        span = max(done_at)
+        srv.close()
+        return dict(p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
+                    solves_per_s=R / span, ok=ok, offered_per_s=R / arr[-1])
+
+    hot = serve(1.0, args.slots)
+    cool = serve(max(1.0, (R / gaps.sum()) / (0.5 * hot["solves_per_s"])), args.slots)
+    # plain FP64 path, one request at a time: service times, then a single-server queue
+    service = []
+    for (prob, _, _), f in zip(reqs, fs):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        P = Problem(dict(prob, smooth_prec="fp64"))
+        N = P.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device=dev)
+        P.rhs(torch.from_numpy(f).to(dev), b)
+        u = torch.zeros_like(b)
+        P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+        u.cpu()
+        P.close()
+        service.append(time.perf_counter() - t)
+    arr = np.cumsum(gaps)
+    fin, lat = 0.0, []
+    for a, sv in zip(arr, service):
+        start = max(a, fin)
+        fin = start + sv
+        lat.append(fin - a)
+    print(json.dumps({
+        "serve": f"{R} requests, Poisson 2000/s, {args.slots} slots", "at_2000_per_s": hot,
+        "below_saturation": cool,
+        "fp64_one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                               "p99_ms": 1e3 * float(np.percentile(lat, 99)), "solves_per_s": R / fin,
+                               "mean_service_ms": 1e3 * float(np.mean(service))}}), flush=True)
+    return 0
+
+
 def run_profile_apply(args):
     """Small fixed launch sequence for ncu: build the hierarchy of the warped var-coef problem
     (--mesh elements per axis, --order p, p-multigrid), then two applies on each of the three
@@ -390,12 +526,21 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
     ap.add_argument("--sweep", action="store_true", help="order sweep at ~2M DOF, FP64 vs mixed precision")
+    ap.add_argument("--batched", action="store_true", help="512-solve batched workload vs FP64 one at a time")
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--serve", action="store_true", help="Poisson-arrival serving workload")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--mesh", type=int, default=16, help="--profile-apply: elements per axis")
     ap.add_argument("--order", type=int, default=4, help="--profile-apply: polynomial order")
     ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="--profile-apply: precision")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)
+    if args.batched:
+        return run_batched(args)
+    if args.serve:
+        return run_serve(args)
     if args.profile_apply:
         return run_profile_apply(args)
     if args.impl == "reference":
