@@ -446,16 +446,20 @@ def run_serve(args):
             if dt > 0:
                 time.sleep(dt)
             tickets.append(srv.submit(prob, f, rtol=1e-8, mode="pcg", maxit=500))
-        lat, ok, done_at = [], 0, []
-        for (t, n), a in zip(tickets, arr):
+        lat, ok, done_at, failed = [], 0, [], []
+        for i, ((t, n), a) in enumerate(zip(tickets, arr)):
             st, u, it, res, l = srv.wait(t, n)
             ok += int(st == 0)
+            if st != 0:
+                p = reqs[i][0]
+                failed.append({"i": i, "status": st, "iters": it, "dim": p["dim"], "nelem": p["nelem"][0],
+                               "order": p["order"], "res": res})
             lat.append(l)
             done_at.append(a + l)
         span = max(done_at)
         srv.close()
         return dict(p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
-                    solves_per_s=R / span, ok=ok, offered_per_s=R / arr[-1])
+                    solves_per_s=R / span, ok=ok, offered_per_s=R / arr[-1], failed=failed)
 
     hot = serve(1.0, args.slots)
     cool = serve(max(1.0, (R / gaps.sum()) / (0.5 * hot["solves_per_s"])), args.slots)

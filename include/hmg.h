@@ -227,6 +227,11 @@ hmg_status hmg_server_destroy(hmg_server* srv);
 const char* hmg_status_string(hmg_status s);
 const char* hmg_last_error(void);
 
+/* Failure-detection self test: one device thread waits, with at most `polls` polls, on an
+ * mbarrier that nothing completes (no copy in flight) -- the bounded wait every TMA-staged kernel
+ * uses. *timed_out = 1 and HMG_ETIMEOUT when the wait gave up; the context stays usable. */
+hmg_status hmg_selftest_bounded_wait(unsigned polls, int* timed_out);
+
 /* ---- host-only helpers (no device needed): the library's own 1D tables and eigen step ---- */
 
 /* GLL nodes r[p+1], Gauss points g[p+1] and weights w[p+1] on [0,1] (Sec. 2.3, Fig. 1). */

@@ -12,6 +12,12 @@
 #include <string>
 #include <vector>
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "ops.cuh"
 #include "vector.cuh"
@@ -42,6 +48,36 @@ cudaError_t ensure_smem_ptr(const void* kernel, size_t bytes) {
   if (e == cudaSuccess) g_smem_done.insert({kernel, dev});
   return e;
 }
+
+// Phase tracing: an NVTX range per phase (visible to Nsight tools), and with HMG_TRACE=1 in the
+// environment the phase's wall time (after synchronizing its stream) on stderr.
+struct Phase {
+  const char* name;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  static bool timing() {
+    static const bool on = [] {
+      const char* v = getenv("HMG_TRACE");
+      return v && v[0] == '1';
+    }();
+    return on;
+  }
+  Phase(const char* n, cudaStream_t st) : name(n), s(st) {
+    nvtxRangePushA(n);
+    if (timing()) {
+      cudaStreamSynchronize(s);
+      t0 = std::chrono::steady_clock::now();
+    }
+  }
+  ~Phase() {
+    if (timing()) {
+      cudaStreamSynchronize(s);
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      fprintf(stderr, "hmg %s: %.3f ms\n", name, ms);
+    }
+    nvtxRangePop();
+  }
+};
 
 struct Level {
   Mesh m{};
@@ -88,6 +124,9 @@ struct ProblemImpl {
   long long gkern[2][3] = {};  // kernel nodes per graph section: prologue, loop body (part 1), PCG part 2
   bool capturing = false;
 
+  // Device allocation zeroed in order on the setup stream (the caller's stream may be a
+  // non-blocking stream that the legacy default stream does not order against).
+  cudaStream_t setup_stream = nullptr;
   cudaError_t alloc(void** p, size_t nbytes) {
     *p = nullptr;
     if (nbytes == 0) nbytes = 16;
@@ -95,7 +134,7 @@ struct ProblemImpl {
     if (e != cudaSuccess) return e;
     dev_allocs.push_back(*p);
     bytes += nbytes;
-    return cudaMemset(*p, 0, nbytes);
+    return cudaMemsetAsync(*p, 0, nbytes, setup_stream);
   }
   ~ProblemImpl() {
     for (int m = 0; m < 2; ++m) {
@@ -244,10 +283,12 @@ hmg_status build_axis(ProblemImpl& P, const Level& f, const Level& c, int a, Axi
     TRY(P.alloc((void**)&out->col, ci.size() * sizeof(int)));
     TRY(P.alloc((void**)&out->val, v.size() * sizeof(double)));
     TRY(P.alloc((void**)&out->val32, v32.size() * sizeof(float)));
-    TRY(cudaMemcpy(out->rowptr, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(out->col, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(out->val, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(out->val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    // pageable sources: each asynchronous copy has staged them when it returns
+    cudaStream_t s = P.setup_stream;
+    TRY(cudaMemcpyAsync(out->rowptr, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(out->col, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(out->val, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(out->val32, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     return HMG_OK;
   };
   CHECK(upload(rows, ncn, Pax));
@@ -490,7 +531,7 @@ hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
     if (!bd) gm.push_back(g);
   }
   TRY(P.alloc((void**)&l.gmap, nI * sizeof(long long)));
-  TRY(cudaMemcpy(l.gmap, gm.data(), nI * sizeof(long long), cudaMemcpyHostToDevice));
+  TRY(cudaMemcpyAsync(l.gmap, gm.data(), nI * sizeof(long long), cudaMemcpyHostToDevice, s));
   TRY(launch_elem_dense(l.m, l.basis, l.G, l.Ainv, nI, s));
   double *rowk = nullptr, *colk = nullptr;
   TRY(cudaMalloc((void**)&rowk, nI * sizeof(double)));
@@ -506,6 +547,7 @@ hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
 
 hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   const hmg_desc& D = P.desc;
+  P.setup_stream = s;
   std::vector<std::pair<std::vector<int>, int>> shapes;
   CHECK(level_shapes(D, shapes));
   P.L.resize(shapes.size());
@@ -526,6 +568,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
     long long rd[3] = {f.Nn[0], f.Nn[1], f.Nn[2]};
     for (int a = 0; a < D.dim; ++a) { rd[a] = c.Nn[a]; max_tbuf = std::max(max_tbuf, (size_t)(rd[0] * rd[1] * rd[2])); }
   }
+  Phase ph_all("setup", s);
   TRY(P.alloc((void**)&P.S, 64 * sizeof(double)));
   TRY(P.alloc((void**)&P.err, sizeof(int)));
   TRY(P.alloc((void**)&P.partial, kRedBlocks * sizeof(double)));
@@ -549,6 +592,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   hmg_status st = [&]() -> hmg_status {
     const bool mixed = D.smooth_prec == HMG_PREC_FP32;
     for (size_t k = 0; k < P.L.size(); ++k) {
+      Phase ph("setup: level geometry, diagonal", s);
       Level& l = P.L[k];
       const long long n = l.m.N;
       const long long gsz = l.m.nelem * np_of(l.m);
@@ -580,11 +624,19 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         TRY(to_f32(l.dinv32, l.dinv, n, s));
       }
     }
-    for (size_t k = 0; k + 1 < P.L.size(); ++k)
-      for (int a = 0; a < D.dim; ++a) CHECK(build_axis(P, P.L[k], P.L[k + 1], a, &P.L[k].P[a], &P.L[k].PT[a]));
-    CHECK(build_coarse(P, P.L.back(), s));
-    if (D.smoother == HMG_SMOOTH_CHEB)
+    {
+      Phase ph("setup: transfer stencils", s);
+      for (size_t k = 0; k + 1 < P.L.size(); ++k)
+        for (int a = 0; a < D.dim; ++a) CHECK(build_axis(P, P.L[k], P.L[k + 1], a, &P.L[k].P[a], &P.L[k].PT[a]));
+    }
+    {
+      Phase ph("setup: coarsest dense inverse", s);
+      CHECK(build_coarse(P, P.L.back(), s));
+    }
+    if (D.smoother == HMG_SMOOTH_CHEB) {
+      Phase ph("setup: Arnoldi bounds", s);
       for (size_t k = 0; k + 1 < P.L.size(); ++k) CHECK(arnoldi(P, (int)k, s));
+    }
     TRY(cudaStreamSynchronize(s));
     return HMG_OK;
   }();
@@ -878,9 +930,10 @@ hmg_status hmg_destroy(hmg_problem* p) {
   if (!p) return HMG_OK;
   int cur = 0;
   cudaGetDevice(&cur);
-  if (cur != p->impl.device) cudaSetDevice(p->impl.device);
+  const int dev = p->impl.device;
+  if (cur != dev) cudaSetDevice(dev);
   delete p;
-  if (cur != p->impl.device) cudaSetDevice(cur);
+  if (cur != dev) cudaSetDevice(cur);
   return HMG_OK;
 }
 
@@ -1010,6 +1063,7 @@ hmg_status hmg_solve(hmg_problem* p, int mode, const double* b, double* u, doubl
   if (p && p->impl.desc.solve_graph && (mode == HMG_MODE_MG || mode == HMG_MODE_PCG) && b && u && maxit >= 0 &&
       rtol >= 0.0) {
     cudaStream_t s = (cudaStream_t)stream;
+    Phase ph(mode == HMG_MODE_PCG ? "solve (PCG graph)" : "solve (MG graph)", s);
     st = graph_solve_enqueue(p->impl, mode, b, u, rtol, maxit, s);
     if (st == HMG_OK) {
       cudaError_t e = cudaStreamSynchronize(s);
@@ -1179,6 +1233,20 @@ const char* hmg_status_string(hmg_status s) {
 }
 
 const char* hmg_last_error(void) { return g_err.c_str(); }
+
+hmg_status hmg_selftest_bounded_wait(unsigned polls, int* timed_out) {
+  if (!timed_out || polls == 0 || polls > (1u << 24)) { set_error("polls must be in 1..2^24"); return HMG_EINVAL; }
+  int* d = nullptr;
+  TRY(cudaMalloc((void**)&d, sizeof(int)));
+  cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) e = bounded_wait_probe(polls, d, 0);
+  int h = -1;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  TRY(e);
+  *timed_out = h;
+  return h == 1 ? HMG_ETIMEOUT : HMG_OK;
+}
 
 hmg_status hmg_host_basis(int order, double* gll, double* gx, double* gw) {
   if (order < 1 || order > 16) { set_error("order must be in 1..16"); return HMG_EINVAL; }

@@ -77,6 +77,7 @@ struct hmg_server {
   unsigned long long next_ticket = 1, tick = 0;
   long long completed = 0, cache_hits = 0;
   int inflight = 0;
+  bool admitting = false;  // a worker is inside admit(), which may drop the lock to evict
   bool stop = false;
   std::vector<std::thread> threads;
   std::vector<Worker> workers;
@@ -127,12 +128,16 @@ void hmg_server::run(int w) {
     std::shared_ptr<Request> r;
     cv_work.wait(lk, [&] {
       if (stop) return true;
+      if (admitting) return false;  // one admission at a time: admit() may unlock to evict
+      bool got = false;
+      admitting = true;
       while (!queue.empty()) {
         std::shared_ptr<Request> head = queue.front();
         if (admit(head, lk)) {
           r = head;
           queue.pop_front();
-          return true;
+          got = true;
+          break;
         }
         // nothing running or cached could make room: this request can never start
         if (inflight == 0 && cache.empty()) {
@@ -143,9 +148,11 @@ void hmg_server::run(int w) {
           cv_done.notify_all();
           continue;
         }
-        return false;
+        break;
       }
-      return false;
+      admitting = false;
+      cv_work.notify_all();  // let waiting workers look at the new queue head
+      return got;
     });
     if (stop && !r) return;
     if (!r) continue;

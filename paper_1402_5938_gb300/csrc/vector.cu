@@ -4,6 +4,7 @@
 
 #include <type_traits>
 
+#include "tma.cuh"
 #include "vector.cuh"
 
 namespace hmg {
@@ -232,6 +233,17 @@ __global__ void k_step_check(const double* S, int* ctrl, double* hist, cudaGraph
   if (has_if) cudaGraphSetConditional(hi, cont);
 }
 
+// Waits on an mbarrier that nothing ever arrives at (no copy in flight), with `polls` polls,
+// and records whether the bounded wait gave up: exercises the timeout path the kernels use.
+__global__ void k_wait_probe(uint32_t polls, int* out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    out[0] = mbar_wait(&bar, 0, polls) ? 0 : 1;
+  }
+}
+
 struct Gll {
   double r[kMaxN];
 };
@@ -431,6 +443,10 @@ cudaError_t div_dev(double* y, const double* x, long long n, const double* den, 
 }
 cudaError_t copy_scalar(double* dst, const double* src, cudaStream_t s) {
   k_copy_scalar<<<1, 1, 0, s>>>(dst, src);
+  return counted(cudaGetLastError());
+}
+cudaError_t bounded_wait_probe(unsigned polls, int* out_dev, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(polls, out_dev);
   return counted(cudaGetLastError());
 }
 cudaError_t set_solve_params(double* S, int* ctrl, double rtol, int maxit, int cap, cudaStream_t s) {

@@ -90,6 +90,9 @@ cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const l
 cudaError_t coarse_solve_f32(const double* Ainv, const float* b, float* x, const long long* gmap,
                              long long nI, cudaStream_t s);
 
+// one block waits (bounded, `polls` polls) on a barrier nothing completes; *out_dev = 1 if it gave up
+cudaError_t bounded_wait_probe(unsigned polls, int* out_dev, cudaStream_t s);
+
 // graph-solve control kernels (single thread): parameters, start check, per-iteration check.
 // The checks set the WHILE condition `hw` (and the IF condition `hi` if has_if) to "continue".
 cudaError_t set_solve_params(double* S, int* ctrl, double rtol, int maxit, int cap, cudaStream_t s);

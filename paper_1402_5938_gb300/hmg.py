@@ -77,6 +77,7 @@ _SIGS = {
     "hmg_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
     "hmg_server_destroy": (_I, [_P]),
+    "hmg_selftest_bounded_wait": (_I, [ctypes.c_uint, ctypes.POINTER(_I)]),
     "hmg_fine_applies": (ctypes.c_longlong, [_P]),
     "hmg_launch_count": (ctypes.c_longlong, []),
     "hmg_status_string": (ctypes.c_char_p, [_I]),
@@ -237,7 +238,7 @@ class Problem:
         hist = (ctypes.c_double * (maxit + 1))()
         st = lib().hmg_solve(self.h, MODE[mode], _ptr(b, n), _ptr(u, n), float(rtol), int(maxit),
                              ctypes.byref(it), hist, _stream(stream))
-        if st not in (HMG_OK, HMG_ENOCONV) or (raise_on_noconv and st != HMG_OK):
+        if st not in (HMG_OK, HMG_ENOCONV, HMG_ENAN) or (raise_on_noconv and st != HMG_OK):
             _check(st)
         return st, it.value, np.array(hist[: it.value + 1])
 

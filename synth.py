@@ -101,7 +101,8 @@ def serving_request(i, base_seed=5):
     """Request i of the serving workload: Poisson arrivals (mean rate 2,000/s, exponential
     gaps from SplitMix64 seed base), dimension 2 or 3, target DOF log-uniform in [1e3, 2e6],
     order p uniform in 1..16; elements per axis E = round((N^(1/d) - 1)/p), moved to the nearest
-    m * 2^k whose k halvings reach a p=1 grid of <= 4,913 nodes (m <= 16 in 3D, m <= 69 in 2D),
+    m * 2^k whose k halvings reach a p=1 grid of <= 729 nodes (m <= 8 in 3D, m <= 26 in 2D), which
+    keeps the dense exact coarsest solve (O(n^3) FP64 setup) small,
     p-multigrid to p = 1 then those k h-levels; warped domain, mu = 1 + 1e3 sum cos^2(2 pi x_i),
     V(3,3) Chebyshev, FP32 V-cycle in FP64 PCG to 1e-8. Returns (problem, rhs seed, gap in s)."""
     u = uniform_pm1(base_seed, 5, start=5 * i)
@@ -110,7 +111,7 @@ def serving_request(i, base_seed=5):
     N = 10.0 ** (3.0 + (np.log10(2e6) - 3.0) * 0.5 * (u[2] + 1.0))
     p = 1 + min(15, int(8.0 * (u[3] + 1.0)))
     target = max(1.0, (N ** (1.0 / d) - 1.0) / p)
-    mmax = 16 if d == 3 else 69
+    mmax = 8 if d == 3 else 26
     best = None
     for k in range(0, 12):
         for m in range(1, mmax + 1):
