@@ -104,6 +104,18 @@ def cpu_baseline(hier):
     return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+def aggregate_ranks(t_step_ms, dof_per_rank, world, dist=None, device=None):
+    """Replicas: every rank solves its own copy; the job's time per step is the slowest rank's
+    and its throughput counts every rank's DOF: value = world * N / max_t (GDOF/s)."""
+    import torch
+    t = torch.tensor([float(t_step_ms)], dtype=torch.float64, device=device)
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return t_max, world * dof_per_rank / (t_max * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -211,12 +223,7 @@ def run_gpu(args):
     launches = launch_count() - l0
     applies = (P.fine_applies() - a0) / args.steps
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    t_step = sum(step_ms) / len(step_ms)
-    t_max = torch.tensor([t_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    t_step = float(t_max.item())
-    value = world * N / (t_step * 1e-3) / 1e9
+    t_step, value = aggregate_ranks(sum(step_ms) / len(step_ms), N, world, dist, dev)
     rel_res = float(hist[-1] / hist[0])
 
     # ---- end to end through the public API: pinned host f -> rhs -> solve -> host u
@@ -231,11 +238,7 @@ def run_gpu(args):
         u_host.copy_(u, non_blocking=True)
     e2e_ev[1].record(stream)
     barrier()
-    e2e_ms = e2e_ev[0].elapsed_time(e2e_ev[1]) / args.steps
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * N / (float(e2e_t.item()) * 1e-3) / 1e9
+    _, e2e_value = aggregate_ranks(e2e_ev[0].elapsed_time(e2e_ev[1]) / args.steps, N, world, dist, dev)
 
     # ---- the dominant kernel: the FP64 order-p apply on the finest level, timed alone
     x = torch.from_numpy(synth.uniform_pm1(7, N)).to(dev)
