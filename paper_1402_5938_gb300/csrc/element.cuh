@@ -206,7 +206,7 @@ k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __res
     if (NBUF > 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, b ^ 1);
     const long long e0 = t * epb;
     const int ne = (int)min((long long)epb, m.nelem - e0);
-    if (threadIdx.x < ne) elem_base(m, e0 + threadIdx.x, &ebase[threadIdx.x], &eflag[threadIdx.x]);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) elem_base(m, e0 + e, &ebase[e], &eflag[e]);
     __syncthreads();
     for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
       const int e = i / NP, a = i - e * NP;
@@ -290,12 +290,27 @@ k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __res
 // Buffers (4 per element tile): cur/nxt ping-pong for the B and B^T passes, and the
 // reference gradient (V0 in the free ping-pong buffer, V1, V2).
 // ---------------------------------------------------------------------------------------
-template <int DIM, int N>
+// Block shapes of the FP64 apply: variant V in {0,1,2} of (elements per block NEG, threads GT).
+// Low orders vary the elements per block (one warp's worth, ~128 or ~512 points); high orders
+// keep one element per block and vary the threads. Setup times the variants on each level
+// and keeps the fastest (see tune_apply in hmg.cu).
+constexpr int apply64_gt_rule(int w) { return w <= 512 ? 32 : (w <= 1000 ? 64 : (w <= 2200 ? 128 : (w <= 3400 ? 256 : 512))); }
+constexpr int apply64_neg(int np, int v) {
+  return np >= 100 ? 1 : ((v == 0 ? 32 : (v == 1 ? 128 : 512)) / np > 1 ? (v == 0 ? 32 : (v == 1 ? 128 : 512)) / np : 1);
+}
+constexpr int apply64_gt(int np, int v) {
+  return np < 100 ? apply64_gt_rule(apply64_neg(np, v) * np)
+                  : (v == 0 ? apply64_gt_rule(np)
+                            : (v == 1 ? (2 * apply64_gt_rule(np) > 512 ? 512 : 2 * apply64_gt_rule(np))
+                                      : (apply64_gt_rule(np) >= 64 ? apply64_gt_rule(np) / 2 : 4 * apply64_gt_rule(np))));
+}
+
+template <int DIM, int N, int V>
 struct Apply64Cfg {
   static constexpr int NP = Sh<DIM, N>::NP;
-  static constexpr int NEG = NP >= 100 ? 1 : (NP == 64 ? 2 : (NP == 27 ? 8 : (NP >= 16 ? 4 : 8)));
+  static constexpr int NEG = apply64_neg(NP, V);
   static constexpr int W = NEG * NP;
-  static constexpr int GT = W <= 512 ? 32 : (W <= 1000 ? 64 : (W <= 2200 ? 128 : (W <= 3400 ? 256 : 512)));
+  static constexpr int GT = apply64_gt(NP, V);
   static constexpr size_t smem = (size_t)(2 * N * N + (DIM + 1) * W) * sizeof(double) + NEG * 16;
 };
 
@@ -309,11 +324,11 @@ __device__ __forceinline__ double pt_dot(const double* __restrict__ M, const dou
   return s;
 }
 
-template <int DIM, int N>
-__global__ void __launch_bounds__(Apply64Cfg<DIM, N>::GT)
+template <int DIM, int N, int V>
+__global__ void __launch_bounds__(Apply64Cfg<DIM, N, V>::GT)
 k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ G, const Mesh m,
           const __grid_constant__ Tab<N, double> tab, const double alpha) {
-  using C = Apply64Cfg<DIM, N>;
+  using C = Apply64Cfg<DIM, N, V>;
   constexpr int NP = C::NP, NEG = C::NEG, W = C::W, NC = Sh<DIM, N>::NC;
   constexpr int S1 = N, S2 = N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -332,17 +347,7 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
     sB[t] = tab.B[t];
     sD[t] = tab.D[t];
   }
-  if (threadIdx.x < ne) {
-    const long long e = e0 + threadIdx.x;
-    const int ex = (int)(e % m.E[0]);
-    const long long r = e / m.E[0];
-    const int ey = (int)(r % m.E[1]);
-    const int ez = (int)(r / m.E[1]);
-    ebase[threadIdx.x] = ((long long)ez * m.p * m.Nn[1] + (long long)ey * m.p) * m.Nn[0] + (long long)ex * m.p;
-    int f = (ex == 0) | ((ex == m.E[0] - 1) << 1) | ((ey == 0) << 2) | ((ey == m.E[1] - 1) << 3);
-    if (DIM == 3) f |= ((ez == 0) << 4) | ((ez == m.E[2] - 1) << 5);
-    eflag[threadIdx.x] = f;
-  }
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) elem_base(m, e0 + e, &ebase[e], &eflag[e]);
   __syncthreads();
   const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
   auto node = [&](int t, bool& bd) -> long long {
@@ -366,10 +371,14 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int st = d == 0 ? 1 : (d == 1 ? S1 : S2);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      const int a = t % NP;
+    for (int t = threadIdx.x; t < nt; t += 2 * blockDim.x) {  // two independent chains per thread
+      const int t2 = t + blockDim.x;
+      const int a = t % NP, a2 = t2 % NP;
       const int idx = d == 0 ? a % N : (d == 1 ? (a / N) % N : a / (N * N));
-      nxt[t] = pt_dot<N, false>(sB, cur, idx, t - idx * st, st);
+      const int idx2 = d == 0 ? a2 % N : (d == 1 ? (a2 / N) % N : a2 / (N * N));
+      const double v1 = pt_dot<N, false>(sB, cur, idx, t - idx * st, st);
+      if (t2 < nt) nxt[t2] = pt_dot<N, false>(sB, cur, idx2, t2 - idx2 * st, st);
+      nxt[t] = v1;
     }
     __syncthreads();
     double* tmp = cur; cur = nxt; nxt = tmp;
@@ -414,10 +423,14 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
     const int st = d == 0 ? 1 : (d == 1 ? S1 : S2);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      const int a = t % NP;
+    for (int t = threadIdx.x; t < nt; t += 2 * blockDim.x) {
+      const int t2 = t + blockDim.x;
+      const int a = t % NP, a2 = t2 % NP;
       const int idx = d == 0 ? a % N : (d == 1 ? (a / N) % N : a / (N * N));
-      nxt[t] = pt_dot<N, true>(sB, cur, idx, t - idx * st, st);
+      const int idx2 = d == 0 ? a2 % N : (d == 1 ? (a2 / N) % N : a2 / (N * N));
+      const double v1 = pt_dot<N, true>(sB, cur, idx, t - idx * st, st);
+      if (t2 < nt) nxt[t2] = pt_dot<N, true>(sB, cur, idx2, t2 - idx2 * st, st);
+      nxt[t] = v1;
     }
     __syncthreads();
     double* tmp = cur; cur = nxt; nxt = tmp;

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <set>
 #include <new>
@@ -89,6 +91,7 @@ struct Level {
   float* G32 = nullptr;
   float* dinv32 = nullptr;
   double lam = 0.0;       // Chebyshev bound
+  int v64 = 0, v32 = 0;   // apply block-shape variants chosen by the autotuner
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d32 = nullptr;
   Axis1D P[3]{}, PT[3]{};  // transfer to the next coarser level: P rows fine, PT rows coarse
@@ -317,13 +320,13 @@ template <> struct Acc<float> {
 hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, s));
+  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, s, l.v64));
   return HMG_OK;
 }
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s));
+  TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s, l.v32));
   return HMG_OK;
 }
 
@@ -492,7 +495,7 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
     for (int j = 0; j < m; ++j) {
       double* w = V[j + 1];
       TRY(cudaMemsetAsync(w, 0, n * sizeof(double), s));
-      TRY(launch_apply_f64(l.m, l.basis, V[j], w, l.G, 1.0, s));
+      TRY(launch_apply_f64(l.m, l.basis, V[j], w, l.G, 1.0, s, l.v64));
       TRY(scale_by(w, l.dinv, n, s));
       for (int i = 0; i <= j; ++i) {
         TRY(dot_partial(w, V[i], n, P.partial, s));
@@ -512,6 +515,73 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
   }();
   cleanup();
   return st;
+}
+
+// ---- autotuning of the apply block shape -------------------------------------------------
+// For each level, time the kernel variants (kApplyVariants block shapes) with CUDA events on the
+// level's own buffers and keep the fastest; results are cached per (device, dim, order, element
+// count, precision) for the process. HMG_AUTOTUNE=0 in the environment keeps variant 0.
+bool autotune_on() {
+  static const bool on = [] {
+    const char* v = getenv("HMG_AUTOTUNE");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
+  if (!autotune_on()) return HMG_OK;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, long long, int>, int> cache;
+  int dev = 0;
+  TRY(cudaGetDevice(&dev));
+  const bool mixed = l.G32 != nullptr;
+  for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
+    const auto key = std::make_tuple(dev, l.m.dim, l.m.p, l.m.nelem, prec);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) {
+        (prec ? l.v32 : l.v64) = it->second;
+        continue;
+      }
+    }
+    cudaEvent_t e0, e1;
+    TRY(cudaEventCreate(&e0));
+    TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bv = 0;
+    cudaError_t err = cudaSuccess;
+    for (int v = 0; v < kApplyVariants && err == cudaSuccess; ++v) {
+      auto run = [&]() {
+        return prec ? launch_apply_f32(l.m, l.basis, l.x32, l.r32, l.G32, 1.0f, P.err, s, v)
+                    : launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, s, v);
+      };
+      if ((err = run()) != cudaSuccess) break;  // warm-up (also opts the kernel into its smem)
+      if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
+      for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run();
+      if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && ms < best) {
+        best = ms;
+        bv = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(err);
+    (prec ? l.v32 : l.v64) = bv;
+    if (Phase::timing())
+      fprintf(stderr, "hmg autotune: dim %d p %d elements %lld %s -> variant %d (%.4f ms per apply)\n", l.m.dim,
+              l.m.p, l.m.nelem, prec ? "fp32" : "fp64", bv, best / 3);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = bv;
+  }
+  TRY(cudaMemsetAsync(l.r, 0, l.m.N * sizeof(double), s));
+  if (mixed) TRY(cudaMemsetAsync(l.r32, 0, l.m.N * sizeof(float), s));
+  return HMG_OK;
 }
 
 hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
@@ -623,6 +693,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         TRY(to_f32(l.G32, l.G, gsz * nc_of(D.dim), s));
         TRY(to_f32(l.dinv32, l.dinv, n, s));
       }
+      CHECK(tune_level(P, l, s));
     }
     {
       Phase ph("setup: transfer stencils", s);

@@ -9,10 +9,12 @@ namespace hmg {
 // y += alpha * A x (FP64 or FP32 data; G in the same precision). The FP32 kernel stages G
 // with bulk TMA copies and needs G allocated with >= 16 bytes of tail padding; a timed-out
 // wait sets *err (device int) to a nonzero code.
+// `variant` (0..2) selects the block shape; setup picks it per level by timing (autotuning).
+constexpr int kApplyVariants = 3;
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
-                             const double* G, double alpha, cudaStream_t s);
+                             const double* G, double alpha, cudaStream_t s, int variant = 0);
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
-                             const float* G, float alpha, int* err, cudaStream_t s);
+                             const float* G, float alpha, int* err, cudaStream_t s, int variant = 0);
 
 // Geometry: stage buffer J [E][dim*(dim+1)][NP], then G [E][NC][NP] and wdetJ [E][NP].
 // *bad (device int) is set to 1 where det J <= 0.

@@ -1,4 +1,4 @@
-// Instantiation and launch of the operator-apply kernels (FP64 and FP32).
+// Instantiation and launch of the FP32 operator-apply kernel (TMA-staged geometric factors).
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -42,14 +42,16 @@ int blocks_per_sm(const void* kernel, int threads, size_t smem) {
 
 template <int DIM>
 cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* y, const float* G, float alpha,
-                        int* err, cudaStream_t s) {
+                        int* err, int variant, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
     constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
     constexpr int NBUF = (DIM == 2 || NP <= 3200) ? 2 : 1;
     using C = Apply32Cfg<DIM, N, NBUF>;
     const size_t per = (size_t)(NBUF * NC + 1 + DIM) * NP * 4;
-    int epb = (int)std::max<size_t>(1, (64 * 1024) / per);
+    // variant 0: ~64 KB of shared memory per block; 1: half the tile; 2: double the tile
+    const size_t target = variant == 1 ? 32 * 1024 : (variant == 2 ? 128 * 1024 : 64 * 1024);
+    int epb = (int)std::max<size_t>(1, target / per);
     const long long want = std::max(1LL, m.nelem / (2LL * sm_count()));
     if (epb > want) epb = (int)want;
     if (epb > 64) epb = 64;
@@ -67,30 +69,10 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
 
 }  // namespace
 
-template <int DIM>
-cudaError_t apply64_dim(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* G,
-                        double alpha, cudaStream_t s) {
-  return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
-    constexpr int N = decltype(nc)::value;
-    using C = Apply64Cfg<DIM, N>;
-    auto kern = k_apply64<DIM, N>;
-    cudaError_t e = ensure_smem(kern, C::smem);
-    if (e != cudaSuccess) return e;
-    const long long blocks = (m.nelem + C::NEG - 1) / C::NEG;
-    if (blocks == 0) return cudaSuccess;
-    kern<<<(unsigned)blocks, C::GT, C::smem, s>>>(x, y, G, m, make_tab<N, double>(b), alpha);
-    return counted(cudaGetLastError());
-  });
-}
-
-cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
-                             const double* G, double alpha, cudaStream_t s) {
-  return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, s) : apply64_dim<2>(m, b, x, y, G, alpha, s);
-}
-
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
-                             const float* G, float alpha, int* err, cudaStream_t s) {
-  return m.dim == 3 ? apply32_dim<3>(m, b, x, y, G, alpha, err, s) : apply32_dim<2>(m, b, x, y, G, alpha, err, s);
+                             const float* G, float alpha, int* err, cudaStream_t s, int variant) {
+  return m.dim == 3 ? apply32_dim<3>(m, b, x, y, G, alpha, err, variant, s)
+                    : apply32_dim<2>(m, b, x, y, G, alpha, err, variant, s);
 }
 
 }  // namespace hmg
