@@ -495,6 +495,55 @@ def run_serve(args):
     return 0
 
 
+def paper_table_counts(tab, p, key):
+    """Iteration count of one cell of the paper's Table 1 (2d-const) / Table 4 (3d-const) from the
+    GPU solver: unit square/cube, mu = 1, three meshes, (3,3) smoothing, seeded U(-1,1) load."""
+    import torch
+
+    import synth
+    from paper_1402_5938_gb300 import Problem
+    mode, smoother, hier = key.split()
+    dim, nelem = (2, 32) if tab == "table1_2d_const" else (3, 8)
+    prob = synth.problem(dim, nelem, p, hier=hier, smoother=smoother, nu_pre=3, nu_post=3)
+    P = Problem(prob)
+    N = P.ndof(0)
+    b = torch.zeros(N, dtype=torch.float64, device="cuda")
+    P.rhs(torch.from_numpy(synth.nodal_field(7, N)).cuda(), b)
+    u = torch.zeros_like(b)
+    st, it, _ = P.solve(mode.lower(), b, u, rtol=1e-8, maxit=500)
+    P.close()
+    return it if st == 0 else None
+
+
+def run_paper_tables(args):
+    """Tables 1 and 4 of the paper (point-smoother columns) recomputed on the GPU; prints a
+    markdown table (GPU count / paper count) and one JSON summary line."""
+    import __graft_entry__
+    __graft_entry__.build()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")))
+    keys = ["MG jacobi h", "MG jacobi p", "MG cheb h", "MG cheb p",
+            "PCG jacobi h", "PCG jacobi p", "PCG cheb h", "PCG cheb p"]
+    worst, cells = 0, 0
+    for tab in ("table1_2d_const", "table4_3d_const"):
+        print(f"\n{tab} (GPU / paper)\n")
+        print("| p | " + " | ".join(keys) + " |")
+        print("|---" * (len(keys) + 1) + "|")
+        for p in (1, 2, 3, 4, 5, 6, 7, 8, 16):
+            row = []
+            for key in keys:
+                ref = gold[tab][key].get(str(p))
+                if ref is None or (p == 16 and key.endswith(" h")):
+                    row.append("" if ref is None else f"n/a / {ref}")
+                    continue
+                it = paper_table_counts(tab, p, key)
+                row.append(f"{it} / {ref}")
+                worst = max(worst, abs((it if it is not None else 10 ** 6) - ref))
+                cells += 1
+            print(f"| {p} | " + " | ".join(row) + " |", flush=True)
+    print(json.dumps({"paper_tables": "Tables 1 and 4", "cells": cells, "max_abs_diff": worst}), flush=True)
+    return 0
+
+
 def run_profile_apply(args):
     """Small fixed launch sequence for ncu: build the hierarchy of the warped var-coef problem
     (--mesh elements per axis, --order p, p-multigrid), then two applies on each of the three
@@ -533,6 +582,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
     ap.add_argument("--sweep", action="store_true", help="order sweep at ~2M DOF, FP64 vs mixed precision")
+    ap.add_argument("--paper-tables", action="store_true", help="the paper's Tables 1 and 4 recomputed on the GPU")
     ap.add_argument("--batched", action="store_true", help="512-solve batched workload vs FP64 one at a time")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="Poisson-arrival serving workload")
@@ -546,6 +596,8 @@ def main():
         return run_sweep(args)
     if args.batched:
         return run_batched(args)
+    if args.paper_tables:
+        return run_paper_tables(args)
     if args.serve:
         return run_serve(args)
     if args.profile_apply:
