@@ -368,9 +368,12 @@ hmg_status restrict_(ProblemImpl& P, int k, const T* rf, T* rc, cudaStream_t s) 
   return HMG_OK;
 }
 
-// `steps` smoothing steps on level k. zero: x is taken as 0 on input.
+// `steps` smoothing steps on level k. zero: x is taken as 0 on input. Each step's residual
+// r = b - A x is formed by the apply into r holding b; the update kernel of one step writes
+// r = b for the next step (no separate copy). With leave_r_b, r = b on return.
 template <typename T>
-hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero, cudaStream_t s) {
+hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero, cudaStream_t s,
+                  bool leave_r_b = false) {
   Level& l = P.L[k];
   const hmg_desc& D = P.desc;
   const long long n = l.m.N;
@@ -379,18 +382,25 @@ hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero,
   const T* dinv = Acc<T>::dinv(l);
   if (steps <= 0) {
     if (zero) TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+    if (leave_r_b) TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return HMG_OK;
   }
+  bool r_is_b = false;
+  auto residual = [&]() -> hmg_status {
+    if (!r_is_b) TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    return apply_level(P, k, x, r, (T)-1, s);
+  };
   if (D.smoother == HMG_SMOOTH_JACOBI) {
     const T w = (T)D.omega;
     for (int st = 0; st < steps; ++st) {
+      const bool reset = st + 1 < steps || leave_r_b;
       if (st == 0 && zero) {
-        TRY(jacobi_first<T>(x, b, dinv, n, w, s));
+        TRY(jacobi_first<T>(x, b, dinv, n, w, s, reset ? r : nullptr));
       } else {
-        TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        CHECK(apply_level(P, k, x, r, (T)-1, s));
-        TRY(jacobi_step<T>(x, r, b, dinv, n, w, 0, s));
+        CHECK(residual());
+        TRY(jacobi_step<T>(x, r, b, dinv, n, w, reset ? 1 : 0, s));
       }
+      r_is_b = reset;
     }
     return HMG_OK;
   }
@@ -400,21 +410,21 @@ hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero,
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   for (int st = 0; st < steps; ++st) {
+    const bool reset = st + 1 < steps || leave_r_b;
     if (st == 0) {
       if (zero) {
-        TRY(cheb_first<T>(x, d, b, dinv, n, (T)(1.0 / theta), s));
+        TRY(cheb_first<T>(x, d, b, dinv, n, (T)(1.0 / theta), s, reset ? r : nullptr));
       } else {
-        TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        CHECK(apply_level(P, k, x, r, (T)-1, s));
-        TRY(cheb_step<T>(x, d, r, b, dinv, n, (T)0, (T)(1.0 / theta), 0, s));
+        CHECK(residual());
+        TRY(cheb_step<T>(x, d, r, b, dinv, n, (T)0, (T)(1.0 / theta), reset ? 1 : 0, s));
       }
-      continue;
+    } else {
+      CHECK(residual());
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      TRY(cheb_step<T>(x, d, r, b, dinv, n, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), reset ? 1 : 0, s));
+      rho = rho_new;
     }
-    TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    CHECK(apply_level(P, k, x, r, (T)-1, s));
-    const double rho_new = 1.0 / (2.0 * sigma - rho);
-    TRY(cheb_step<T>(x, d, r, b, dinv, n, (T)(rho_new * rho), (T)(2.0 * rho_new / delta), 0, s));
-    rho = rho_new;
+    r_is_b = reset;
   }
   return HMG_OK;
 }
@@ -441,8 +451,7 @@ hmg_status vcycle(ProblemImpl& P, int k, const T* b, T* x, bool zero, cudaStream
   Level& c = P.L[k + 1];
   const long long n = l.m.N;
   T* r = Acc<T>::r(l);
-  CHECK(smooth<T>(P, k, b, x, P.desc.nu_pre, zero, s));
-  TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CHECK(smooth<T>(P, k, b, x, P.desc.nu_pre, zero, s, true));  // leaves r = b
   CHECK(apply_level(P, k, x, r, (T)-1, s));
   CHECK(restrict_<T>(P, k, r, Acc<T>::b(c), s));
   CHECK(vcycle<T>(P, k + 1, Acc<T>::b(c), Acc<T>::x(c), true, s));

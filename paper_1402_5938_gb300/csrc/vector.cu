@@ -91,9 +91,12 @@ __global__ void k_pcg_dir(double* __restrict__ p, const double* __restrict__ z, 
 
 template <typename T>
 __global__ void k_jacobi_first(T* __restrict__ x, const T* __restrict__ b, const T* __restrict__ dinv, long long n,
-                               T omega) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    x[i] = omega * dinv[i] * b[i];
+                               T omega, T* __restrict__ r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T bi = b[i];
+    x[i] = omega * dinv[i] * bi;
+    if (r) r[i] = bi;
+  }
 }
 
 template <typename T>
@@ -107,11 +110,13 @@ __global__ void k_jacobi(T* __restrict__ x, T* __restrict__ r, const T* __restri
 
 template <typename T>
 __global__ void k_cheb_first(T* __restrict__ x, T* __restrict__ d, const T* __restrict__ b,
-                             const T* __restrict__ dinv, long long n, T inv_theta) {
+                             const T* __restrict__ dinv, long long n, T inv_theta, T* __restrict__ r) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const T v = dinv[i] * b[i] * inv_theta;
+    const T bi = b[i];
+    const T v = dinv[i] * bi * inv_theta;
     d[i] = v;
     x[i] = v;
+    if (r) r[i] = bi;
   }
 }
 
@@ -371,8 +376,8 @@ cudaError_t pcg_direction(double* p, const double* z, long long n, const double*
 }
 
 template <typename T>
-cudaError_t jacobi_first(T* x, const T* b, const T* dinv, long long n, T omega, cudaStream_t s) {
-  k_jacobi_first<T><<<grid_for(n), kThreads, 0, s>>>(x, b, dinv, n, omega);
+cudaError_t jacobi_first(T* x, const T* b, const T* dinv, long long n, T omega, cudaStream_t s, T* r) {
+  k_jacobi_first<T><<<grid_for(n), kThreads, 0, s>>>(x, b, dinv, n, omega, r);
   return counted(cudaGetLastError());
 }
 template <typename T>
@@ -381,8 +386,8 @@ cudaError_t jacobi_step(T* x, T* r, const T* b, const T* dinv, long long n, T om
   return counted(cudaGetLastError());
 }
 template <typename T>
-cudaError_t cheb_first(T* x, T* d, const T* b, const T* dinv, long long n, T inv_theta, cudaStream_t s) {
-  k_cheb_first<T><<<grid_for(n), kThreads, 0, s>>>(x, d, b, dinv, n, inv_theta);
+cudaError_t cheb_first(T* x, T* d, const T* b, const T* dinv, long long n, T inv_theta, cudaStream_t s, T* r) {
+  k_cheb_first<T><<<grid_for(n), kThreads, 0, s>>>(x, d, b, dinv, n, inv_theta, r);
   return counted(cudaGetLastError());
 }
 template <typename T>
@@ -391,15 +396,17 @@ cudaError_t cheb_step(T* x, T* d, T* r, const T* b, const T* dinv, long long n, 
   k_cheb<T><<<grid_for(n), kThreads, 0, s>>>(x, d, r, b, dinv, n, c1, c2, reset);
   return counted(cudaGetLastError());
 }
-template cudaError_t jacobi_first<double>(double*, const double*, const double*, long long, double, cudaStream_t);
-template cudaError_t jacobi_first<float>(float*, const float*, const float*, long long, float, cudaStream_t);
+template cudaError_t jacobi_first<double>(double*, const double*, const double*, long long, double, cudaStream_t,
+                                          double*);
+template cudaError_t jacobi_first<float>(float*, const float*, const float*, long long, float, cudaStream_t, float*);
 template cudaError_t jacobi_step<double>(double*, double*, const double*, const double*, long long, double, int,
                                          cudaStream_t);
 template cudaError_t jacobi_step<float>(float*, float*, const float*, const float*, long long, float, int,
                                         cudaStream_t);
 template cudaError_t cheb_first<double>(double*, double*, const double*, const double*, long long, double,
-                                        cudaStream_t);
-template cudaError_t cheb_first<float>(float*, float*, const float*, const float*, long long, float, cudaStream_t);
+                                        cudaStream_t, double*);
+template cudaError_t cheb_first<float>(float*, float*, const float*, const float*, long long, float, cudaStream_t,
+                                       float*);
 template cudaError_t cheb_step<double>(double*, double*, double*, const double*, const double*, long long, double,
                                        double, int, cudaStream_t);
 template cudaError_t cheb_step<float>(float*, float*, float*, const float*, const float*, long long, float, float,

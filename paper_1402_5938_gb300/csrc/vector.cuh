@@ -47,14 +47,16 @@ cudaError_t pcg_update(double* u, double* r, const double* p, const double* h, l
 // p = z + S_BETA * p
 cudaError_t pcg_direction(double* p, const double* z, long long n, const double* S, cudaStream_t s);
 
-// smoother updates (T = double or float)
+// smoother updates (T = double or float); `r` (nullable) / reset_r also write r = b for the next
+// residual apply
 template <typename T>
-cudaError_t jacobi_first(T* x, const T* b, const T* dinv, long long n, T omega, cudaStream_t s);
+cudaError_t jacobi_first(T* x, const T* b, const T* dinv, long long n, T omega, cudaStream_t s, T* r = nullptr);
 template <typename T>
 cudaError_t jacobi_step(T* x, T* r, const T* b, const T* dinv, long long n, T omega, int reset_r,
                         cudaStream_t s);
 template <typename T>
-cudaError_t cheb_first(T* x, T* d, const T* b, const T* dinv, long long n, T inv_theta, cudaStream_t s);
+cudaError_t cheb_first(T* x, T* d, const T* b, const T* dinv, long long n, T inv_theta, cudaStream_t s,
+                       T* r = nullptr);
 template <typename T>
 cudaError_t cheb_step(T* x, T* d, T* r, const T* b, const T* dinv, long long n, T c1, T c2, int reset_r,
                       cudaStream_t s);
