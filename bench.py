@@ -104,6 +104,38 @@ def cpu_baseline(hier):
     return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
 
 
+def solve_roofline_ms(P, iters, hbm_gbs, fp64_tflops, nu=(3, 3)):
+    """Roofline time of one PCG + V-cycle solve (Sec. 4.2 cost model made explicit): every FP64
+    apply at max(flops / FP64 peak, bytes / HBM), plus the smoother updates (8 vectors per
+    step), residual copies, transfers and PCG vector work at HBM speed, and the dense
+    coarsest GEMV. PCG with `iters` iterations runs `iters` V-cycles and `iters` extra
+    finest-level applies."""
+    L = P.nlevels()
+    v = (nu[0] - 1) + 1 + nu[1]
+    t = 0.0
+    for k in range(L):
+        E3, p, N = P.level_info(k)
+        dim = 3 if E3[2] > 1 or P.desc.dim == 3 else 2
+        n = p + 1
+        E = E3[0] * E3[1] * E3[2]
+        flops = E * ((24 * n ** 4 + 15 * n ** 3) if dim == 3 else (16 * n ** 3 + 6 * n ** 2))
+        nc = 6 if dim == 3 else 3
+        byts = E * n ** dim * nc * 8 + 16 * N
+        t_apply = max(flops / (fp64_tflops * 1e12), byts / (hbm_gbs * 1e9))
+        if k == L - 1:                                   # dense coarsest: one GEMV per V-cycle
+            nI = 1
+            for a in range(dim):
+                nI *= max(0, E3[a] * p - 1)
+            t += iters * (nI * nI * 8) / (hbm_gbs * 1e9)
+            continue
+        applies = iters * v + (iters if k == 0 else 0)
+        vec = iters * (nu[0] + nu[1]) * 8 * 8 * N + iters * 6 * 8 * N   # smoother updates, copies, transfers
+        if k == 0:
+            vec += iters * 13 * 8 * N                     # PCG: update, dots, direction
+        t += applies * t_apply + vec / (hbm_gbs * 1e9)
+    return t * 1e3
+
+
 # ------------------------------------------------------------------ multi-rank aggregation
 def aggregate_ranks(t_step_ms, dof_per_rank, world, dist=None, device=None):
     """Replicas: every rank solves its own copy; the job's time per step is the slowest rank's
@@ -261,6 +293,9 @@ def run_gpu(args):
     eg.record(stream)
     torch.cuda.synchronize()
     apply_ms = (ea.elapsed_time(eb) - ef.elapsed_time(eg)) / reps
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    roof_ms = solve_roofline_ms(P, its[-1], hbm, FP64_PEAK_TFLOPS)
     (E3, p, _) = P.level_info(0)
     n = p + 1
     E = E3[0] * E3[1] * E3[2]
@@ -283,6 +318,9 @@ def run_gpu(args):
                          "kernel": f"k_apply64<3,{n}>",
                          "note": "FP64 pipe; peak = 152 SM x 2.07 GHz x 4 flop/clk (nominal); "
                                  "algorithmic flops 24n^4+15n^3 per element"},
+            "solve_roofline": {"roofline_ms": roof_ms, "measured_ms": t_step, "frac": roof_ms / t_step,
+                               "model": "every apply at max(flops/FP64 peak, bytes/HBM) + vector passes and "
+                                        "coarsest GEMV at HBM (HBM peak from MEASURED_PEAKS.json)"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
             "gpu_launches": launches,

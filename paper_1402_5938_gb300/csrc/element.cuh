@@ -290,16 +290,18 @@ k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __res
 // Buffers (4 per element tile): cur/nxt ping-pong for the B and B^T passes, and the
 // reference gradient (V0 in the free ping-pong buffer, V1, V2).
 // ---------------------------------------------------------------------------------------
-// Block shapes of the FP64 apply: variant V in {0,1,2} of (elements per block NEG, threads GT).
+// Block shapes of the FP64 apply: variant V in {0,1,2} of (elements per block NEG, threads GT);
+// V = 3 is V = 2's shape with the geometric factors staged in shared memory by TMA.
 // Low orders vary the elements per block (one warp's worth, ~128 or ~512 points); high orders
 // keep one element per block and vary the threads. Setup times the variants on each level
 // and keeps the fastest (see tune_apply in hmg.cu).
 constexpr int apply64_gt_rule(int w) { return w <= 512 ? 32 : (w <= 1000 ? 64 : (w <= 2200 ? 128 : (w <= 3400 ? 256 : 512))); }
 constexpr int apply64_neg(int np, int v) {
-  return np >= 100 ? 1 : ((v == 0 ? 32 : (v == 1 ? 128 : 512)) / np > 1 ? (v == 0 ? 32 : (v == 1 ? 128 : 512)) / np : 1);
+  return v == 3 ? apply64_neg(np, 2)   // variant 3: the shape of variant 2 with G staged by TMA
+                : (np >= 100 ? 1 : ((v == 0 ? 32 : (v == 1 ? 128 : 512)) / np > 1 ? (v == 0 ? 32 : (v == 1 ? 128 : 512)) / np : 1));
 }
 constexpr int apply64_gt(int np, int v) {
-  return np < 100 ? apply64_gt_rule(apply64_neg(np, v) * np)
+  return v == 3 ? apply64_gt(np, 2) : np < 100 ? apply64_gt_rule(apply64_neg(np, v) * np)
                   : (v == 0 ? apply64_gt_rule(np)
                             : (v == 1 ? (2 * apply64_gt_rule(np) > 512 ? 512 : 2 * apply64_gt_rule(np))
                                       : (apply64_gt_rule(np) >= 64 ? apply64_gt_rule(np) / 2 : 4 * apply64_gt_rule(np))));
@@ -308,10 +310,19 @@ constexpr int apply64_gt(int np, int v) {
 template <int DIM, int N, int V>
 struct Apply64Cfg {
   static constexpr int NP = Sh<DIM, N>::NP;
+  static constexpr int NC = Sh<DIM, N>::NC;
   static constexpr int NEG = apply64_neg(NP, V);
   static constexpr int W = NEG * NP;
   static constexpr int GT = apply64_gt(NP, V);
-  static constexpr size_t smem = (size_t)(2 * N * N + (DIM + 1) * W) * sizeof(double) + NEG * 16;
+  // shared-memory layout (16-byte aligned regions): [mbarrier, flag | 16 B] [B, D tables]
+  // [4 tiles of W] [element bases, face bits] [G slab of NEG elements + 16 B alignment slack]
+  static constexpr size_t base_bytes = ((16 + (size_t)(2 * N * N + (DIM + 1) * W) * 8 + NEG * 16) + 15) & ~(size_t)15;
+  static constexpr size_t gslab = (((size_t)W * NC * 8 + 16) + 15) & ~(size_t)15;
+  // Variant 3 stages G with a bulk TMA copy that overlaps the gather and interpolation phases.
+  // The kernel is FP64-pipe bound, so staging trades occupancy for load latency; the autotuner
+  // keeps it only where it measures faster.
+  static constexpr bool STAGE = V == 3 && base_bytes + gslab <= 200 * 1024;
+  static constexpr size_t smem = base_bytes + (STAGE ? gslab : 0);
 };
 
 // sum_m M(idx, m) src[base + m*stride]  (TRN: M[m*N + idx], else M[idx*N + m])
@@ -327,12 +338,28 @@ __device__ __forceinline__ double pt_dot(const double* __restrict__ M, const dou
 template <int DIM, int N, int V>
 __global__ void __launch_bounds__(Apply64Cfg<DIM, N, V>::GT)
 k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ G, const Mesh m,
-          const __grid_constant__ Tab<N, double> tab, const double alpha) {
+          const __grid_constant__ Tab<N, double> tab, const double alpha, int* __restrict__ err) {
   using C = Apply64Cfg<DIM, N, V>;
   constexpr int NP = C::NP, NEG = C::NEG, W = C::W, NC = Sh<DIM, N>::NC;
   constexpr int S1 = N, S2 = N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sB = reinterpret_cast<double*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  int* sflag = reinterpret_cast<int*>(smem_raw + 8);
+  const long long e0g = (long long)blockIdx.x * NEG;
+  const int neg = (int)min((long long)NEG, m.nelem - e0g);
+  int goff = 0;  // byte offset of the staged slab above its 16-byte boundary
+  unsigned char* gstage = smem_raw + C::base_bytes;
+  if (C::STAGE) {
+    const char* p = reinterpret_cast<const char*>(G + e0g * NC * NP);
+    goff = (int)(reinterpret_cast<uintptr_t>(p) & 15);
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_init_fence();
+      const uint32_t bytes = (uint32_t)(((long long)neg * NC * NP * 8 + goff + 15) & ~15LL);
+      bulk_g2s(gstage, p - goff, bytes, bar);
+    }
+  }
+  double* sB = reinterpret_cast<double*>(smem_raw + 16);
   double* sD = sB + N * N;
   double* T0 = sD + N * N;
   double* T1 = T0 + W;
@@ -340,8 +367,8 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
   double* V2 = V1 + W;  // 3D only
   long long* ebase = reinterpret_cast<long long*>(T0 + (DIM + 1) * W);
   int* eflag = reinterpret_cast<int*>(ebase + NEG);
-  const long long e0 = (long long)blockIdx.x * NEG;
-  const int ne = (int)min((long long)NEG, m.nelem - e0);
+  const long long e0 = e0g;
+  const int ne = neg;
   const int nt = ne * NP;
   for (int t = threadIdx.x; t < N * N; t += blockDim.x) {
     sB[t] = tab.B[t];
@@ -386,6 +413,16 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
   // collocated reference gradient and the pointwise geometric factor
   double* V0 = nxt;
   const double* Gb = G + e0 * NC * NP;
+  if (C::STAGE) {  // the slab's bulk copy: thread 0 waits with a limit, then all observe the phase
+    if (threadIdx.x == 0) *sflag = mbar_wait(bar, 0, kWaitPolls) ? 0 : 1;
+    __syncthreads();
+    if (*sflag) {
+      if (threadIdx.x == 0) atomicExch(err, kErrTmaTimeout);
+      return;
+    }
+    mbar_wait(bar, 0, kWaitPolls);
+    Gb = reinterpret_cast<const double*>(gstage + goff);
+  }
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     const int a = t % NP;
     const int i = a % N, j = (a / N) % N;

@@ -320,7 +320,7 @@ template <> struct Acc<float> {
 hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, s, l.v64));
+  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, P.err, s, l.v64));
   return HMG_OK;
 }
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
@@ -504,7 +504,7 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
     for (int j = 0; j < m; ++j) {
       double* w = V[j + 1];
       TRY(cudaMemsetAsync(w, 0, n * sizeof(double), s));
-      TRY(launch_apply_f64(l.m, l.basis, V[j], w, l.G, 1.0, s, l.v64));
+      TRY(launch_apply_f64(l.m, l.basis, V[j], w, l.G, 1.0, P.err, s, l.v64));
       TRY(scale_by(w, l.dinv, n, s));
       for (int i = 0; i <= j; ++i) {
         TRY(dot_partial(w, V[i], n, P.partial, s));
@@ -527,7 +527,7 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
 }
 
 // ---- autotuning of the apply block shape -------------------------------------------------
-// For each level, time the kernel variants (kApplyVariants block shapes) with CUDA events on the
+// For each level, time the kernel variants (block shapes, and for FP64 TMA staging) with CUDA events on the
 // level's own buffers and keep the fastest; results are cached per (device, dim, order, element
 // count, precision) for the process. HMG_AUTOTUNE=0 in the environment keeps variant 0.
 bool autotune_on() {
@@ -561,10 +561,10 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     float best = 1e30f;
     int bv = 0;
     cudaError_t err = cudaSuccess;
-    for (int v = 0; v < kApplyVariants && err == cudaSuccess; ++v) {
+    for (int v = 0; v < (prec ? kApply32Variants : kApply64Variants) && err == cudaSuccess; ++v) {
       auto run = [&]() {
         return prec ? launch_apply_f32(l.m, l.basis, l.x32, l.r32, l.G32, 1.0f, P.err, s, v)
-                    : launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, s, v);
+                    : launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v);
       };
       if ((err = run()) != cudaSuccess) break;  // warm-up (also opts the kernel into its smem)
       if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
@@ -675,7 +675,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       Level& l = P.L[k];
       const long long n = l.m.N;
       const long long gsz = l.m.nelem * np_of(l.m);
-      TRY(P.alloc((void**)&l.G, gsz * nc_of(D.dim) * sizeof(double)));
+      TRY(P.alloc((void**)&l.G, gsz * nc_of(D.dim) * sizeof(double) + 256));  // TMA tail padding
       TRY(P.alloc((void**)&l.wdetJ, gsz * sizeof(double)));
       TRY(P.alloc((void**)&l.dinv, n * sizeof(double)));
       TRY(P.alloc((void**)&l.b, n * sizeof(double)));
@@ -910,7 +910,7 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   for (size_t k = 0; k < ms.size(); ++k) {
     const Mesh& m = ms[k];
     const size_t gsz = (size_t)(m.nelem * np_of(m)), n = (size_t)m.N;
-    add(gsz * nc_of(D.dim) * 8); add(gsz * 8);
+    add(gsz * nc_of(D.dim) * 8 + 256); add(gsz * 8);
     for (int v = 0; v < 5; ++v) add(n * 8);
     if (mixed) { add(gsz * nc_of(D.dim) * 4 + 256); for (int v = 0; v < 5; ++v) add(n * 4); }
     max_stage = std::max(max_stage, gsz * D.dim * (D.dim + 1) * 8);

@@ -6,13 +6,15 @@
 
 namespace hmg {
 
-// y += alpha * A x (FP64 or FP32 data; G in the same precision). The FP32 kernel stages G
-// with bulk TMA copies and needs G allocated with >= 16 bytes of tail padding; a timed-out
-// wait sets *err (device int) to a nonzero code.
-// `variant` (0..2) selects the block shape; setup picks it per level by timing (autotuning).
-constexpr int kApplyVariants = 3;
+// y += alpha * A x (FP64 or FP32 data; G in the same precision). Both kernels stage G with
+// bulk TMA copies (FP64: when the slab fits in shared memory) and need G allocated with >= 16
+// bytes of tail padding; a timed-out wait sets *err (device int) to a nonzero code.
+// `variant` selects the block shape (FP64: 0..3, 3 = TMA-staged G; FP32: 0..2 tile sizes); setup
+// picks it per level by timing (autotuning).
+constexpr int kApply64Variants = 4;
+constexpr int kApply32Variants = 3;
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
-                             const double* G, double alpha, cudaStream_t s, int variant = 0);
+                             const double* G, double alpha, int* err, cudaStream_t s, int variant = 0);
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
                              const float* G, float alpha, int* err, cudaStream_t s, int variant = 0);
 

@@ -8,26 +8,27 @@ namespace {
 
 template <int DIM, int N, int V>
 cudaError_t apply64_variant(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* G,
-                            double alpha, cudaStream_t s) {
+                            double alpha, int* err, cudaStream_t s) {
   using C = Apply64Cfg<DIM, N, V>;
   auto kern = k_apply64<DIM, N, V>;
   cudaError_t e = ensure_smem(kern, C::smem);
   if (e != cudaSuccess) return e;
   const long long blocks = (m.nelem + C::NEG - 1) / C::NEG;
   if (blocks == 0) return cudaSuccess;
-  kern<<<(unsigned)blocks, C::GT, C::smem, s>>>(x, y, G, m, make_tab<N, double>(b), alpha);
+  kern<<<(unsigned)blocks, C::GT, C::smem, s>>>(x, y, G, m, make_tab<N, double>(b), alpha, err);
   return counted(cudaGetLastError());
 }
 
 template <int DIM>
 cudaError_t apply64_dim(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* G,
-                        double alpha, int variant, cudaStream_t s) {
+                        double alpha, int* err, int variant, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
     switch (variant) {
-      case 1: return apply64_variant<DIM, N, 1>(m, b, x, y, G, alpha, s);
-      case 2: return apply64_variant<DIM, N, 2>(m, b, x, y, G, alpha, s);
-      default: return apply64_variant<DIM, N, 0>(m, b, x, y, G, alpha, s);
+      case 1: return apply64_variant<DIM, N, 1>(m, b, x, y, G, alpha, err, s);
+      case 2: return apply64_variant<DIM, N, 2>(m, b, x, y, G, alpha, err, s);
+      case 3: return apply64_variant<DIM, N, 3>(m, b, x, y, G, alpha, err, s);
+      default: return apply64_variant<DIM, N, 0>(m, b, x, y, G, alpha, err, s);
     }
   });
 }
@@ -35,9 +36,9 @@ cudaError_t apply64_dim(const Mesh& m, const Basis1D& b, const double* x, double
 }  // namespace
 
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
-                             const double* G, double alpha, cudaStream_t s, int variant) {
-  return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, variant, s)
-                    : apply64_dim<2>(m, b, x, y, G, alpha, variant, s);
+                             const double* G, double alpha, int* err, cudaStream_t s, int variant) {
+  return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, err, variant, s)
+                    : apply64_dim<2>(m, b, x, y, G, alpha, err, variant, s);
 }
 
 }  // namespace hmg
