@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <map>
 #include <tuple>
 #include <mutex>
@@ -125,6 +126,10 @@ struct ProblemImpl {
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   long long gkern[2][3] = {};  // kernel nodes per graph section: prologue, loop body (part 1), PCG part 2
+  // lockstep graphs of batched solves (no conditional nodes, so different problems overlap):
+  // [mode][0] prologue, [mode][1] first iteration half (PCG), [mode][2] one iteration
+  cudaGraphExec_t lexec[2][3] = {};
+  long long lkern[2][3] = {};
   bool capturing = false;
 
   // Device allocation zeroed in order on the setup stream (the caller's stream may be a
@@ -143,6 +148,8 @@ struct ProblemImpl {
     for (int m = 0; m < 2; ++m) {
       if (gexec[m]) cudaGraphExecDestroy(gexec[m]);
       if (graph[m]) cudaGraphDestroy(graph[m]);
+      for (int k = 0; k < 3; ++k)
+        if (lexec[m][k]) cudaGraphExecDestroy(lexec[m][k]);
     }
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : dev_allocs) cudaFree(p);
@@ -475,7 +482,7 @@ hmg_status precondition(ProblemImpl& P, const double* r, double* z, cudaStream_t
 hmg_status dot_to(ProblemImpl& P, const double* x, const double* y, long long n, int op, int idx, int aux,
                   bool to_host, cudaStream_t s) {
   TRY(dot_partial(x, y, n, P.partial, s));
-  TRY(finish(P.partial, P.S, op, idx, aux, to_host ? P.hostS : nullptr, s));
+  TRY(finish(P.partial, n, P.S, op, idx, aux, to_host ? P.hostS : nullptr, s));
   return HMG_OK;
 }
 
@@ -499,7 +506,7 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
     const unsigned long long seed = (P.desc.arnoldi_seed ? P.desc.arnoldi_seed : 0x1402593800000000ull) + (unsigned long long)k;
     TRY(start_vector(V[0], l.m, seed, s));
     TRY(dot_partial(V[0], V[0], n, P.partial, s));
-    TRY(finish(P.partial, P.S, FIN_SQRT, S_TMP, 0, nullptr, s));
+    TRY(finish(P.partial, n, P.S, FIN_SQRT, S_TMP, 0, nullptr, s));
     TRY(div_dev(V[0], V[0], n, P.S + S_TMP, s));
     for (int j = 0; j < m; ++j) {
       double* w = V[j + 1];
@@ -508,11 +515,11 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
       TRY(scale_by(w, l.dinv, n, s));
       for (int i = 0; i <= j; ++i) {
         TRY(dot_partial(w, V[i], n, P.partial, s));
-        TRY(finish(P.partial, Hd, FIN_STORE, i * m + j, 0, nullptr, s));
+        TRY(finish(P.partial, n, Hd, FIN_STORE, i * m + j, 0, nullptr, s));
         TRY(axpy_dev(w, V[i], n, Hd + i * m + j, -1.0, s));
       }
       TRY(dot_partial(w, w, n, P.partial, s));
-      TRY(finish(P.partial, Hd, FIN_SQRT, (j + 1) * m + j, 0, nullptr, s));
+      TRY(finish(P.partial, n, Hd, FIN_SQRT, (j + 1) * m + j, 0, nullptr, s));
       if (j + 1 < m) TRY(div_dev(w, w, n, Hd + (j + 1) * m + j, s));
     }
     std::vector<double> H((m + 1) * m);
@@ -833,7 +840,7 @@ hmg_status build_graph(ProblemImpl& P, int mode, int cap) {
         CHECK(apply_level(P, 0, P.pp, P.ph, 1.0, s));
         CHECK(dot_to(P, P.pp, P.ph, n, FIN_STORE, S_PH, 0, false, s));
         TRY(pcg_update(P.gu, r, P.pp, P.ph, n, P.S, P.partial, s));
-        TRY(finish(P.partial, P.S, FIN_STORE, S_RR, 0, nullptr, s));
+        TRY(finish(P.partial, n, P.S, FIN_STORE, S_RR, 0, nullptr, s));
         TRY(step_check(P.S, P.ctrl, P.hist, hw, hi, 1, s));
         return HMG_OK;
       }, &l1));
@@ -860,6 +867,82 @@ hmg_status build_graph(ProblemImpl& P, int mode, int cap) {
   P.capturing = false;
   if (st != HMG_OK) cudaGraphDestroy(g);
   return st;
+}
+
+// ---- lockstep graphs for batched solves ----------------------------------------------------
+// Plain graphs (no conditional nodes): PCG: prologue [r = b, u = 0, ||r||, z = V(r), p = z, (z,r)],
+// half [h = A p, alpha, u, r, ||r||] and step [z = V(r), beta, p, h = A p, alpha, u, r, ||r||];
+// MG: prologue [r = b, u = 0, ||r||] and step [z = V(r), u += z, r = b - A u, ||r||]. Each ends by
+// copying ||r_0||^2 and ||r||^2 (slots S_LRR0, S_LRR) into pinned host memory; the host tests convergence between
+// launches (Algorithm 1's test position), one synchronization per step for the whole batch.
+hmg_status capture_plain(ProblemImpl& P, int mode, int k, cudaStream_t s,
+                         const std::function<hmg_status()>& fn) {
+  cudaGraph_t g = nullptr;
+  const long long c0 = add_launches(0);
+  P.capturing = true;
+  hmg_status st = HMG_OK;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = fn();
+    if (st == HMG_OK) e = cudaMemcpyAsync(P.hostS + 2, P.S + S_LRR0, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  P.capturing = false;
+  P.lkern[mode][k] = add_launches(0) - c0;
+  add_launches(-P.lkern[mode][k]);
+  if (st != HMG_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&P.lexec[mode][k], g, 0);
+  if (g) cudaGraphDestroy(g);
+  TRY(e);
+  return HMG_OK;
+}
+
+hmg_status build_lockstep(ProblemImpl& P, int mode) {
+  if (P.lexec[mode][2]) return HMG_OK;
+  if (!P.cap_stream) TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+  cudaStream_t s = P.cap_stream;
+  const long long n = P.L[0].m.N;
+  double* r = P.pr;
+  double* z = P.pz;
+  auto norm = [&]() -> hmg_status { return dot_to(P, r, r, n, FIN_STORE, S_LRR, 0, false, s); };
+  auto apply_update = [&]() -> hmg_status {
+    TRY(cudaMemsetAsync(P.ph, 0, n * sizeof(double), s));
+    CHECK(apply_level(P, 0, P.pp, P.ph, 1.0, s));
+    CHECK(dot_to(P, P.pp, P.ph, n, FIN_STORE, S_PH, 0, false, s));
+    TRY(pcg_update(P.gu, r, P.pp, P.ph, n, P.S, P.partial, s));
+    TRY(finish(P.partial, n, P.S, FIN_STORE, S_LRR, 0, nullptr, s));
+    return HMG_OK;
+  };
+  CHECK(capture_plain(P, mode, 0, s, [&]() -> hmg_status {
+    TRY(cudaMemcpyAsync(r, P.gb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(cudaMemsetAsync(P.gu, 0, n * sizeof(double), s));
+    CHECK(dot_to(P, r, r, n, FIN_STORE, S_LRR0, 0, false, s));
+    if (mode == HMG_MODE_PCG) {
+      CHECK(precondition(P, r, z, s));
+      TRY(cudaMemcpyAsync(P.pp, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CHECK(dot_to(P, z, r, n, FIN_STORE, S_RHO, 0, false, s));
+    }
+    return HMG_OK;
+  }));
+  if (mode == HMG_MODE_PCG) {
+    CHECK(capture_plain(P, mode, 1, s, [&]() -> hmg_status { return apply_update(); }));
+    CHECK(capture_plain(P, mode, 2, s, [&]() -> hmg_status {
+      CHECK(precondition(P, r, z, s));
+      CHECK(dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s));
+      TRY(pcg_direction(P.pp, z, n, P.S, s));
+      return apply_update();
+    }));
+  } else {
+    CHECK(capture_plain(P, mode, 2, s, [&]() -> hmg_status {
+      CHECK(precondition(P, r, z, s));
+      TRY(axpy(P.gu, z, n, 1.0, s));
+      TRY(cudaMemcpyAsync(r, P.gb, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CHECK(apply_level(P, 0, P.gu, r, -1.0, s));
+      return norm();
+    }));
+  }
+  return HMG_OK;
 }
 
 // Enqueue one graph solve on s (no host synchronization); results land in pinned buffers.
@@ -1210,7 +1293,7 @@ static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* 
     CHECK(apply_level(P, 0, pp, h, 1.0, s));
     CHECK(dot_to(P, pp, h, n, FIN_STORE, S_PH, 0, false, s));
     TRY(pcg_update(u, r, pp, h, n, P.S, P.partial, s));
-    TRY(finish(P.partial, P.S, FIN_STORE, S_RR, 0, P.hostS, s));
+    TRY(finish(P.partial, n, P.S, FIN_STORE, S_RR, 0, P.hostS, s));
     TRY(cudaStreamSynchronize(s));
     const double rn = sqrt(*P.hostS);
     if (res_hist) res_hist[it] = rn;
@@ -1238,14 +1321,17 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
     for (int j = 0; j < i; ++j)
       if (probs[j] == probs[i]) { set_error("a handle appears twice in the batch"); return HMG_EINVAL; }
   }
-  const int cap = std::max(maxit, 64);
-  for (int i = 0; i < n; ++i) CHECK(build_graph(probs[i]->impl, mode, cap));
-  // fan out over a pool of streams, join back on the caller's stream
+  for (int i = 0; i < n; ++i) CHECK(build_lockstep(probs[i]->impl, mode));
+  // streams in the fan-out (HMG_BATCH_STREAMS, 1..64, default 16)
+  static const int K = [] {
+    const char* v = getenv("HMG_BATCH_STREAMS");
+    const int k = v ? atoi(v) : 16;
+    return k < 1 ? 1 : (k > 64 ? 64 : k);
+  }();
   static std::mutex pool_mu;
   static std::vector<cudaStream_t> pool[64];
   int dev = 0;
   TRY(cudaGetDevice(&dev));
-  const int K = 16;
   {
     std::lock_guard<std::mutex> lk(pool_mu);
     if (dev >= 0 && dev < 64 && pool[dev].empty())
@@ -1256,29 +1342,98 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
       }
   }
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<cudaEvent_t> ev(K + 1, nullptr);
+  const int used = std::min(n, K);
+  std::vector<cudaEvent_t> ev(used + 1, nullptr);
   for (auto& e : ev) TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  hmg_status st = [&]() -> hmg_status {
-    TRY(cudaEventRecord(ev[K], s));
-    const int used = std::min(n, K);
-    for (int k = 0; k < used; ++k) TRY(cudaStreamWaitEvent(pool[dev][k], ev[K], 0));
-    for (int i = 0; i < n; ++i) CHECK(graph_solve_enqueue(probs[i]->impl, mode, b[i], u[i], rtol, maxit, pool[dev][i % K]));
-    for (int k = 0; k < used; ++k) {
-      TRY(cudaEventRecord(ev[k], pool[dev][k]));
-      TRY(cudaStreamWaitEvent(s, ev[k], 0));
+  std::vector<int> it(n, 0), st(n, 1);  // st: 1 running, 0 converged, -3 maxit, -7 nan
+  std::vector<double> r0(n, 0.0);
+  auto hist_set = [&](int i, int k, double v) { if (res_hist && res_hist[i]) res_hist[i][k] = v; };
+  // launch `k`-graphs of the problems in `which` over the pool, then join on s and synchronize
+  auto step = [&](const std::vector<int>& which, int k0, int k1) -> hmg_status {
+    TRY(cudaEventRecord(ev[used], s));
+    for (int q = 0; q < used; ++q) TRY(cudaStreamWaitEvent(pool[dev][q], ev[used], 0));
+    for (size_t w = 0; w < which.size(); ++w) {
+      const int i = which[w];
+      ProblemImpl& P = probs[i]->impl;
+      cudaStream_t si = pool[dev][i % K];
+      if (k0 == 0) {
+        TRY(copy_masked(P.gb, b[i], P.L[0].m, si));
+      }
+      for (int k = k0; k <= k1; ++k) {
+        if (!P.lexec[mode][k]) continue;
+        TRY(cudaGraphLaunch(P.lexec[mode][k], si));
+        add_launches(P.lkern[mode][k]);
+      }
+    }
+    for (int q = 0; q < used; ++q) {
+      TRY(cudaEventRecord(ev[q], pool[dev][q]));
+      TRY(cudaStreamWaitEvent(s, ev[q], 0));
+    }
+    TRY(cudaStreamSynchronize(s));
+    return HMG_OK;
+  };
+  hmg_status err = [&]() -> hmg_status {
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    // prologue (+ PCG's first half-iteration unless maxit == 0)
+    CHECK(step(all, 0, (mode == HMG_MODE_PCG && maxit > 0) ? 1 : 0));
+    std::vector<int> active;
+    auto check = [&](int i) {
+      ProblemImpl& P = probs[i]->impl;
+      const double rn = sqrt(P.hostS[3]);
+      hist_set(i, it[i], rn);
+      if (!std::isfinite(rn)) st[i] = -7;
+      else if (rn <= rtol * r0[i]) st[i] = 0;
+      else if (it[i] >= maxit) st[i] = -3;
+    };
+    for (int i = 0; i < n; ++i) {
+      ProblemImpl& P = probs[i]->impl;
+      r0[i] = sqrt(P.hostS[2]);
+      hist_set(i, 0, r0[i]);
+      if (!std::isfinite(r0[i])) { st[i] = -7; continue; }
+      if (r0[i] == 0.0) { st[i] = 0; continue; }
+      if (maxit == 0) { st[i] = -3; continue; }
+      if (mode == HMG_MODE_PCG) {
+        it[i] = 1;
+        check(i);
+      }
+      if (st[i] == 1) active.push_back(i);
+    }
+    while (!active.empty()) {
+      CHECK(step(active, 2, 2));
+      std::vector<int> next;
+      for (int i : active) {
+        ++it[i];
+        check(i);
+        if (st[i] == 1) next.push_back(i);
+      }
+      active.swap(next);
+    }
+    for (int i = 0; i < n; ++i) {
+      ProblemImpl& P = probs[i]->impl;
+      if (r0[i] == 0.0 || !std::isfinite(r0[i]) || maxit == 0)
+        TRY(cudaMemsetAsync(u[i], 0, P.L[0].m.N * sizeof(double), s));
+      else
+        TRY(cudaMemcpyAsync(u[i], P.gu, P.L[0].m.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     TRY(cudaStreamSynchronize(s));
     return HMG_OK;
   }();
   for (auto& e : ev) cudaEventDestroy(e);
-  if (st != HMG_OK) return st;
+  if (err != HMG_OK) return err;
   hmg_status first = HMG_OK;
   for (int i = 0; i < n; ++i) {
-    hmg_status si = graph_solve_finish(probs[i]->impl, mode, iters ? &iters[i] : nullptr, res_hist ? res_hist[i] : nullptr);
-    if (si == HMG_OK) si = device_error(probs[i]->impl, s);
+    ProblemImpl& P = probs[i]->impl;
+    const long long v = vcycle_fine_applies(P);
+    if (it[i] > 0) P.fine_applies += mode == HMG_MODE_MG ? (long long)it[i] * (v + 1) : v + it[i] + (long long)(it[i] - 1) * v;
+    hmg_status si = st[i] == 0 ? HMG_OK : (st[i] == -3 ? HMG_ENOCONV : HMG_ENAN);
+    if (si == HMG_OK) si = device_error(P, s);
+    if (iters) iters[i] = it[i];
     if (status) status[i] = si;
     if (first == HMG_OK && si != HMG_OK) first = si;
   }
+  if (first == HMG_ENOCONV) set_error("maximum number of iterations reached in the batch");
+  if (first == HMG_ENAN) set_error("non-finite residual in the batch");
   return first;
 }
 

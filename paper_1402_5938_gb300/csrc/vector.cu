@@ -20,6 +20,20 @@ inline unsigned grid_for(long long n) {
   return (unsigned)g;
 }
 
+}  // namespace
+
+// Blocks of a reduction over n entries: about 4 entries per thread, at most kRedBlocks. Fixed
+// for a given n, so sums are reproducible; small vectors use few blocks and leave the GPU to
+// other streams' work.
+int red_blocks(long long n) {
+  long long b = (n + 4LL * kThreads - 1) / (4LL * kThreads);
+  if (b < 1) b = 1;
+  if (b > kRedBlocks) b = kRedBlocks;
+  return (int)b;
+}
+
+namespace {
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -51,10 +65,10 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial(const T* __restrict__ 
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ partial, double* S, int op,
-                                                     int idx, int aux) {
+__global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ partial, int np, double* S,
+                                                     int op, int idx, int aux) {
   double acc = 0.0;
-  for (int i = threadIdx.x; i < kRedBlocks; i += kThreads) acc += partial[i];
+  for (int i = threadIdx.x; i < np; i += kThreads) acc += partial[i];
   acc = block_sum(acc);
   if (threadIdx.x == 0) {
     if (op == FIN_STORE) S[idx] = acc;
@@ -70,7 +84,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(double* __restrict__ u,
                                                          const double* __restrict__ p, const double* __restrict__ h,
                                                          long long n, const double* __restrict__ S,
                                                          double* __restrict__ partial) {
-  const double alpha = S[S_RHO] / S[S_PH];
+  const double ph = S[S_PH];
+  const double alpha = ph != 0.0 ? S[S_RHO] / ph : 0.0;  // p = 0 (zero right-hand side): no step
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
     u[i] = fma(alpha, p[i], u[i]);
@@ -349,24 +364,25 @@ __global__ void k_coarse_gemv(const double* __restrict__ Ainv, const T* __restri
 }  // namespace
 
 cudaError_t dot_partial(const double* x, const double* y, long long n, double* partial, cudaStream_t s) {
-  k_dot_partial<double><<<kRedBlocks, kThreads, 0, s>>>(x, y, n, partial);
+  k_dot_partial<double><<<red_blocks(n), kThreads, 0, s>>>(x, y, n, partial);
   return counted(cudaGetLastError());
 }
 cudaError_t dot_partial_f32(const float* x, const float* y, long long n, double* partial, cudaStream_t s) {
-  k_dot_partial<float><<<kRedBlocks, kThreads, 0, s>>>(x, y, n, partial);
+  k_dot_partial<float><<<red_blocks(n), kThreads, 0, s>>>(x, y, n, partial);
   return counted(cudaGetLastError());
 }
 
-cudaError_t finish(const double* partial, double* S, int op, int idx, int aux, double* host_copy, cudaStream_t s) {
-  k_finish<<<1, kThreads, 0, s>>>(partial, S, op, idx, aux);
-  cudaError_t e = cudaGetLastError();
+cudaError_t finish(const double* partial, long long n, double* S, int op, int idx, int aux, double* host_copy,
+                   cudaStream_t s) {
+  k_finish<<<1, kThreads, 0, s>>>(partial, red_blocks(n), S, op, idx, aux);
+  cudaError_t e = counted(cudaGetLastError());
   if (e != cudaSuccess || host_copy == nullptr) return e;
   return cudaMemcpyAsync(host_copy, S + idx, sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
 cudaError_t pcg_update(double* u, double* r, const double* p, const double* h, long long n, const double* S,
                        double* partial, cudaStream_t s) {
-  k_pcg_update<<<kRedBlocks, kThreads, 0, s>>>(u, r, p, h, n, S, partial);
+  k_pcg_update<<<red_blocks(n), kThreads, 0, s>>>(u, r, p, h, n, S, partial);
   return counted(cudaGetLastError());
 }
 

@@ -15,7 +15,9 @@ enum Scalar : int {
   S_TMP = 4,    // scratch scalar (Arnoldi h_ij, norms)
   S_RR0 = 5,    // ||r_0||^2
   S_RTOL = 6,   // relative tolerance of a graph solve
-  S_COUNT = 8
+  S_LRR0 = 8,   // ||r_0||^2 of a lockstep (batched) solve
+  S_LRR = 9,    // ||r||^2 of a lockstep solve (copied to the host with S_LRR0)
+  S_COUNT = 10
 };
 
 // Device-side solve control of a graph solve: ctrl[0] iteration, ctrl[1] status, ctrl[2] maxit,
@@ -35,10 +37,11 @@ struct Axis1D {
   float* val32;      // device, nnz
 };
 
-// reductions: partial[kRedBlocks] then finish into S
+// reductions over n entries: red_blocks(n) partials, then finish into S (pass the same n)
+int red_blocks(long long n);
 cudaError_t dot_partial(const double* x, const double* y, long long n, double* partial, cudaStream_t s);
 cudaError_t dot_partial_f32(const float* x, const float* y, long long n, double* partial, cudaStream_t s);
-cudaError_t finish(const double* partial, double* S, int op, int idx, int aux, double* host_copy,
+cudaError_t finish(const double* partial, long long n, double* S, int op, int idx, int aux, double* host_copy,
                    cudaStream_t s);
 
 // PCG: alpha = S_RHO / S_PH; u += alpha p; r -= alpha h; partial <- ||r||^2

@@ -106,3 +106,37 @@ def test_batched_matches_oracle_counts(hmg):
         _, it_ref, _, ok = H.solve_pcg(H.fine.disc.rhs(f))
         assert sts[0] == 0 and ok and abs(its[0] - it_ref) <= 1
         P.close()
+
+
+@pytest.mark.parametrize("mode", ["mg", "pcg"])
+def test_batched_lockstep_edges(hmg, mode):
+    """Mixed batch: ordinary solves, a zero right-hand side (converged at iteration 0) and a
+    problem that runs out of iterations; histories agree with solving each problem alone."""
+    probs, bs = [], []
+    for i in (1, 2, 5):
+        prob, seed = synth.batched_problem(i)
+        P = hmg.Problem(prob)
+        N = P.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device=DEV)
+        P.rhs(torch.from_numpy(synth.nodal_field(seed, N)).to(DEV), b)
+        probs.append(P)
+        bs.append(b)
+    bs[1].zero_()
+    us = [torch.full_like(b, 7.0) for b in bs]
+    sts, its, hists = hmg.solve_batched(probs, mode, bs, us, rtol=1e-8, maxit=60)
+    assert sts[0] == 0 and sts[1] == 0 and its[1] == 0 and float(torch.linalg.norm(us[1])) == 0.0
+    for k in (0, 2):
+        u1 = torch.zeros_like(bs[k])
+        st1, it1, h1 = probs[k].solve(mode, bs[k], u1, rtol=1e-8, maxit=60)
+        assert st1 == sts[k] and it1 == its[k] and len(hists[k]) == its[k] + 1
+        big = [j for j in range(len(h1)) if h1[j] > 1e-6 * h1[0]]
+        assert max(abs(hists[k][j] - h1[j]) / h1[j] for j in big) < 1e-5  # FP32 V-cycle
+        assert float(torch.linalg.norm(us[k] - u1) / torch.linalg.norm(u1)) < 1e-8
+    # an iteration cap below what problem 0 needs
+    cap = max(1, its[0] - 2)
+    us = [torch.zeros_like(b) for b in bs]
+    sts, its2, hists = hmg.solve_batched(probs, mode, bs, us, rtol=1e-8, maxit=cap)
+    assert sts[0] == hmg.hmg.HMG_ENOCONV and its2[0] == cap and len(hists[0]) == cap + 1
+    assert sts[1] == 0 and its2[1] == 0
+    for P in probs:
+        P.close()
