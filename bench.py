@@ -335,9 +335,10 @@ def run_gpu(args):
 
 def run_sweep(args):
     """Order sweep at ~2M DOF (129^3 nodes; (64^3,2), (32^3,4), (16^3,8), (8^3,16)), same warp and
-    coefficient: per order the FP64 and FP32 apply times, and FP64 vs mixed-precision (FP32
-    V-cycle) PCG + p-MG time to 1e-8, iterations, and the mixed solution's relative difference
-    from the FP64 one. One JSON line per order (not the benchmark line)."""
+    coefficient: per order the FP64 apply time and the V-cycle operator's time in FP32, FP16 and
+    BF16 (tensor cores, orders <= 7), and FP64 vs mixed-precision PCG + p-MG time to 1e-8,
+    iterations, the mixed solution's FP64 residual and relative difference from the FP64 one.
+    One JSON line per order (not the benchmark line)."""
     import torch
 
     import __graft_entry__
@@ -362,34 +363,40 @@ def run_sweep(args):
     for E, p in [(64, 2), (32, 4), (16, 8), (8, 16)]:
         prob = synth.warped_var3d(E, p, hier="p")
         P64 = Problem(prob)
-        P32 = Problem(dict(prob, smooth_prec="fp32"))
         N = P64.ndof(0)
         f = torch.from_numpy(synth.nodal_field(synth.SEED_PSWEEP3D, N)).to(dev)
         b = torch.zeros(N, dtype=torch.float64, device=dev)
         P64.rhs(f, b)
-        x, y = torch.zeros_like(b), torch.zeros_like(b)
-        x32, y32 = torch.zeros(N, dtype=torch.float32, device=dev), torch.zeros(N, dtype=torch.float32, device=dev)
+        y = torch.zeros_like(b)
         t64, _ = timed(lambda: P64.apply(0, b, y), 10)
-        t32, _ = timed(lambda: P32.apply_f32(0, x32, y32), 10)
-        u64, u32 = torch.zeros_like(b), torch.zeros_like(b)
+        u64 = torch.zeros_like(b)
         s64, (_, it64, h64) = timed(lambda: P64.solve("pcg", b, u64, rtol=1e-8, maxit=500), 3)
-        s32, (_, it32, h32) = timed(lambda: P32.solve("pcg", b, u32, rtol=1e-8, maxit=500), 3)
-        P64.apply(0, u32, y)
-        res32 = float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
-        diff = float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64))
         n = p + 1
         flops = E ** 3 * (24 * n ** 4 + 15 * n ** 3)
-        print(json.dumps({
-            "sweep": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_tflops": flops / t64 / 1e9,
-            "apply_fp64_frac_of_fp64_peak": flops / t64 / 1e9 / FP64_PEAK_TFLOPS,
-            "apply_fp32_ms": t32, "apply_fp32_gdofs": N / t32 / 1e6,
-            "apply_fp32_hbm_gbs": (E ** 3 * 24 * n ** 3 + 8 * N) / t32 / 1e6,
-            "pcg_fp64_ms": s64, "pcg_fp64_iters": it64, "pcg_mixed_ms": s32, "pcg_mixed_iters": it32,
-            "mixed_speedup": s64 / s32, "mixed_final_rel_residual_fp64": res32,
-            "mixed_vs_fp64_solution_rel_diff": diff,
-            "setup_bytes_fp64": P64.device_bytes(), "setup_bytes_mixed": P32.device_bytes()}), flush=True)
+        line = {"sweep": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_tflops": flops / t64 / 1e9,
+                "apply_fp64_frac_of_fp64_peak": flops / t64 / 1e9 / FP64_PEAK_TFLOPS,
+                "pcg_fp64_ms": s64, "pcg_fp64_iters": it64, "setup_bytes_fp64": P64.device_bytes()}
+        # V-cycle precisions: FP32, and FP16 / BF16 tensor-core applies (orders <= 7) with flexible PCG
+        for prec, gbytes in (("fp32", 4), ("fp16", 2), ("bf16", 2)):
+            Pm = Problem(dict(prob, smooth_prec=prec))
+            x32, y32 = torch.zeros(N, dtype=torch.float32, device=dev), torch.zeros(N, dtype=torch.float32, device=dev)
+            x32.copy_(b)
+            tm, _ = timed(lambda: Pm.apply_f32(0, x32, y32), 10)
+            um = torch.zeros_like(b)
+            sm, (stm, itm, hm) = timed(lambda: Pm.solve("pcg", b, um, rtol=1e-8, maxit=500), 3)
+            P64.apply(0, um, y)
+            res = float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
+            diff = float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64))
+            fine_bytes = gbytes if (prec == "fp32" or p <= 7) else 4
+            line.update({
+                f"apply_{prec}_ms": tm, f"apply_{prec}_gdofs": N / tm / 1e6,
+                f"apply_{prec}_hbm_gbs": (E ** 3 * 6 * fine_bytes * n ** 3 + 8 * N) / tm / 1e6,
+                f"pcg_{prec}_ms": sm, f"pcg_{prec}_iters": itm, f"pcg_{prec}_status": stm,
+                f"{prec}_speedup_vs_fp64": s64 / sm, f"{prec}_final_rel_residual_fp64": res,
+                f"{prec}_vs_fp64_solution_rel_diff": diff, f"setup_bytes_{prec}": Pm.device_bytes()})
+            Pm.close()
+        print(json.dumps(line), flush=True)
         P64.close()
-        P32.close()
     return 0
 
 
@@ -585,7 +592,7 @@ def run_paper_tables(args):
 def run_profile_apply(args):
     """Small fixed launch sequence for ncu: build the hierarchy of the warped var-coef problem
     (--mesh elements per axis, --order p, p-multigrid), then two applies on each of the three
-    finest levels (FP64 hmg_apply, or hmg_apply_f32 with --prec fp32) after setup's applies."""
+    finest levels (FP64 hmg_apply, or hmg_apply_f32 with --prec fp32/fp16/bf16) after setup's applies."""
     import torch
 
     import __graft_entry__
@@ -593,15 +600,15 @@ def run_profile_apply(args):
     import synth
     from paper_1402_5938_gb300 import Problem
     prob = synth.warped_var3d(args.mesh, args.order, hier=args.hier)
-    if args.prec == "fp32":
-        prob = dict(prob, smooth_prec="fp32")
+    if args.prec != "fp64":
+        prob = dict(prob, smooth_prec=args.prec)
     P = Problem(prob)
     for lev in range(min(3, P.nlevels())):
         N = P.ndof(lev)
         x = torch.from_numpy(synth.uniform_pm1(7, N)).cuda()
         y = torch.zeros_like(x)
         for _ in range(2):
-            if args.prec == "fp32":
+            if args.prec != "fp64":
                 P.apply_f32(lev, x.float(), y.float())
             else:
                 P.apply(lev, x, y)
@@ -628,7 +635,8 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--mesh", type=int, default=16, help="--profile-apply: elements per axis")
     ap.add_argument("--order", type=int, default=4, help="--profile-apply: polynomial order")
-    ap.add_argument("--prec", choices=["fp64", "fp32"], default="fp64", help="--profile-apply: precision")
+    ap.add_argument("--prec", choices=["fp64", "fp32", "fp16", "bf16"], default="fp64",
+                    help="--profile-apply: precision")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)

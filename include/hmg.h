@@ -45,7 +45,7 @@ typedef enum {
 typedef enum { HMG_HIER_H = 0, HMG_HIER_P = 1 } hmg_hier;
 typedef enum { HMG_SMOOTH_JACOBI = 0, HMG_SMOOTH_CHEB = 1 } hmg_smoother;
 typedef enum { HMG_MODE_MG = 0, HMG_MODE_PCG = 1 } hmg_mode;
-typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1 } hmg_prec;
+typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC_BF16 = 3 } hmg_prec;
 
 /*
  * Problem descriptor (paper Sec. 2 problem statement, Sec. 2.3 meshing, Sec. 4.3 settings).
@@ -67,6 +67,12 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1 } hmg_prec;
  *                        0 selects 0x1402593800000000.
  *   smooth_prec        : HMG_PREC_FP64, or HMG_PREC_FP32 for the V-cycle's smoother, residual and
  *                        transfer work below the FP64 fine residual / PCG / coarsest solve.
+ *                        HMG_PREC_FP16 / HMG_PREC_BF16: the same FP32 V-cycle whose operator
+ *                        applies on levels of order p <= 7 store the geometric factors in 16 bits
+ *                        (FP16 with a power-of-two scale per element) and run the 1D contractions
+ *                        on the tensor cores with 16-bit operands and FP32 accumulation (levels of
+ *                        higher order keep the FP32 apply); PCG then uses the flexible
+ *                        (Polak-Ribiere) beta, since such a preconditioner is only nearly linear.
  *   solve_graph        : 1 (default): hmg_solve runs each solve as one instantiated CUDA graph with
  *                        a device-side loop (no host round trip per iteration); 0: host-driven loop
  *                        that reads the residual norm back every iteration. Same results.
@@ -129,8 +135,10 @@ hmg_status hmg_rhs(hmg_problem* prob, const double* f_nodal_dev, double* b_dev, 
  * discussion; (A_k)_ij = a(phi_i, phi_j), Sec. 2.1), Dirichlet nodes masked. */
 hmg_status hmg_apply(hmg_problem* prob, int level, const double* x_dev, double* y_dev, void* stream);
 
-/* FP32 variant of hmg_apply (FP32 geometric factors and vectors, FP32 arithmetic): the
- * operator of the mixed-precision V-cycle. Needs smooth_prec = HMG_PREC_FP32 at setup. */
+/* FP32-vector variant of hmg_apply: the operator the mixed-precision V-cycle applies on level k
+ * (smooth_prec = HMG_PREC_FP32: FP32 factors and arithmetic; HMG_PREC_FP16 / HMG_PREC_BF16:
+ * 16-bit factors and tensor-core contractions with FP32 accumulation where the level's order is
+ * <= 7, else FP32). Needs a smooth_prec other than HMG_PREC_FP64 at setup. */
 hmg_status hmg_apply_f32(hmg_problem* prob, int level, const float* x_dev, float* y_dev, void* stream);
 
 /* D^-1 of level k (inverse diagonal of A_k; 0 on boundary nodes), Sec. 3.2.1. */

@@ -90,9 +90,12 @@ struct Level {
   double* wdetJ = nullptr;
   double* dinv = nullptr;
   float* G32 = nullptr;
+  void* G16 = nullptr;    // 16-bit factors of the FP16/BF16 V-cycle operator (orders <= 7)
+  float* gsc = nullptr;   // FP16: per-element power-of-two factor scales
   float* dinv32 = nullptr;
   double lam = 0.0;       // Chebyshev bound
-  int v64 = 0, v32 = 0;   // apply block-shape variants chosen by the autotuner
+  int v64 = 0, v32 = 0;   // apply block-shape variants chosen by the autotuner (v32: of the
+                          // V-cycle operator, FP32 or 16-bit)
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d32 = nullptr;
   Axis1D P[3]{}, PT[3]{};  // transfer to the next coarser level: P rows fine, PT rows coarse
@@ -254,7 +257,7 @@ hmg_status validate(const hmg_desc* d) {
                                          !(d->cheb_safety > 0.0))) {
     set_error("bad Chebyshev parameters"); return HMG_EINVAL;
   }
-  if (d->smooth_prec != HMG_PREC_FP64 && d->smooth_prec != HMG_PREC_FP32) { set_error("bad smooth_prec"); return HMG_EINVAL; }
+  if (d->smooth_prec < HMG_PREC_FP64 || d->smooth_prec > HMG_PREC_BF16) { set_error("bad smooth_prec"); return HMG_EINVAL; }
   return HMG_OK;
 }
 
@@ -333,7 +336,10 @@ hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s, l.v32));
+  if (l.G16)
+    TRY(launch_apply_lowp(l.m, l.basis, x, y, l.G16, l.gsc, alpha, P.desc.smooth_prec, P.err, s, l.v32));
+  else
+    TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s, l.v32));
   return HMG_OK;
 }
 
@@ -469,7 +475,7 @@ hmg_status vcycle(ProblemImpl& P, int k, const T* b, T* x, bool zero, cudaStream
 
 // z = B r on the finest level (FP64 in and out; FP32 internally for the mixed form).
 hmg_status precondition(ProblemImpl& P, const double* r, double* z, cudaStream_t s) {
-  if (P.desc.smooth_prec == HMG_PREC_FP32 && P.L.size() > 1) {
+  if (P.desc.smooth_prec != HMG_PREC_FP64 && P.L.size() > 1) {
     Level& l = P.L[0];
     TRY(to_f32(l.b32, r, l.m.N, s));
     CHECK(vcycle<float>(P, 0, l.b32, l.x32, true, s));
@@ -484,6 +490,18 @@ hmg_status dot_to(ProblemImpl& P, const double* x, const double* y, long long n,
   TRY(dot_partial(x, y, n, P.partial, s));
   TRY(finish(P.partial, n, P.S, op, idx, aux, to_host ? P.hostS : nullptr, s));
   return HMG_OK;
+}
+
+// New rho = (z, r) and beta of PCG (Algorithm 1). With a 16-bit V-cycle the preconditioner is
+// only nearly linear, so beta takes the flexible (Polak-Ribiere) form
+// (z_new, r_new - r_old) / (z_old, r_old) = -(z_new, A p_old) / (p_old, A p_old), using h = A p
+// still held in P.ph; otherwise the standard (z_new, r_new) / (z_old, r_old).
+hmg_status pcg_rho_beta(ProblemImpl& P, const double* z, const double* r, long long n, cudaStream_t s) {
+  if (P.desc.smooth_prec == HMG_PREC_FP16 || P.desc.smooth_prec == HMG_PREC_BF16) {
+    CHECK(dot_to(P, z, P.ph, n, FIN_NEG_RATIO, S_BETA, S_PH, false, s));
+    return dot_to(P, z, r, n, FIN_STORE, S_RHO, 0, false, s);
+  }
+  return dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s);
 }
 
 hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
@@ -551,9 +569,10 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   static std::map<std::tuple<int, int, int, long long, int>, int> cache;
   int dev = 0;
   TRY(cudaGetDevice(&dev));
-  const bool mixed = l.G32 != nullptr;
+  const bool mixed = l.G32 != nullptr || l.G16 != nullptr;
   for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
-    const auto key = std::make_tuple(dev, l.m.dim, l.m.p, l.m.nelem, prec);
+    const int kind = prec == 0 ? 0 : (l.G16 ? P.desc.smooth_prec : HMG_PREC_FP32);
+    const auto key = std::make_tuple(dev, l.m.dim, l.m.p, l.m.nelem, kind);
     {
       std::lock_guard<std::mutex> lk(mu);
       auto it = cache.find(key);
@@ -568,10 +587,13 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     float best = 1e30f;
     int bv = 0;
     cudaError_t err = cudaSuccess;
-    for (int v = 0; v < (prec ? kApply32Variants : kApply64Variants) && err == cudaSuccess; ++v) {
+    const int nvar = prec == 0 ? kApply64Variants : (l.G16 ? kApply16Variants : kApply32Variants);
+    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
       auto run = [&]() {
-        return prec ? launch_apply_f32(l.m, l.basis, l.x32, l.r32, l.G32, 1.0f, P.err, s, v)
-                    : launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v);
+        if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v);
+        if (l.G16)
+          return launch_apply_lowp(l.m, l.basis, l.x32, l.r32, l.G16, l.gsc, 1.0f, P.desc.smooth_prec, P.err, s, v);
+        return launch_apply_f32(l.m, l.basis, l.x32, l.r32, l.G32, 1.0f, P.err, s, v);
       };
       if ((err = run()) != cudaSuccess) break;  // warm-up (also opts the kernel into its smem)
       if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
@@ -591,7 +613,7 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     (prec ? l.v32 : l.v64) = bv;
     if (Phase::timing())
       fprintf(stderr, "hmg autotune: dim %d p %d elements %lld %s -> variant %d (%.4f ms per apply)\n", l.m.dim,
-              l.m.p, l.m.nelem, prec ? "fp32" : "fp64", bv, best / 3);
+              l.m.p, l.m.nelem, kind == 0 ? "fp64" : (kind == HMG_PREC_FP32 ? "fp32" : "16-bit"), bv, best / 3);
     std::lock_guard<std::mutex> lk(mu);
     cache[key] = bv;
   }
@@ -676,7 +698,8 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   TRY(cudaMalloc((void**)&Jstage, max_stage));
   if (cudaMalloc((void**)&bad, sizeof(int)) != cudaSuccess) { cudaFree(Jstage); set_error("alloc"); return HMG_ENOMEM; }
   hmg_status st = [&]() -> hmg_status {
-    const bool mixed = D.smooth_prec == HMG_PREC_FP32;
+    const bool mixed = D.smooth_prec != HMG_PREC_FP64;
+    const bool lowp = D.smooth_prec == HMG_PREC_FP16 || D.smooth_prec == HMG_PREC_BF16;
     for (size_t k = 0; k < P.L.size(); ++k) {
       Phase ph("setup: level geometry, diagonal", s);
       Level& l = P.L[k];
@@ -700,13 +723,21 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       TRY(dinv_from_diag(l.r, l.dinv, n, s));
       TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));
       if (mixed) {
-        TRY(P.alloc((void**)&l.G32, gsz * nc_of(D.dim) * sizeof(float) + 256));  // TMA tail padding
+        if (lowp && l.m.p <= kMaxOrder16) {
+          TRY(P.alloc((void**)&l.G16, gsz * nc_of(D.dim) * 2 + 256));  // TMA tail padding
+          if (D.smooth_prec == HMG_PREC_FP16) TRY(P.alloc((void**)&l.gsc, l.m.nelem * sizeof(float)));
+        } else {
+          TRY(P.alloc((void**)&l.G32, gsz * nc_of(D.dim) * sizeof(float) + 256));  // TMA tail padding
+        }
         TRY(P.alloc((void**)&l.dinv32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.b32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.x32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.r32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.d32, n * sizeof(float)));
-        TRY(to_f32(l.G32, l.G, gsz * nc_of(D.dim), s));
+        if (l.G16)
+          TRY(launch_pack_g16(l.G, l.G16, l.gsc, l.m.nelem, (int)(np_of(l.m) * nc_of(D.dim)), D.smooth_prec, s));
+        else
+          TRY(to_f32(l.G32, l.G, gsz * nc_of(D.dim), s));
         TRY(to_f32(l.dinv32, l.dinv, n, s));
       }
       CHECK(tune_level(P, l, s));
@@ -850,7 +881,7 @@ hmg_status build_graph(ProblemImpl& P, int mode, int cap) {
       CHECK(add_conditional(body, l1, hi, cudaGraphCondTypeIf, &rest));
       CHECK(capture_into(rest, s, [&]() -> hmg_status {
         CHECK(precondition(P, r, z, s));
-        CHECK(dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s));
+        CHECK(pcg_rho_beta(P, z, r, n, s));
         TRY(pcg_direction(P.pp, z, n, P.S, s));
         return HMG_OK;
       }, nullptr));
@@ -929,7 +960,7 @@ hmg_status build_lockstep(ProblemImpl& P, int mode) {
     CHECK(capture_plain(P, mode, 1, s, [&]() -> hmg_status { return apply_update(); }));
     CHECK(capture_plain(P, mode, 2, s, [&]() -> hmg_status {
       CHECK(precondition(P, r, z, s));
-      CHECK(dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s));
+      CHECK(pcg_rho_beta(P, z, r, n, s));
       TRY(pcg_direction(P.pp, z, n, P.S, s));
       return apply_update();
     }));
@@ -985,7 +1016,8 @@ hmg_status graph_solve_finish(ProblemImpl& P, int mode, int* iters, double* res_
 hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   std::vector<std::pair<std::vector<int>, int>> shapes;
   CHECK(level_shapes(D, shapes));
-  const bool mixed = D.smooth_prec == HMG_PREC_FP32;
+  const bool mixed = D.smooth_prec != HMG_PREC_FP64;
+  const bool lowp = D.smooth_prec == HMG_PREC_FP16 || D.smooth_prec == HMG_PREC_BF16;
   std::vector<Mesh> ms;
   for (auto& sh : shapes) ms.push_back(make_mesh(D.dim, sh.first.data(), sh.second));
   size_t res = 0, allocs = 0, max_stage = 0, max_tbuf = 0, arnoldi = 0;
@@ -995,7 +1027,15 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     const size_t gsz = (size_t)(m.nelem * np_of(m)), n = (size_t)m.N;
     add(gsz * nc_of(D.dim) * 8 + 256); add(gsz * 8);
     for (int v = 0; v < 5; ++v) add(n * 8);
-    if (mixed) { add(gsz * nc_of(D.dim) * 4 + 256); for (int v = 0; v < 5; ++v) add(n * 4); }
+    if (mixed) {
+      if (lowp && m.p <= kMaxOrder16) {
+        add(gsz * nc_of(D.dim) * 2 + 256);
+        if (D.smooth_prec == HMG_PREC_FP16) add((size_t)m.nelem * 4);
+      } else {
+        add(gsz * nc_of(D.dim) * 4 + 256);
+      }
+      for (int v = 0; v < 5; ++v) add(n * 4);
+    }
     max_stage = std::max(max_stage, gsz * D.dim * (D.dim + 1) * 8);
     if (D.smoother == HMG_SMOOTH_CHEB && k + 1 < ms.size())
       arnoldi = std::max(arnoldi, (size_t)(std::min<long long>(D.arnoldi_iters, interior_count(m)) + 1) * n * 8);
@@ -1143,7 +1183,10 @@ hmg_status hmg_apply(hmg_problem* p, int level, const double* x, double* y, void
 
 hmg_status hmg_apply_f32(hmg_problem* p, int level, const float* x, float* y, void* stream) {
   if (!level_ok(p, level) || !x || !y) { set_error("null argument"); return HMG_EINVAL; }
-  if (!p->impl.L[level].G32) { set_error("the FP32 operator exists only for smooth_prec = HMG_PREC_FP32"); return HMG_EINVAL; }
+  if (!p->impl.L[level].G32 && !p->impl.L[level].G16) {
+    set_error("the V-cycle operator in FP32 vectors exists only for a smooth_prec other than HMG_PREC_FP64");
+    return HMG_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   TRY(cudaMemsetAsync(y, 0, p->impl.L[level].m.N * sizeof(float), s));
   return apply_level(p->impl, level, x, y, 1.0f, s);
@@ -1301,7 +1344,7 @@ static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* 
     if (!isfinite(rn)) { set_error("non-finite residual"); return HMG_ENAN; }
     if (rn <= tol) return HMG_OK;
     CHECK(precondition(P, r, z, s));
-    CHECK(dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s));
+    CHECK(pcg_rho_beta(P, z, r, n, s));
     TRY(pcg_direction(pp, z, n, P.S, s));
   }
   set_error("maximum number of PCG iterations reached");

@@ -18,6 +18,17 @@ cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, d
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
                              const float* G, float alpha, int* err, cudaStream_t s, int variant = 0);
 
+// y += alpha * A x with 16-bit geometric factors and tensor-core contractions (FP32 vectors),
+// for orders p <= 7; prec is HMG_PREC_FP16 (gsc: per-element factor scales) or HMG_PREC_BF16
+// (gsc unused). G16 needs >= 16 bytes of tail padding. variant 0..2 selects the warps per block.
+constexpr int kApply16Variants = 3;
+constexpr int kMaxOrder16 = 7;
+cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
+                              const float* gsc, float alpha, int prec, int* err, cudaStream_t s, int variant = 0);
+// G16 = G / gsc[e] in 16-bit (FP16: gsc[e] a power of two, largest |G16| in [0.5, 1); BF16: no scale).
+cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int per_elem, int prec,
+                            cudaStream_t s);
+
 // Geometry: stage buffer J [E][dim*(dim+1)][NP], then G [E][NC][NP] and wdetJ [E][NP].
 // *bad (device int) is set to 1 where det J <= 0.
 cudaError_t launch_geometry(const Mesh& m, const Basis1D& b, double warp_amp, double mu_a,

@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ 
   if (threadIdx.x == 0) {
     if (op == FIN_STORE) S[idx] = acc;
     else if (op == FIN_SQRT) S[idx] = sqrt(acc);
+    else if (op == FIN_NEG_RATIO) S[idx] = S[aux] != 0.0 ? -acc / S[aux] : 0.0;
     else {  // FIN_RHO_BETA: beta = new / old, rho = new
       S[aux] = acc / S[idx];
       S[idx] = acc;

@@ -24,7 +24,7 @@ enum Scalar : int {
 // ctrl[3] capacity of the residual-history array.
 enum SolveStatus : int { ST_RUNNING = 0, ST_CONVERGED = 1, ST_MAXIT = 2, ST_NAN = 3 };
 
-enum FinishOp : int { FIN_STORE = 0, FIN_SQRT = 1, FIN_RHO_BETA = 2 };
+enum FinishOp : int { FIN_STORE = 0, FIN_SQRT = 1, FIN_RHO_BETA = 2, FIN_NEG_RATIO = 3 };
 
 constexpr int kRedBlocks = 1216;  // fixed partial count (8 x 152 SMs); fixed => deterministic sums
 

@@ -18,7 +18,7 @@ HMG_OK, HMG_EINVAL, HMG_ENOMEM, HMG_ENOCONV, HMG_EDEVICE, HMG_ETIMEOUT, HMG_EBUS
 HIER = {"h": 0, "p": 1}
 SMOOTHER = {"jacobi": 0, "cheb": 1}
 MODE = {"mg": 0, "pcg": 1}
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 
 
 class HmgError(RuntimeError):

@@ -1,0 +1,170 @@
+"""FP16 / BF16 V-cycle: the tensor-core operator against the FP64 oracle, and FP64 PCG /
+MG-refinement solves whose V-cycle applies it (FP64 fine residual, inner products and
+coarsest solve).
+
+Tolerance of the 16-bit apply, from its arithmetic: a term of y_i = sum_e K^T G K x passes
+through k roundings to the 16-bit format (unit roundoff u = 2^-11 for FP16, 2^-8 for BF16):
+x, the d-1 stored forward intermediates, G, v = G grad u, the d-1 stored transposed
+intermediates, and the 2d 1D-table entries of its factor chain, so k = 4d + 1 (13 in 3D, 9 in
+2D); the power-of-two scales are exact and the FP32 accumulation adds O(N 2^-24). To first
+order |y16_i - y_i| <= k u S_i with S = sum_e |K|^T |G| |K| |x| (absolute values of every
+factor), which the test evaluates with the oracle's basis tables and geometry; it allows
+(k + 1) u S_i."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+U16 = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.fixture(scope="module")
+def hmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1402_5938_gb300 as pkg
+    return pkg
+
+
+def _t(a, dt=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dt)
+
+
+def abs_bound_scale(d, x_full):
+    """S = sum_e |K_e|^T |G_e| |K_e| |x_e| (all factors in absolute value), full-length."""
+    Phi, dPhi, W = d.basis_tables()
+    el = np.arange(d.n_elem)
+    xq, J, detJ = d.element_geometry(el, (Phi, dPhi, W))
+    Jinv = np.linalg.inv(J)                                          # [e,q,k,i] = dxi_k / dx_i
+    c = W[None, :] * np.abs(detJ) * d.mu(xq.reshape(-1, d.dim)).reshape(detJ.shape)
+    G = c[:, :, None, None] * np.einsum("eqki,eqli->eqkl", Jinv, Jinv)
+    nodes = d.element_nodes(el)
+    X = np.abs(x_full)[nodes]                                        # (e, a)
+    U = np.stack([X @ np.abs(dPhi[k]).T for k in range(d.dim)], axis=-1)   # (e, q, k)
+    V = np.einsum("eqkl,eqk->eql", np.abs(G), U)
+    Se = sum(V[:, :, l] @ np.abs(dPhi[l]) for l in range(d.dim))    # (e, a)
+    S = np.zeros(d.N)
+    np.add.at(S, nodes.ravel(), Se.ravel())
+    return S
+
+
+CASES = [dict(dim=3, nelem=(3, 2, 2), order=p) for p in (1, 2, 3, 4, 5, 6, 7)] + [
+    dict(dim=3, nelem=(5, 3, 2), order=4),      # ragged last warp group (EW = 3)
+    dict(dim=3, nelem=(4, 4, 3), order=2),
+    dict(dim=2, nelem=(7, 5), order=3),
+    dict(dim=2, nelem=(9, 4), order=5),
+    dict(dim=2, nelem=(3, 3), order=7),
+    dict(dim=2, nelem=(6, 6), order=1),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['dim']}d-{c['nelem']}-p{c['order']}")
+def test_lowp_apply_within_rounding_bound(hmg, case, prec):
+    mu_b = 1e3
+    prob = dict(synth.problem(case["dim"], case["nelem"], case["order"], warp_amp=0.1, mu_b=mu_b, n_hlevels=1,
+                              smoother="jacobi"), smooth_prec=prec)
+    P = hmg.Problem(prob)
+    d = fem.Discretization(case["dim"], case["nelem"], case["order"], warp_amp=0.1, mu_b=mu_b)
+    x = synth.uniform_pm1(21, d.N)
+    y = torch.zeros(d.N, dtype=torch.float32, device=DEV)
+    P.apply_f32(0, _t(x, torch.float32), y)
+    torch.cuda.synchronize()
+    y = y.cpu().numpy().astype(np.float64)
+    xr = x.astype(np.float32).astype(np.float64)
+    xr[d.boundary] = 0.0
+    ref = d.to_full(d.stiffness() @ xr[d.interior])
+    S = abs_bound_scale(d, xr)
+    k = 4 * case["dim"] + 1
+    err = np.abs(y - ref)[d.interior]
+    assert np.all(err <= (k + 1) * U16[prec] * S[d.interior] + 1e-30), float(np.max(err / S[d.interior]))
+    # and it is a real 16-bit result, not an FP32 one in disguise: the error is well above FP32 rounding
+    assert np.max(err / S[d.interior]) > 2.0 ** -20
+    assert np.all(y[d.boundary] == 0.0)
+    P.close()
+
+
+def test_lowp_fp16_scaling_keeps_tiny_and_huge_inputs(hmg):
+    """FP16 scales x per element by a power of two: y(c x) = c y(x) for c = 2^-40 and 2^40 (the
+    scaled 16-bit operands are identical), where unscaled FP16 would flush to zero or overflow."""
+    prob = dict(synth.problem(3, (3, 2, 2), 4, warp_amp=0.1, mu_b=1e3, n_hlevels=1, smoother="jacobi"),
+                smooth_prec="fp16")
+    P = hmg.Problem(prob)
+    N = P.ndof(0)
+    x = _t(synth.uniform_pm1(22, N), torch.float32)
+    ys = []
+    for c in (1.0, 2.0 ** -40, 2.0 ** 40):
+        y = torch.zeros(N, dtype=torch.float32, device=DEV)
+        P.apply_f32(0, x * c, y)
+        ys.append(y.double().cpu().numpy() / c)
+    assert np.all(np.isfinite(ys[1])) and np.all(np.isfinite(ys[2]))
+    top = np.abs(ys[0]).max()
+    # identical 16-bit operands; only the FP32 atomic scatter order may differ between launches
+    assert np.abs(ys[1] - ys[0]).max() <= 1e-6 * top and np.abs(ys[2] - ys[0]).max() <= 1e-6 * top
+    P.close()
+
+
+SOLVES = [
+    (synth.warped_var3d(8, 4, hier="p"), "pcg"),
+    (synth.warped_var3d(8, 2, hier="h"), "pcg"),
+    (synth.warped_var3d(4, 4, hier="p"), "mg"),
+    (synth.problem(2, 16, 6, warp_amp=0.1, mu_b=1e3, hier="p"), "pcg"),
+    (synth.problem(3, 4, 8, warp_amp=0.1, mu_b=1e3, hier="p"), "pcg"),   # p = 8 fine level stays FP32
+]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prob,mode", SOLVES, ids=lambda c: str(c)[:60])
+def test_lowp_solve_reaches_fp64_accuracy(hmg, prob, mode, prec):
+    """The 16-bit V-cycle inside FP64 PCG (flexible beta) or MG refinement reaches the FP64
+    tolerance: true FP64 residual <= 1e-8 relative, solution equal to the FP64 solve's to the
+    accuracy the residual bound gives, iteration count at most 1.5x + 2 the FP64 one."""
+    P64 = hmg.Problem(prob)
+    Pl = hmg.Problem(dict(prob, smooth_prec=prec))
+    N = P64.ndof(0)
+    f = _t(synth.nodal_field(31, N))
+    b = torch.zeros(N, dtype=torch.float64, device=DEV)
+    P64.rhs(f, b)
+    u64 = torch.zeros_like(b)
+    ul = torch.zeros_like(b)
+    st64, it64, _ = P64.solve(mode, b, u64, rtol=1e-8, maxit=400)
+    st, it, h = Pl.solve(mode, b, ul, rtol=1e-8, maxit=400)
+    assert st64 == 0 and st == 0
+    r = torch.zeros_like(b)
+    P64.apply(0, ul, r)
+    res = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
+    assert res <= 1.05e-8
+    assert it <= 1.5 * it64 + 2
+    rel = float(torch.linalg.norm(ul - u64) / torch.linalg.norm(u64))
+    assert rel < 1e-5
+    print(f"{prec} {mode}: iterations {it} (FP64 {it64}), true residual {res:.2e}, |u - u64|/|u64| {rel:.1e}")
+    P64.close()
+    Pl.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_lowp_graph_and_batched_equal_host_loop(hmg, prec):
+    """The flexible-beta PCG gives the same iterations through the device-side graph loop, the
+    host loop and a lockstep batch."""
+    prob = dict(synth.warped_var3d(8, 4, hier="p"), smooth_prec=prec)
+    Pg = hmg.Problem(dict(prob, solve_graph=1))
+    Ph = hmg.Problem(dict(prob, solve_graph=0))
+    N = Pg.ndof(0)
+    b = torch.zeros(N, dtype=torch.float64, device=DEV)
+    Pg.rhs(_t(synth.nodal_field(32, N)), b)
+    ug, uh, ub = (torch.zeros_like(b) for _ in range(3))
+    stg, itg, hg = Pg.solve("pcg", b, ug, rtol=1e-8, maxit=200)
+    sth, ith, hh = Ph.solve("pcg", b, uh, rtol=1e-8, maxit=200)
+    sts, its, _ = hmg.solve_batched([Pg], "pcg", [b], [ub], rtol=1e-8, maxit=200)
+    assert stg == sth == sts[0] == 0
+    assert abs(itg - ith) <= 1 and abs(its[0] - ith) <= 1
+    assert float(torch.linalg.norm(ug - uh) / torch.linalg.norm(uh)) < 1e-6
+    Pg.close()
+    Ph.close()
