@@ -45,6 +45,9 @@ struct Lowp<__half> {
   }
   static __device__ __forceinline__ uint16_t bits(float v) { return __half_as_ushort(__float2half_rn(v)); }
   static __device__ __forceinline__ float val(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+  static __device__ __forceinline__ float2 val2(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  }
   static __device__ __forceinline__ void mma(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -60,6 +63,9 @@ struct Lowp<__nv_bfloat16> {
   }
   static __device__ __forceinline__ uint16_t bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
   static __device__ __forceinline__ float val(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+  static __device__ __forceinline__ float2 val2(uint32_t w) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+  }
   static __device__ __forceinline__ void mma(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
     asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -166,7 +172,8 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
     // (e, a, b) -> value a of line (e, c, b)
     const int s1 = ok ? C::pos((L / N) * N + c, L % N) : -1;
     const int s2 = (ok && DIM == 3) ? C::pos(((L / (N * N)) * N + c) * N + L % N, (L / N) % N) : -1;
-    const int gq = ok ? e * NC * NP + c * NL + rem : -1;
+    // factors: 3D point-major [e][q][6] (three 32-bit loads per point), 2D [e][3][q]
+    const int gq = !ok ? -1 : (DIM == 3 ? (e * NP + c * NL + rem) * NC : e * NC * NP + c * NL + rem);
     const int kk = DIM == 3 ? rem / N : 0, jj = DIM == 3 ? rem % N : rem;
     int fb = (c == 0) | ((c == N - 1) << 1) | ((jj == 0) << 2) | ((jj == N - 1) << 3);
     if (DIM == 3) fb |= ((kk == 0) << 4) | ((kk == N - 1) << 5);
@@ -352,8 +359,9 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
         const bool pv = gq[u] >= 0;
         const uint16_t* q = Gs + (pv ? gq[u] : 0);
         if (DIM == 3) {
-          const float g00 = L::val(q[0]), g01 = L::val(q[NP]), g02 = L::val(q[2 * NP]);
-          const float g11 = L::val(q[3 * NP]), g12 = L::val(q[4 * NP]), g22 = L::val(q[5 * NP]);
+          const uint32_t* q32 = reinterpret_cast<const uint32_t*>(q);  // 4-byte aligned: 12 B per point
+          const float2 ga = L::val2(q32[0]), gb = L::val2(q32[1]), gc = L::val2(q32[2]);
+          const float g00 = ga.x, g01 = ga.y, g02 = gb.x, g11 = gb.y, g12 = gc.x, g22 = gc.y;
           v[0][u] = pv ? g00 * gr[0][u] + g01 * gr[1][u] + g02 * gr[2][u] : 0.0f;
           v[1][u] = pv ? g01 * gr[0][u] + g11 * gr[1][u] + g12 * gr[2][u] : 0.0f;
           v[2][u] = pv ? g02 * gr[0][u] + g12 * gr[1][u] + g22 * gr[2][u] : 0.0f;
@@ -427,13 +435,15 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
   }
 }
 
-// G16[e][c][q] = G[e][c][q] / gsc[e] in 16-bit; FP16 takes gsc[e] = the power of two at or above
-// the element's largest |G| (so every stored factor is <= 1), BF16 gsc = nullptr (no scale).
+// 16-bit factors G16 = G / gsc[e] of one element per block, from G[e][c][q] (nc components, np
+// points): point-major G16[e][q][c] when point_major (3D), else G16[e][c][q]. FP16 takes gsc[e] =
+// the power of two with the element's largest |G| / gsc in [0.5, 1); BF16 gsc = nullptr (no scale).
 template <typename T>
 __global__ void k_pack_g16(const double* __restrict__ G, T* __restrict__ G16, float* __restrict__ gsc,
-                           long long nelem, int per_elem) {
+                           long long nelem, int nc, int np, int point_major) {
   const long long e = blockIdx.x;
   if (e >= nelem) return;
+  const int per_elem = nc * np;
   const double* ge = G + e * per_elem;
   __shared__ double red[32];
   double amax = 0.0;
@@ -451,11 +461,14 @@ __global__ void k_pack_g16(const double* __restrict__ G, T* __restrict__ G16, fl
   if (gsc != nullptr) {
     int ex = 0;
     if (red[0] > 0.0) frexp(red[0], &ex);
-    sc = ldexp(1.0, ex);  // largest |G| / sc in [0.5, 1)
+    sc = ldexp(1.0, ex);
     if (threadIdx.x == 0) gsc[e] = (float)sc;
   }
   T* oe = G16 + e * per_elem;
-  for (int i = threadIdx.x; i < per_elem; i += blockDim.x) oe[i] = (T)(float)(ge[i] / sc);
+  for (int i = threadIdx.x; i < per_elem; i += blockDim.x) {
+    const int comp = i / np, q = i - comp * np;
+    oe[point_major ? q * nc + comp : i] = (T)(float)(ge[i] / sc);
+  }
 }
 
 }  // namespace hmg

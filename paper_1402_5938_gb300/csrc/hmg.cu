@@ -735,7 +735,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         TRY(P.alloc((void**)&l.r32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.d32, n * sizeof(float)));
         if (l.G16)
-          TRY(launch_pack_g16(l.G, l.G16, l.gsc, l.m.nelem, (int)(np_of(l.m) * nc_of(D.dim)), D.smooth_prec, s));
+          TRY(launch_pack_g16(l.G, l.G16, l.gsc, l.m.nelem, nc_of(D.dim), (int)np_of(l.m), D.dim, D.smooth_prec, s));
         else
           TRY(to_f32(l.G32, l.G, gsz * nc_of(D.dim), s));
         TRY(to_f32(l.dinv32, l.dinv, n, s));

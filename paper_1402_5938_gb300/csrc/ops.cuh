@@ -25,9 +25,10 @@ constexpr int kApply16Variants = 3;
 constexpr int kMaxOrder16 = 7;
 cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
                               const float* gsc, float alpha, int prec, int* err, cudaStream_t s, int variant = 0);
-// G16 = G / gsc[e] in 16-bit (FP16: gsc[e] a power of two, largest |G16| in [0.5, 1); BF16: no scale).
-cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int per_elem, int prec,
-                            cudaStream_t s);
+// G16 = G / gsc[e] in 16-bit (FP16: gsc[e] a power of two, largest |G16| in [0.5, 1); BF16: no scale),
+// in the layout launch_apply_lowp reads (3D: point-major [e][q][6]; 2D: [e][3][q]).
+cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int nc, int np, int dim,
+                            int prec, cudaStream_t s);
 
 // Geometry: stage buffer J [E][dim*(dim+1)][NP], then G [E][NC][NP] and wdetJ [E][NP].
 // *bad (device int) is set to 1 where det J <= 0.

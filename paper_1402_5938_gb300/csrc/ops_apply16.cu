@@ -91,14 +91,15 @@ cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, f
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int per_elem, int prec,
-                            cudaStream_t s) {
+cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int nc, int np, int dim,
+                            int prec, cudaStream_t s) {
   if (nelem == 0) return cudaSuccess;
+  const int pm = dim == 3;  // the 3D kernel reads a point's six factors as three 32-bit words
   if (prec == HMG_PREC_FP16)
-    k_pack_g16<__half><<<(unsigned)nelem, 128, 0, s>>>(G, static_cast<__half*>(G16), gsc, nelem, per_elem);
+    k_pack_g16<__half><<<(unsigned)nelem, 128, 0, s>>>(G, static_cast<__half*>(G16), gsc, nelem, nc, np, pm);
   else if (prec == HMG_PREC_BF16)
     k_pack_g16<__nv_bfloat16><<<(unsigned)nelem, 128, 0, s>>>(G, static_cast<__nv_bfloat16*>(G16), nullptr,
-                                                             nelem, per_elem);
+                                                             nelem, nc, np, pm);
   else
     return cudaErrorInvalidValue;
   return counted(cudaGetLastError());
