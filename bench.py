@@ -218,6 +218,8 @@ def run_gpu(args):
     from paper_1402_5938_gb300 import Problem, launch_count
 
     prob = workload(args.hier)
+    if args.host_loop:  # same kernels launched one by one (for launch lists; graph nodes are not listed)
+        prob = dict(prob, solve_graph=0)
     t0 = time.perf_counter()
     P = Problem(prob)
     torch.cuda.synchronize()
@@ -309,7 +311,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "hier": args.hier, "global_batch": world, "dof": N,
-                       "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed solves"},
+                       "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed solves",
+                       "solve_loop": "host" if args.host_loop else "graph"},
             "solve_ms": t_step, "setup_ms": setup_ms, "iterations": its[-1], "final_rel_residual": rel_res,
             "fine_applies_per_solve": applies, "apply_gdofs": N / (apply_ms * 1e-3) / 1e9,
             "apply_ms": apply_ms,
@@ -624,6 +627,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--hier", choices=["h", "p"], default="p")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven solve loop instead of the graph (for ncu launch lists)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
     ap.add_argument("--sweep", action="store_true", help="order sweep at ~2M DOF, FP64 vs mixed precision")

@@ -563,10 +563,47 @@ bool autotune_on() {
   return on;
 }
 
+// Autotuner decisions, keyed by (device, dim, order, elements, precision kind). With
+// HMG_AUTOTUNE_CACHE=<file> they persist across processes: the file's lines
+// "device dim order elements kind variant" are read once, and new decisions are appended, so a
+// later process (for instance one run under a profiler, whose timings would be distorted)
+// reuses them instead of timing again.
+using TuneKey = std::tuple<int, int, int, long long, int>;
+std::map<TuneKey, int>& tune_cache() {
+  static std::map<TuneKey, int> cache = [] {
+    std::map<TuneKey, int> m;
+    if (const char* f = getenv("HMG_AUTOTUNE_CACHE")) {
+      if (FILE* fp = fopen(f, "r")) {
+        int dev, dim, p, kind, v;
+        long long ne;
+        while (fscanf(fp, "%d %d %d %lld %d %d", &dev, &dim, &p, &ne, &kind, &v) == 6)
+          m[std::make_tuple(dev, dim, p, ne, kind)] = v;
+        fclose(fp);
+      }
+    }
+    return m;
+  }();
+  return cache;
+}
+
+void tune_cache_store(const TuneKey& k, int v) {
+  tune_cache()[k] = v;
+  if (const char* f = getenv("HMG_AUTOTUNE_CACHE")) {
+    if (FILE* fp = fopen(f, "a")) {
+      fprintf(fp, "%d %d %d %lld %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+              std::get<4>(k), v);
+      fclose(fp);
+    }
+  }
+}
+
 hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   if (!autotune_on()) return HMG_OK;
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, long long, int>, int> cache;
+  std::map<TuneKey, int>& cache = [&]() -> std::map<TuneKey, int>& {
+    std::lock_guard<std::mutex> lk(mu);
+    return tune_cache();
+  }();
   int dev = 0;
   TRY(cudaGetDevice(&dev));
   const bool mixed = l.G32 != nullptr || l.G16 != nullptr;
@@ -615,7 +652,7 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
       fprintf(stderr, "hmg autotune: dim %d p %d elements %lld %s -> variant %d (%.4f ms per apply)\n", l.m.dim,
               l.m.p, l.m.nelem, kind == 0 ? "fp64" : (kind == HMG_PREC_FP32 ? "fp32" : "16-bit"), bv, best / 3);
     std::lock_guard<std::mutex> lk(mu);
-    cache[key] = bv;
+    tune_cache_store(key, bv);
   }
   TRY(cudaMemsetAsync(l.r, 0, l.m.N * sizeof(double), s));
   if (mixed) TRY(cudaMemsetAsync(l.r32, 0, l.m.N * sizeof(float), s));
