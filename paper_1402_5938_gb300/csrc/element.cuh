@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(256)
 k_geom_stage(double* __restrict__ J, const Mesh m, const double warp_amp,
              const __grid_constant__ GeoTab<N> tab, const int epb) {
   constexpr int NP = Sh<DIM, N>::NP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   double* U = reinterpret_cast<double*>(smem_raw);
   double* V = U + epb * NP;
   const long long e0 = (long long)blockIdx.x * epb;
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256)
 k_diag(const double* __restrict__ G, double* __restrict__ diag, const Mesh m,
        const __grid_constant__ GeoTab<N> tab, const int epb) {
   constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   double* U = reinterpret_cast<double*>(smem_raw);
   double* Dt = U + epb * NP;
   const long long e0 = (long long)blockIdx.x * epb;
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(256)
 k_mass(const double* __restrict__ f, double* __restrict__ b, const double* __restrict__ wdetJ,
        const Mesh m, const __grid_constant__ GeoTab<N> tab, const int epb) {
   constexpr int NP = Sh<DIM, N>::NP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   double* U = reinterpret_cast<double*>(smem_raw);
   const long long e0 = (long long)blockIdx.x * epb;
   const int ne = (int)min((long long)epb, m.nelem - e0);
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(256)
 k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
              const __grid_constant__ Tab<N, double> tab, const long long nI, const int epb) {
   constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   double* U = reinterpret_cast<double*>(smem_raw);
   double* V = U + epb * NP;
   const long long t0 = (long long)blockIdx.x * epb;

@@ -120,11 +120,18 @@ struct Apply16Cfg {
 
 namespace lp {
 
-// A-operand rows 16 mt + g and 16 mt + g + 8 of a line buffer (lp points at row 16 mt + g,
-// column 2t), columns 2t, 2t+1
-__device__ __forceinline__ void ldA(const uint16_t* lp, uint32_t& a0, uint32_t& a1) {
-  a0 = *reinterpret_cast<const uint32_t*>(lp);
-  a1 = *reinterpret_cast<const uint32_t*>(lp + 64);
+// A operand of one 16-row tile (rows 16 mt .. 16 mt + 15, 16 bytes each) by ldmatrix: lane l
+// passes the address of row (l & 15) of the tile (ra = shared address of that row); a lane then
+// holds rows g and g+8, columns 2t, 2t+1, the m16n8k8 A fragment. ldA2 loads the same rows of two
+// buffers (lanes 16-31 address the second).
+__device__ __forceinline__ void ldA(uint32_t ra, uint32_t& a0, uint32_t& a1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(a0), "=r"(a1) : "r"(ra) : "memory");
+}
+__device__ __forceinline__ void ldA2(uint32_t ra, uint32_t& a0, uint32_t& a1, uint32_t& b0, uint32_t& b1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a0), "=r"(a1), "=r"(b0), "=r"(b1)
+               : "r"(ra)
+               : "memory");
 }
 
 // Store an accumulator tile into the line buffer of the next direction at the table's offsets
@@ -148,19 +155,19 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
   using L = Lowp<T>;
   constexpr int NP = C::NP, NL = C::NL, NC = C::NC, EW = C::EW, NLG = C::NLG, MT = C::MT, BUF = C::BUF;
   constexpr int H = C::H, NPAD = C::NPAD;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem16[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
 
   // ---- block table of per-lane index offsets (depends on the lane and the mesh strides only) ----
-  short4* ts1 = reinterpret_cast<short4*>(smem_raw + C::TAB_S1);
-  short4* ts2 = reinterpret_cast<short4*>(smem_raw + C::TAB_S2);
-  short4* tgo = reinterpret_cast<short4*>(smem_raw + C::TAB_G);
-  int4* tyo = reinterpret_cast<int4*>(smem_raw + C::TAB_YO);
-  int4* tyi = reinterpret_cast<int4*>(smem_raw + C::TAB_YI);
-  int* go = reinterpret_cast<int*>(smem_raw + C::TAB_GO);
-  int* gcode = reinterpret_cast<int*>(smem_raw + C::TAB_GC);
+  short4* ts1 = reinterpret_cast<short4*>(smem16 + C::TAB_S1);
+  short4* ts2 = reinterpret_cast<short4*>(smem16 + C::TAB_S2);
+  short4* tgo = reinterpret_cast<short4*>(smem16 + C::TAB_G);
+  int4* tyo = reinterpret_cast<int4*>(smem16 + C::TAB_YO);
+  int4* tyi = reinterpret_cast<int4*>(smem16 + C::TAB_YI);
+  int* go = reinterpret_cast<int*>(smem16 + C::TAB_GO);
+  int* gcode = reinterpret_cast<int*>(smem16 + C::TAB_GC);
   for (int i = threadIdx.x; i < MT * 32 * 4; i += blockDim.x) {
     const int mt = i >> 7, ln = (i >> 2) & 31, u = i & 3;
     const int r = mt * 16 + (ln >> 2) + 8 * (u >> 1);       // accumulator row
@@ -193,7 +200,7 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
     gcode[i] = ok ? (e | (fb << 8) | (C::pos(e * NL + a / N, ii) << 16)) : 0;
   }
 
-  unsigned char* ws = smem_raw + C::TAB_BYTES + warp * C::WARP_BYTES;
+  unsigned char* ws = smem16 + C::TAB_BYTES + warp * C::WARP_BYTES;
   uint64_t* bar = reinterpret_cast<uint64_t*>(ws + C::OFF_BAR);
   uint16_t* buf = reinterpret_cast<uint16_t*>(ws + C::OFF_BUF);
   unsigned char* gslot = ws + C::OFF_G;
@@ -220,7 +227,8 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
   const uint32_t fD = L::pack(tb(tab.Bd, g, 2 * t), tb(tab.Bd, g, 2 * t + 1));
   const uint32_t bB = L::pack(tb(tab.B, 2 * t, g), tb(tab.B, 2 * t + 1, g));
   const uint32_t bD = L::pack(tb(tab.Bd, 2 * t, g), tb(tab.Bd, 2 * t + 1, g));
-  const int lofs = g * 8 + 2 * t;  // A-operand offset of this lane within a 16-row tile
+  // ldmatrix row address of this lane: row (lane & 15) of a tile, in the buffer of half-warp lane >> 4
+  const uint32_t rowb = (uint32_t)(lane & 15) * 16u;
 
   const long long gstride = (long long)gridDim.x * (blockDim.x >> 5);
   long long grp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -277,6 +285,11 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
       if (u * 32 + lane < EW * NP) buf[gcode[u * 32 + lane] >> 16] = L::bits(xv[u] * sx);
     __syncwarp();
 
+    const uint32_t s0 = smem_addr(buf);  // shared address of line buffer 0; buffer k at s0 + k * BUF * 2
+    auto sa = [&](int k, int mt) { return s0 + (uint32_t)(k * BUF * 2 + mt * 256) + rowb; };
+    auto sa2 = [&](int k0, int k1, int mt) {  // lanes 0-15 address buffer k0, lanes 16-31 buffer k1
+      return s0 + (uint32_t)(((lane >> 4) ? k1 : k0) * BUF * 2 + mt * 256) + rowb;
+    };
     uint16_t* B0 = buf;
     uint16_t* B1 = buf + BUF;
     uint16_t* B2 = buf + 2 * BUF;
@@ -286,9 +299,8 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
     // ---- forward: direction 0 (i): t1 = B x, t2 = Bd x -> direction-1 buffers B1, B2 ----
 #pragma unroll 1
     for (int mt = 0; mt < MT; ++mt) {
-      const int lo = mt * 128 + lofs;
       uint32_t a0, a1;
-      lp::ldA(B0 + lo, a0, a1);
+      lp::ldA(sa(0, mt), a0, a1);
       float c1[4] = {0.f, 0.f, 0.f, 0.f}, c2[4] = {0.f, 0.f, 0.f, 0.f};
       L::mma(c1, a0, a1, fB);
       L::mma(c2, a0, a1, fD);
@@ -301,10 +313,8 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
       // direction 1 (j): t11 = B t1, t12 = Bd t1, t21 = B t2 -> direction-2 buffers B0, B3, B4
 #pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
-        const int lo = mt * 128 + lofs;
         uint32_t a0, a1, p0, p1;
-        lp::ldA(B1 + lo, a0, a1);
-        lp::ldA(B2 + lo, p0, p1);
+        lp::ldA2(sa2(1, 2, mt), a0, a1, p0, p1);
         float c11[4] = {0.f, 0.f, 0.f, 0.f}, c12[4] = {0.f, 0.f, 0.f, 0.f}, c21[4] = {0.f, 0.f, 0.f, 0.f};
         L::mma(c11, a0, a1, fB);
         L::mma(c12, a0, a1, fD);
@@ -329,25 +339,22 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
     // ---- last forward direction, pointwise G, first transposed contraction (registers) ----
 #pragma unroll 1
     for (int mt = 0; mt < MT; ++mt) {
-      const int lo = mt * 128 + lofs;
       float gr[3][4];  // gradient components along directions 0, 1, 2 at this lane's 4 points
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int u = 0; u < 4; ++u) gr[d][u] = 0.0f;
-      uint32_t a0, a1;
+      uint32_t a0, a1, p0, p1;
       if (DIM == 3) {
-        lp::ldA(B0 + lo, a0, a1);
+        lp::ldA2(sa2(0, 3, mt), a0, a1, p0, p1);
         L::mma(gr[2], a0, a1, fD);  // Bd_k B_j B_i x
-        lp::ldA(B3 + lo, a0, a1);
-        L::mma(gr[1], a0, a1, fB);  // B_k Bd_j B_i x
-        lp::ldA(B4 + lo, a0, a1);
+        L::mma(gr[1], p0, p1, fB);  // B_k Bd_j B_i x
+        lp::ldA(sa(4, mt), a0, a1);
         L::mma(gr[0], a0, a1, fB);  // B_k B_j Bd_i x
       } else {
-        lp::ldA(B1 + lo, a0, a1);
+        lp::ldA2(sa2(1, 2, mt), a0, a1, p0, p1);
         L::mma(gr[1], a0, a1, fD);  // Bd_j B_i x
-        lp::ldA(B2 + lo, a0, a1);
-        L::mma(gr[0], a0, a1, fB);  // B_j Bd_i x
+        L::mma(gr[0], p0, p1, fB);  // B_j Bd_i x
       }
       // entries without a point read the first factors of the slot and get v = 0 (they meet
       // zero table entries in the next contraction, so they must be finite)
@@ -397,14 +404,12 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
       // direction 1 transposed: s1' = B^T s1, r23 = Bd^T s2 + B^T s3 -> direction-0 buffers B0, B3
 #pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
-        const int lo = mt * 128 + lofs;
-        uint32_t a0, a1;
+        uint32_t a0, a1, p0, p1;
         float c1[4] = {0.f, 0.f, 0.f, 0.f}, c2[4] = {0.f, 0.f, 0.f, 0.f};
-        lp::ldA(B1 + lo, a0, a1);
+        lp::ldA2(sa2(1, 2, mt), a0, a1, p0, p1);
         L::mma(c1, a0, a1, bB);
-        lp::ldA(B2 + lo, a0, a1);
-        L::mma(c2, a0, a1, bD);
-        lp::ldA(B5 + lo, a0, a1);
+        L::mma(c2, p0, p1, bD);
+        lp::ldA(sa(5, mt), a0, a1);
         L::mma(c2, a0, a1, bB);
         const short4 o = ts1[mt * 32 + lane];
         lp::stC<T>(B0, c1, o);
@@ -416,13 +421,11 @@ k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restric
     // ---- direction 0 transposed: y_e = Bd^T (.) + B^T (.), scatter-add to interior nodes ----
 #pragma unroll 1
     for (int mt = 0; mt < MT; ++mt) {
-      const int lo = mt * 128 + lofs;
-      uint32_t a0, a1;
+      uint32_t a0, a1, p0, p1;
       float c[4] = {0.f, 0.f, 0.f, 0.f};
-      lp::ldA(B0 + lo, a0, a1);
+      lp::ldA2(sa2(0, 3, mt), a0, a1, p0, p1);
       L::mma(c, a0, a1, bD);
-      lp::ldA(B3 + lo, a0, a1);
-      L::mma(c, a0, a1, bB);
+      L::mma(c, p0, p1, bB);
       const int4 yo = tyo[mt * 32 + lane], yi = tyi[mt * 32 + lane];
       const int off[4] = {yo.x, yo.y, yo.z, yo.w}, inf[4] = {yi.x, yi.y, yi.z, yi.w};
 #pragma unroll
