@@ -592,6 +592,46 @@ def run_paper_tables(args):
     return 0
 
 
+def run_mesh_independence(args):
+    """Mesh independence (the paper's Table 6 setting with this library's smoothers): PCG with an
+    h-multigrid V(3,3) down to 2 x 2 elements on 2D meshes E x E, E = 4..256, orders 1..16, for
+    2d-const and 2d-var and point Jacobi / Chebyshev smoothing. Prints markdown tables with the
+    paper's SSOR(2,1) counts beside (context) and one JSON summary line."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    from paper_1402_5938_gb300 import Problem
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")))["table6_mesh_independence"]
+    Es = gold["E"]
+    spread = {}
+    for kind in ("2d-const", "2d-var"):
+        for smoother in ("jacobi", "cheb"):
+            print(f"\n{kind}, PCG + h-MG V(3,3) {smoother} (GPU count / paper SSOR(2,1) count)\n")
+            print("| p | " + " | ".join(f"E={E}" for E in Es) + " |")
+            print("|---" * (len(Es) + 1) + "|")
+            for p in (1, 2, 4, 8, 16):
+                row, counts = [], []
+                for E, ref in zip(Es, gold[kind][str(p)]):
+                    P = Problem(synth.mesh_independence_problem(kind, E, p, smoother))
+                    N = P.ndof(0)
+                    b = torch.zeros(N, dtype=torch.float64, device="cuda")
+                    P.rhs(torch.from_numpy(synth.nodal_field(11, N)).cuda(), b)
+                    u = torch.zeros_like(b)
+                    st, it, _ = P.solve("pcg", b, u, rtol=1e-8, maxit=300)
+                    P.close()
+                    counts.append(it if st == 0 else None)
+                    row.append(f"{it if st == 0 else '-'} / {ref if ref is not None else '*'}")
+                ok = [k for k, E in zip(counts, Es) if E >= 16 and k is not None]
+                spread[f"{kind} {smoother} p{p}"] = (max(ok) - min(ok)) if ok else None
+                print(f"| {p} | " + " | ".join(row) + " |", flush=True)
+    print(json.dumps({"mesh_independence": "PCG + h-MG V(3,3) to 2x2 elements, E = 4..256",
+                      "max_spread_E_ge_16": max(v for v in spread.values() if v is not None),
+                      "spread": spread}), flush=True)
+    return 0
+
+
 def run_profile_apply(args):
     """Small fixed launch sequence for ncu: build the hierarchy of the warped var-coef problem
     (--mesh elements per axis, --order p, p-multigrid), then two applies on each of the three
@@ -633,6 +673,8 @@ def main():
     ap.add_argument("--profile-apply", action="store_true", help="launch sequence for ncu captures")
     ap.add_argument("--sweep", action="store_true", help="order sweep at ~2M DOF, FP64 vs mixed precision")
     ap.add_argument("--paper-tables", action="store_true", help="the paper's Tables 1 and 4 recomputed on the GPU")
+    ap.add_argument("--mesh-independence", action="store_true",
+                    help="Table 6 setting: iterations vs fine mesh at a fixed 2x2 coarsest grid")
     ap.add_argument("--batched", action="store_true", help="512-solve batched workload vs FP64 one at a time")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="Poisson-arrival serving workload")
@@ -649,6 +691,8 @@ def main():
         return run_batched(args)
     if args.paper_tables:
         return run_paper_tables(args)
+    if args.mesh_independence:
+        return run_mesh_independence(args)
     if args.serve:
         return run_serve(args)
     if args.profile_apply:

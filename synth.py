@@ -76,6 +76,18 @@ def warped_var3d(nelem=16, order=4, hier="h", **kw):
     return problem(3, nelem, order, **base)
 
 
+def mesh_independence_problem(kind, E, order, smoother="cheb"):
+    """Mesh-independence study (the paper's Sec. 4.4 setting): 2D fine mesh E x E (E a power of
+    two >= 4), h-multigrid down to 2 x 2 elements at fixed order, V(3,3) point smoothing.
+    kind "2d-const": unit square, mu = 1; "2d-var": warped square, mu = 1 + 1e6 sum cos^2(2 pi x_i)
+    (the paper's amplitude for this study)."""
+    levels = E.bit_length() - 1          # E = 2^(levels) -> levels-1 halvings reach 2 x 2
+    base = dict(hier="h", n_hlevels=levels, smoother=smoother, nu_pre=3, nu_post=3)
+    if kind == "2d-var":
+        base.update(warp_amp=0.1, mu_a=1.0, mu_b=1e6, mu_k=2.0)
+    return problem(2, E, order, **base)
+
+
 # Seeds of the nodal right-hand sides for the 3D workloads.
 SEED_WARPED_VAR3D = 2
 SEED_PSWEEP3D = 3
