@@ -14,7 +14,10 @@ TEST INFRASTRUCTURE ONLY. Follows the paper's problem statement and discretizati
 Readings where the paper is silent: q = p+1 Gauss points per direction; mu is
 evaluated at the isoparametric image of each Gauss point; Dirichlet unknowns are
 eliminated (interior numbering); the warp x_i += amp * prod_j sin(pi x_j) and the
-coefficient mu = a + b sum_i cos^2(k pi x_i) are parameters of the workload.
+coefficient mu = a + b sum_i cos^2(k pi x_i) are parameters of the workload. A user may
+instead give the finest level's node coordinates (node_xyz) and a coefficient function
+(mu_fn); a coarser level then takes the finest level's isoparametric map evaluated at its
+own reference nodes (map_points).
 
 Global nodes are numbered lexicographically, x fastest, boundary nodes included
 (N = prod_i (E_i p + 1)); interior unknowns keep that order.
@@ -30,7 +33,10 @@ from . import basis
 class Discretization:
     """One level: structured E_1 x ... x E_d mesh of [0,1]^d, order p, mapped by the warp."""
 
-    def __init__(self, dim, nelem, p, warp_amp=0.0, mu_a=1.0, mu_b=0.0, mu_k=2.0, q=None):
+    def __init__(self, dim, nelem, p, warp_amp=0.0, mu_a=1.0, mu_b=0.0, mu_k=2.0, q=None,
+                 node_xyz=None, mu_fn=None):
+        """node_xyz: optional (dim, N) physical coordinates of the global nodes (replacing the
+        warp); mu_fn: optional callable, (dim, n) points -> (n,) coefficient values."""
         if dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")
         self.dim = dim
@@ -40,6 +46,8 @@ class Discretization:
         self.q = int(q) if q is not None else self.p + 1
         self.warp_amp = float(warp_amp)
         self.mu_a, self.mu_b, self.mu_k = float(mu_a), float(mu_b), float(mu_k)
+        self.node_xyz = None if node_xyz is None else np.asarray(node_xyz, dtype=np.float64)
+        self.mu_fn = mu_fn
         self.Nn = tuple(e * self.p + 1 for e in self.E)          # nodes per axis
         self.N = int(np.prod(self.Nn))
         self.n_elem = int(np.prod(self.E))
@@ -74,11 +82,40 @@ class Discretization:
         return X + self.warp_amp * s[:, None]
 
     def node_coords(self):
+        """(N, dim) physical node coordinates: the given ones, else the warp of the reference ones."""
+        if self.node_xyz is not None:
+            return self.node_xyz.T.copy()
         return self.warp(self.reference_coords())
 
     def mu(self, x):
-        """mu(x) = a + b sum_i cos^2(k pi x_i)."""
+        """mu(x) for points x of shape (n, dim): mu_fn if given, else a + b sum_i cos^2(k pi x_i)."""
+        if self.mu_fn is not None:
+            return np.asarray(self.mu_fn(np.ascontiguousarray(x.T)), dtype=np.float64).reshape(-1)
         return self.mu_a + self.mu_b * np.sum(np.cos(self.mu_k * np.pi * x) ** 2, axis=1)
+
+    def map_points(self, Xref):
+        """Isoparametric map of this level at reference points Xref (n, dim) in [0,1]^d: the
+        element containing each point (either one on an element face), then
+        x = sum_a x_a prod_axis l_{a_axis}(xi_axis) over its n^d nodes (Sec. 2.3's
+        isoparametric geometry). Returns (n, dim)."""
+        Xref = np.asarray(Xref, dtype=np.float64)
+        npt = Xref.shape[0]
+        X = self.node_coords()
+        eid = np.zeros(npt, dtype=np.int64)
+        stride = 1
+        weights = []
+        for ax in range(self.dim):
+            t = Xref[:, ax] * self.E[ax]
+            e = np.minimum(np.floor(t).astype(np.int64), self.E[ax] - 1)
+            e = np.maximum(e, 0)
+            weights.append(basis.lagrange_values(self.r, t - e))     # (npt, n)
+            eid += e * stride
+            stride *= self.E[ax]
+        nodes = self.element_nodes(eid)                               # (npt, n^d), x fastest
+        w = weights[self.dim - 1]
+        for ax in range(self.dim - 2, -1, -1):
+            w = (w[:, :, None] * weights[ax][:, None, :]).reshape(npt, -1)
+        return np.einsum("pa,pac->pc", w, X[nodes])
 
     # ---------------------------------------------------------------- elements
     def element_nodes(self, elems=None):

@@ -82,8 +82,17 @@ class Hierarchy:
         self.prob = prob
         self.levels = []
         for E, p in level_shapes(prob):
+            xyz = None
+            if prob.get("node_xyz") is not None:
+                # finest level: the given coordinates; coarser: the finest map at their nodes
+                if not self.levels:
+                    xyz = prob["node_xyz"]
+                else:
+                    ref = Discretization(prob["dim"], E, p).reference_coords()
+                    xyz = self.levels[0].disc.map_points(ref).T
             disc = Discretization(prob["dim"], E, p, warp_amp=prob["warp_amp"],
-                                  mu_a=prob["mu_a"], mu_b=prob["mu_b"], mu_k=prob["mu_k"])
+                                  mu_a=prob["mu_a"], mu_b=prob["mu_b"], mu_k=prob["mu_k"],
+                                  node_xyz=xyz, mu_fn=prob.get("mu_fn"))
             self.levels.append(Level(disc))
         for k in range(len(self.levels) - 1):
             self.levels[k].P = prolongation(self.levels[k].disc, self.levels[k + 1].disc)

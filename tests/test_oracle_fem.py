@@ -140,3 +140,51 @@ def test_apply_rows_equals_assembled_rows():
     rows = d.interior[rng.choice(d.n_interior, 12, replace=False)]
     ref = (d.assemble() @ x)[rows]
     assert np.allclose(d.apply_rows(x, rows), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+# ---- user-given geometry (node_xyz) and coefficient (mu_fn) -------------------------------
+
+def _poly_map(X):
+    """A smooth polynomial map of [0,1]^d of degree <= 3 per coordinate (fixes the boundary)."""
+    s = np.prod(X * (1.0 - X), axis=1)
+    return X + 0.5 * s[:, None] * (1.0 + X[:, :1])
+
+
+@pytest.mark.parametrize("dim,E,p", [(2, (3, 2), 3), (3, (2, 2, 1), 3), (2, (2, 3), 4)])
+def test_map_points_reproduces_polynomial_maps(dim, E, p):
+    """Isoparametric interpolation of a map of degree <= p is exact (Sec. 2.3 geometry):
+    map_points at arbitrary reference points equals the map itself."""
+    ref = fem.Discretization(dim, E, p)
+    d = fem.Discretization(dim, E, p, node_xyz=_poly_map(ref.reference_coords()).T)
+    pts = np.random.default_rng(3).uniform(0, 1, (200, dim))
+    pts[:5] = 0.5                                   # on element faces (either element is fine)
+    assert np.abs(d.map_points(pts) - _poly_map(pts)).max() < 1e-13
+    plain = fem.Discretization(dim, E, p)
+    assert np.abs(plain.map_points(pts) - pts).max() < 1e-14
+
+
+def test_given_coordinates_and_coefficient_reproduce_the_built_in_ones():
+    """node_xyz = the warp at the nodes and mu_fn = the cos^2 formula give the built-in operator
+    exactly; a constant mu_fn = c scales the mu = 1 operator by c."""
+    d0 = fem.Discretization(2, (3, 2), 3, warp_amp=0.1, mu_b=1e3)
+    xyz = d0.node_coords().T
+    d1 = fem.Discretization(2, (3, 2), 3, node_xyz=xyz,
+                            mu_fn=lambda x: 1.0 + 1e3 * np.sum(np.cos(2.0 * np.pi * x) ** 2, axis=0))
+    assert abs(d1.stiffness() - d0.stiffness()).max() == 0.0
+    one = fem.Discretization(2, (3, 2), 3, node_xyz=xyz)
+    three = fem.Discretization(2, (3, 2), 3, node_xyz=xyz, mu_fn=lambda x: np.full(x.shape[1], 3.0))
+    assert abs(three.stiffness() - 3.0 * one.stiffness()).max() <= 1e-14 * abs(one.stiffness()).max()
+
+
+def test_hierarchy_coarse_levels_use_the_finest_map():
+    """With given coordinates, a coarser level's nodes are the finest map at its reference
+    nodes: exact for a polynomial map the finest order reproduces (p = 4, degree 3)."""
+    import synth
+    from oracle import multigrid
+    prob = synth.problem(2, 8, 4, hier="p", n_hlevels=2)
+    fine = fem.Discretization(2, 8, 4)
+    prob = dict(prob, node_xyz=_poly_map(fine.reference_coords()).T)
+    H = multigrid.Hierarchy(prob, arnoldi=False)
+    for L in H.levels[1:]:
+        d = L.disc
+        assert np.abs(d.node_coords() - _poly_map(d.reference_coords())).max() < 1e-13
