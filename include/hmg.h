@@ -73,6 +73,9 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC
  *                        on the tensor cores with 16-bit operands and FP32 accumulation (levels of
  *                        higher order keep the FP32 apply); PCG then uses the flexible
  *                        (Polak-Ribiere) beta, since such a preconditioner is only nearly linear.
+ *   node_xyz, mu_fn    : optional user geometry and coefficient (Sec. 2: a general domain Omega
+ *                        and mu(x) >= mu_0 > 0); NULL keeps the warp map and the cos^2 formula.
+ *                        The solve server takes built-in geometry and coefficients only.
  *   solve_graph        : 1 (default): hmg_solve runs each solve as one instantiated CUDA graph with
  *                        a device-side loop (no host round trip per iteration); 0: host-driven loop
  *                        that reads the residual norm back every iteration. Same results.
@@ -94,6 +97,16 @@ typedef struct hmg_desc {
   unsigned long long arnoldi_seed;
   int smooth_prec;
   int solve_graph;
+  /* Optional, read during hmg_setup only (host memory, owned by the caller): */
+  const double* node_xyz; /* [dim][N] physical coordinates of the finest level's nodes (numbering
+                             x fastest, boundary nodes included), replacing the warp map; the
+                             mapped mesh must not fold (det J > 0, else HMG_EINVAL). Coarser levels
+                             take the finest level's isoparametric map at their own nodes. */
+  void (*mu_fn)(size_t n, const double* xyz, double* mu, void* user);
+                          /* coefficient at n Gauss points xyz[dim][n] -> mu[n] (> 0 and finite,
+                             else HMG_EINVAL), called on the setup thread once per level;
+                             replaces mu_a + mu_b sum cos^2(mu_k pi x_i). */
+  void* mu_user;          /* passed to mu_fn */
 } hmg_desc;
 
 typedef struct hmg_problem hmg_problem;

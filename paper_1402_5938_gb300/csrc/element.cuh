@@ -480,13 +480,14 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
 }
 
 // ---------------------------------------------------------------------------------------
-// Geometry, stage 1: node coordinates x = X + amp prod sin(pi X) of every element node,
-// interpolated to the Gauss points (x_q) and differentiated (dx_c/dxi_d), written to
-// J[e][c*(DIM+1) + s][NP] with s = 0 for x_q and s = 1+d for dx_c/dxi_d.
+// Geometry, stage 1: node coordinates of every element node -- x = X + amp prod sin(pi X), or
+// the given coords[c][global node] -- interpolated to the Gauss points (x_q) and
+// differentiated (dx_c/dxi_d), written to J[e][c*(DIM+1) + s][NP] with s = 0 for x_q and
+// s = 1+d for dx_c/dxi_d (isoparametric geometry, Sec. 2.3).
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N>
 __global__ void __launch_bounds__(256)
-k_geom_stage(double* __restrict__ J, const Mesh m, const double warp_amp,
+k_geom_stage(double* __restrict__ J, const Mesh m, const double warp_amp, const double* __restrict__ coords,
              const __grid_constant__ GeoTab<N> tab, const int epb) {
   constexpr int NP = Sh<DIM, N>::NP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -498,6 +499,11 @@ k_geom_stage(double* __restrict__ J, const Mesh m, const double warp_amp,
     for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
       const int e = t / NP, a = t - e * NP;
       const long long eg = e0 + e;
+      if (coords != nullptr) {
+        bool bd;
+        U[t] = coords[c * m.N + elem_node<DIM, N>(m, eg, a, bd)];
+        continue;
+      }
       const int idx[3] = {a % N, (a / N) % N, a / (N * N)};
       const long long ee[3] = {eg % m.E[0], (eg / m.E[0]) % m.E[1], eg / ((long long)m.E[0] * m.E[1])};
       double X[3], s = 1.0;
@@ -525,12 +531,12 @@ k_geom_stage(double* __restrict__ J, const Mesh m, const double warp_amp,
 }
 
 // Geometry, stage 2: G = mu(x_q) w_q det(J) J^-1 J^-T (symmetric, NC entries) and
-// w_q det(J), one thread per Gauss point. Returns the minimum det J through *min_det
-// (as ordered int bits of a positive double; 0 if non-positive).
+// w_q det(J), one thread per Gauss point; mu from the formula a + b sum cos^2(k pi x), or the
+// given values mu_arr[e * NP + q]. Sets *bad where det J <= 0.
 template <int DIM, int N>
 __global__ void k_geom_point(const double* __restrict__ J, double* __restrict__ G,
                              double* __restrict__ wdetJ, const Mesh m, const double mu_a,
-                             const double mu_b, const double mu_k,
+                             const double mu_b, const double mu_k, const double* __restrict__ mu_arr,
                              const __grid_constant__ GeoTab<N> tab, int* __restrict__ bad) {
   constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
   const long long tot = m.nelem * NP;
@@ -545,11 +551,15 @@ __global__ void k_geom_point(const double* __restrict__ J, double* __restrict__ 
       for (int d = 0; d < DIM; ++d) A[c][d] = src[(c * (DIM + 1) + 1 + d) * NP];
     }
     double mu = 0.0;
-    for (int c = 0; c < DIM; ++c) {
-      const double cs = cospi(mu_k * xq[c]);
-      mu += cs * cs;
+    if (mu_arr != nullptr) {
+      mu = mu_arr[t];
+    } else {
+      for (int c = 0; c < DIM; ++c) {
+        const double cs = cospi(mu_k * xq[c]);
+        mu += cs * cs;
+      }
+      mu = mu_a + mu_b * mu;
     }
-    mu = mu_a + mu_b * mu;
     double w = tab.w[q % N] * tab.w[(q / N) % N];
     if (DIM == 3) w *= tab.w[q / (N * N)];
     double* g = G + e * NC * NP + q;
@@ -585,6 +595,68 @@ __global__ void k_geom_point(const double* __restrict__ J, double* __restrict__ 
       g[2 * NP] = s * (a10 * a10 + a11 * a11);
       wdetJ[e * NP + q] = w * det;
     }
+  }
+}
+
+// Gauss-point coordinates out of the stage-1 buffer: xq[c][e * NP + q].
+template <int DIM, int N>
+__global__ void k_extract_xq(const double* __restrict__ J, double* __restrict__ xq, const Mesh m) {
+  constexpr int NP = Sh<DIM, N>::NP;
+  const long long tot = m.nelem * NP;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / NP;
+    const int q = (int)(t - e * NP);
+    for (int c = 0; c < DIM; ++c) xq[c * tot + t] = J[(e * (DIM * (DIM + 1)) + c * (DIM + 1)) * NP + q];
+  }
+}
+
+// GLL nodes on [0,1] of the finest level and of a coarser one (n0, nk <= kMaxN).
+struct MapNodes {
+  double r0[kMaxN];
+  double rk[kMaxN];
+};
+
+// Node coordinates of a coarser level from the finest level's isoparametric map: each node's
+// reference coordinate X (element ec of the coarse mesh, GLL node i) lies in the fine element
+// ef = floor(X E0) along each axis (the last one at X = 1), at xi = X E0 - ef, where
+// x(X) = sum over the fine element's nodes of x_a prod_axis l_{a_axis}(xi_axis) (Sec. 2.3's
+// isoparametric geometry). Xk[c][node], X0[c][fine node].
+template <int DIM>
+__global__ void k_level_coords(const double* __restrict__ X0, const Mesh m0, const Mesh mk,
+                               const __grid_constant__ MapNodes nodes, double* __restrict__ Xk) {
+  const int n0 = m0.p + 1;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < mk.N;
+       g += (long long)gridDim.x * blockDim.x) {
+    long long I[3] = {g % mk.Nn[0], (g / mk.Nn[0]) % mk.Nn[1], DIM == 3 ? g / (mk.Nn[0] * mk.Nn[1]) : 0};
+    long long ef[3] = {0, 0, 0};
+    double w[3][kMaxN];
+    for (int a = 0; a < DIM; ++a) {
+      const long long ec = min(I[a] / mk.p, (long long)mk.E[a] - 1);
+      const double X = ((double)ec + nodes.rk[I[a] - ec * mk.p]) / (double)mk.E[a];
+      const double tt = X * (double)m0.E[a];
+      long long f = (long long)floor(tt);
+      f = max(0LL, min(f, (long long)m0.E[a] - 1));
+      ef[a] = f;
+      const double xi = tt - (double)f;
+      for (int j = 0; j < n0; ++j) {
+        double l = 1.0;
+        for (int q = 0; q < n0; ++q)
+          if (q != j) l *= (xi - nodes.r0[q]) / (nodes.r0[j] - nodes.r0[q]);
+        w[a][j] = l;
+      }
+    }
+    double x[3] = {0.0, 0.0, 0.0};
+    const int nk2 = DIM == 3 ? n0 : 1;
+    for (int k = 0; k < nk2; ++k)
+      for (int j = 0; j < n0; ++j)
+        for (int i = 0; i < n0; ++i) {
+          const double wt = w[0][i] * w[1][j] * (DIM == 3 ? w[2][k] : 1.0);
+          const long long node = ((DIM == 3 ? (ef[2] * m0.p + k) : 0) * m0.Nn[1] + ef[1] * m0.p + j) * m0.Nn[0] +
+                                 ef[0] * m0.p + i;
+          for (int c = 0; c < DIM; ++c) x[c] += wt * X0[c * m0.N + node];
+        }
+    for (int c = 0; c < DIM; ++c) Xk[c * mk.N + g] = x[c];
   }
 }
 

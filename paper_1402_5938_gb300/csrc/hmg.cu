@@ -734,7 +734,26 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   int* bad = nullptr;
   TRY(cudaMalloc((void**)&Jstage, max_stage));
   if (cudaMalloc((void**)&bad, sizeof(int)) != cudaSuccess) { cudaFree(Jstage); set_error("alloc"); return HMG_ENOMEM; }
+  // user geometry / coefficient: finest coordinates, a coarse level's coordinates, Gauss points, mu
+  std::vector<void*> tmp;
+  auto talloc = [&](void** ptr, size_t bytes) -> hmg_status {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) { set_error("device allocation failed"); return HMG_ENOMEM; }
+    tmp.push_back(*ptr);
+    return HMG_OK;
+  };
+  double *X0 = nullptr, *Xk = nullptr, *xq_d = nullptr, *mu_d = nullptr;
+  std::vector<double> xq_h, mu_h;
   hmg_status st = [&]() -> hmg_status {
+    const long long nq0 = P.L[0].m.nelem * np_of(P.L[0].m);
+    if (D.node_xyz) {
+      CHECK(talloc((void**)&X0, (size_t)D.dim * N0 * sizeof(double)));
+      CHECK(talloc((void**)&Xk, (size_t)D.dim * N0 * sizeof(double)));
+      TRY(cudaMemcpyAsync(X0, D.node_xyz, (size_t)D.dim * N0 * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    if (D.mu_fn) {
+      CHECK(talloc((void**)&xq_d, (size_t)D.dim * nq0 * sizeof(double)));
+      CHECK(talloc((void**)&mu_d, (size_t)nq0 * sizeof(double)));
+    }
     const bool mixed = D.smooth_prec != HMG_PREC_FP64;
     const bool lowp = D.smooth_prec == HMG_PREC_FP16 || D.smooth_prec == HMG_PREC_BF16;
     for (size_t k = 0; k < P.L.size(); ++k) {
@@ -750,7 +769,27 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       TRY(P.alloc((void**)&l.r, n * sizeof(double)));
       TRY(P.alloc((void**)&l.d, n * sizeof(double)));
       TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
-      TRY(launch_geometry(l.m, l.basis, D.warp_amp, D.mu_a, D.mu_b, D.mu_k, Jstage, l.G, l.wdetJ, bad, s));
+      const double* coords = nullptr;
+      if (D.node_xyz) {
+        if (k > 0) TRY(launch_level_coords(P.L[0].m, P.L[0].basis, X0, l.m, l.basis, Xk, s));
+        coords = k == 0 ? X0 : Xk;
+      }
+      TRY(launch_geom_stage(l.m, l.basis, D.warp_amp, coords, Jstage, s));
+      const double* mu_arr = nullptr;
+      if (D.mu_fn) {  // the user's coefficient at this level's Gauss points
+        const size_t nq = (size_t)gsz;
+        xq_h.resize((size_t)D.dim * nq);
+        mu_h.assign(nq, 0.0);
+        TRY(launch_extract_xq(l.m, l.basis, Jstage, xq_d, s));
+        TRY(cudaMemcpyAsync(xq_h.data(), xq_d, xq_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TRY(cudaStreamSynchronize(s));
+        D.mu_fn(nq, xq_h.data(), mu_h.data(), D.mu_user);
+        for (double v : mu_h)
+          if (!(v > 0.0) || !std::isfinite(v)) { set_error("mu_fn returned a non-positive or non-finite value"); return HMG_EINVAL; }
+        TRY(cudaMemcpyAsync(mu_d, mu_h.data(), nq * sizeof(double), cudaMemcpyHostToDevice, s));
+        mu_arr = mu_d;
+      }
+      TRY(launch_geom_point(l.m, l.basis, D.mu_a, D.mu_b, D.mu_k, mu_arr, Jstage, l.G, l.wdetJ, bad, s));
       int hbad = 0;
       TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaStreamSynchronize(s));
@@ -795,6 +834,8 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
     TRY(cudaStreamSynchronize(s));
     return HMG_OK;
   }();
+  cudaStreamSynchronize(s);  // nothing may still read the temporaries or the host staging vectors
+  for (void* t : tmp) cudaFree(t);
   cudaFree(Jstage);
   cudaFree(bad);
   return st;
@@ -1098,7 +1139,11 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   add(16);
   res += 1001 * 8;                        // residual history of graph solves (default capacity)
   res += allocs * 512;                    // allocation granularity
-  const size_t temp = std::max(max_stage + 16, std::max(arnoldi, (size_t)nI * 16));
+  size_t custom = 0;  // setup temporaries of user geometry / coefficient
+  const size_t nq0 = (size_t)(ms[0].nelem * np_of(ms[0]));
+  if (D.node_xyz) custom += 2 * (size_t)D.dim * N0 * 8;
+  if (D.mu_fn) custom += (size_t)(D.dim + 1) * nq0 * 8;
+  const size_t temp = std::max(max_stage + 16 + custom, std::max(arnoldi, (size_t)nI * 16));
   if (resident) *resident = res;
   if (peak) *peak = res + temp;
   return HMG_OK;
@@ -1140,6 +1185,9 @@ hmg_status hmg_desc_default(hmg_desc* d) {
   d->arnoldi_seed = 0;
   d->smooth_prec = HMG_PREC_FP64;
   d->solve_graph = 1;
+  d->node_xyz = nullptr;
+  d->mu_fn = nullptr;
+  d->mu_user = nullptr;
   return HMG_OK;
 }
 

@@ -30,11 +30,22 @@ cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, f
 cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int nc, int np, int dim,
                             int prec, cudaStream_t s);
 
-// Geometry: stage buffer J [E][dim*(dim+1)][NP], then G [E][NC][NP] and wdetJ [E][NP].
-// *bad (device int) is set to 1 where det J <= 0.
-cudaError_t launch_geometry(const Mesh& m, const Basis1D& b, double warp_amp, double mu_a,
-                            double mu_b, double mu_k, double* Jstage, double* G, double* wdetJ,
-                            int* bad, cudaStream_t s);
+// Geometry, stage 1: Gauss-point coordinates and Jacobians into the stage buffer
+// J [E][dim*(dim+1)][NP], from the warp map (coords = nullptr) or given node coordinates
+// coords[c][node] of this level.
+cudaError_t launch_geom_stage(const Mesh& m, const Basis1D& b, double warp_amp, const double* coords,
+                              double* Jstage, cudaStream_t s);
+// Geometry, stage 2: G [E][NC][NP] and wdetJ [E][NP] with mu from the formula (mu_arr = nullptr)
+// or given values mu_arr[e * NP + q]. *bad (device int) is set to 1 where det J <= 0.
+cudaError_t launch_geom_point(const Mesh& m, const Basis1D& b, double mu_a, double mu_b, double mu_k,
+                              const double* mu_arr, const double* Jstage, double* G, double* wdetJ, int* bad,
+                              cudaStream_t s);
+// Gauss-point coordinates xq[c][e * NP + q] out of the stage buffer.
+cudaError_t launch_extract_xq(const Mesh& m, const Basis1D& b, const double* Jstage, double* xq, cudaStream_t s);
+// Node coordinates Xk[c][node] of level mesh mk from the finest level's isoparametric map
+// (node coordinates X0[c][node] on mesh m0).
+cudaError_t launch_level_coords(const Mesh& m0, const Basis1D& b0, const double* X0, const Mesh& mk,
+                                const Basis1D& bk, double* Xk, cudaStream_t s);
 // diag += diag(A) over interior nodes.
 cudaError_t launch_diag(const Mesh& m, const Basis1D& b, const double* G, double* diag, cudaStream_t s);
 // b += M f over interior rows.

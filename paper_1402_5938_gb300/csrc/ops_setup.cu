@@ -8,23 +8,43 @@ namespace hmg {
 namespace {
 
 template <int DIM>
-cudaError_t geometry_dim(const Mesh& m, const Basis1D& b, double amp, double mu_a, double mu_b,
-                         double mu_k, double* Js, double* G, double* wdetJ, int* bad, cudaStream_t s) {
+cudaError_t geom_stage_dim(const Mesh& m, const Basis1D& b, double amp, const double* coords, double* Js,
+                           cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
     constexpr int NP = Sh<DIM, N>::NP;
-    const GeoTab<N> tab = make_geotab<N>(b);
     const size_t per = (size_t)(1 + DIM) * NP * sizeof(double);
     const int epb = epb_for(per);
     auto k1 = k_geom_stage<DIM, N>;
     cudaError_t e = ensure_smem(k1, per * epb);
     if (e != cudaSuccess) return e;
     const long long blocks = (m.nelem + epb - 1) / epb;
-    k1<<<(unsigned)blocks, 256, per * epb, s>>>(Js, m, amp, tab, epb);
-    if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
+    k1<<<(unsigned)blocks, 256, per * epb, s>>>(Js, m, amp, coords, make_geotab<N>(b), epb);
+    return counted(cudaGetLastError());
+  });
+}
+
+template <int DIM>
+cudaError_t geom_point_dim(const Mesh& m, const Basis1D& b, double mu_a, double mu_b, double mu_k,
+                           const double* mu_arr, const double* Js, double* G, double* wdetJ, int* bad,
+                           cudaStream_t s) {
+  return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
+    constexpr int N = decltype(nc)::value;
+    constexpr int NP = Sh<DIM, N>::NP;
     const long long tot = m.nelem * NP;
     const unsigned g2 = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 64);
-    k_geom_point<DIM, N><<<g2, 256, 0, s>>>(Js, G, wdetJ, m, mu_a, mu_b, mu_k, tab, bad);
+    k_geom_point<DIM, N><<<g2, 256, 0, s>>>(Js, G, wdetJ, m, mu_a, mu_b, mu_k, mu_arr, make_geotab<N>(b), bad);
+    return counted(cudaGetLastError());
+  });
+}
+
+template <int DIM>
+cudaError_t extract_xq_dim(const Mesh& m, const Basis1D& b, const double* Js, double* xq, cudaStream_t s) {
+  return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
+    constexpr int N = decltype(nc)::value;
+    const long long tot = m.nelem * Sh<DIM, N>::NP;
+    const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 64);
+    k_extract_xq<DIM, N><<<g, 256, 0, s>>>(Js, xq, m);
     return counted(cudaGetLastError());
   });
 }
@@ -81,10 +101,34 @@ cudaError_t dense_dim(const Mesh& m, const Basis1D& b, const double* G, double* 
 
 }  // namespace
 
-cudaError_t launch_geometry(const Mesh& m, const Basis1D& b, double amp, double mu_a, double mu_b,
-                            double mu_k, double* Js, double* G, double* wdetJ, int* bad, cudaStream_t s) {
-  return m.dim == 3 ? geometry_dim<3>(m, b, amp, mu_a, mu_b, mu_k, Js, G, wdetJ, bad, s)
-                    : geometry_dim<2>(m, b, amp, mu_a, mu_b, mu_k, Js, G, wdetJ, bad, s);
+cudaError_t launch_geom_stage(const Mesh& m, const Basis1D& b, double amp, const double* coords, double* Js,
+                              cudaStream_t s) {
+  return m.dim == 3 ? geom_stage_dim<3>(m, b, amp, coords, Js, s) : geom_stage_dim<2>(m, b, amp, coords, Js, s);
+}
+
+cudaError_t launch_geom_point(const Mesh& m, const Basis1D& b, double mu_a, double mu_b, double mu_k,
+                              const double* mu_arr, const double* Js, double* G, double* wdetJ, int* bad,
+                              cudaStream_t s) {
+  return m.dim == 3 ? geom_point_dim<3>(m, b, mu_a, mu_b, mu_k, mu_arr, Js, G, wdetJ, bad, s)
+                    : geom_point_dim<2>(m, b, mu_a, mu_b, mu_k, mu_arr, Js, G, wdetJ, bad, s);
+}
+
+cudaError_t launch_extract_xq(const Mesh& m, const Basis1D& b, const double* Js, double* xq, cudaStream_t s) {
+  return m.dim == 3 ? extract_xq_dim<3>(m, b, Js, xq, s) : extract_xq_dim<2>(m, b, Js, xq, s);
+}
+
+cudaError_t launch_level_coords(const Mesh& m0, const Basis1D& b0, const double* X0, const Mesh& mk,
+                                const Basis1D& bk, double* Xk, cudaStream_t s) {
+  MapNodes nodes{};
+  for (int i = 0; i < b0.n; ++i) nodes.r0[i] = b0.r[i];
+  for (int i = 0; i < bk.n; ++i) nodes.rk[i] = bk.r[i];
+  const unsigned g = (unsigned)std::min<long long>((mk.N + 255) / 256, 152LL * 64);
+  if (mk.N == 0) return cudaSuccess;
+  if (m0.dim == 3)
+    k_level_coords<3><<<g, 256, 0, s>>>(X0, m0, mk, nodes, Xk);
+  else
+    k_level_coords<2><<<g, 256, 0, s>>>(X0, m0, mk, nodes, Xk);
+  return counted(cudaGetLastError());
 }
 
 cudaError_t launch_diag(const Mesh& m, const Basis1D& b, const double* G, double* diag, cudaStream_t s) {

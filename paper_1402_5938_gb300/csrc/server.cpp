@@ -271,6 +271,7 @@ hmg_status hmg_server_submit(hmg_server* s, const hmg_desc* desc, const double* 
     return HMG_EINVAL;
   const size_t n = hmg_desc_ndof(desc);
   if (n == 0) return HMG_EINVAL;
+  if (desc->node_xyz || desc->mu_fn) return HMG_EINVAL;  // the server caches by descriptor values only
   size_t res = 0, peak = 0;
   hmg_status st = hmg_estimate_bytes(desc, &res, &peak);
   if (st != HMG_OK) return st;

@@ -27,6 +27,11 @@ class HmgError(RuntimeError):
         self.status = status
 
 
+# void mu_fn(size_t n, const double* xyz, double* mu, void* user)
+MU_FN = ctypes.CFUNCTYPE(None, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                         ctypes.c_void_p)
+
+
 class Desc(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int), ("nelem", ctypes.c_int * 3), ("order", ctypes.c_int),
@@ -36,6 +41,7 @@ class Desc(ctypes.Structure):
         ("omega", ctypes.c_double), ("arnoldi_iters", ctypes.c_int),
         ("cheb_lo_frac", ctypes.c_double), ("cheb_safety", ctypes.c_double),
         ("arnoldi_seed", ctypes.c_ulonglong), ("smooth_prec", ctypes.c_int), ("solve_graph", ctypes.c_int),
+        ("node_xyz", ctypes.POINTER(ctypes.c_double)), ("mu_fn", MU_FN), ("mu_user", ctypes.c_void_p),
     ]
 
 
@@ -145,6 +151,24 @@ def make_desc(prob: dict) -> Desc:
     d.arnoldi_seed = prob.get("arnoldi_seed", 0)
     d.smooth_prec = PREC[prob.get("smooth_prec", "fp64")]
     d.solve_graph = int(prob.get("solve_graph", 1))
+    keep = []
+    if prob.get("node_xyz") is not None:
+        xyz = np.ascontiguousarray(prob["node_xyz"], dtype=np.float64)
+        keep.append(xyz)
+        d.node_xyz = xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if prob.get("mu_fn") is not None:
+        f, dim = prob["mu_fn"], d.dim
+
+        def _mu(n, xyz, mu, user):
+            try:
+                x = np.ctypeslib.as_array(xyz, shape=(dim * n,)).reshape(dim, n)
+                np.ctypeslib.as_array(mu, shape=(n,))[:] = np.asarray(f(x), dtype=np.float64).reshape(n)
+            except Exception:  # reported by the library as a non-finite coefficient
+                np.ctypeslib.as_array(mu, shape=(n,))[:] = np.nan
+        cb = MU_FN(_mu)
+        keep.append(cb)
+        d.mu_fn = cb
+    d._keep = keep  # the arrays and the callback must outlive hmg_setup
     return d
 
 
