@@ -121,6 +121,10 @@ hmg_status hmg_desc_default(hmg_desc* d);
  * operator. Work runs on `stream`; the call synchronizes it. Owns all memory it allocates.
  * Errors: HMG_EINVAL (bad descriptor), HMG_ENOMEM, HMG_EDEVICE. */
 hmg_status hmg_setup(const hmg_desc* desc, void* stream, hmg_problem** out);
+/* Release a hierarchy. Work the caller enqueued on it (hmg_apply, hmg_vcycle, ... on any
+ * stream) must have completed: work on the legacy default stream is waited for, other streams
+ * are the caller's to synchronize. Device memory returns to the stream-ordered pool and pinned
+ * host buffers to the library's pool, without a device-wide synchronization. */
 hmg_status hmg_destroy(hmg_problem* prob);
 
 /* Node count N of the finest level a descriptor describes (0 if the descriptor is invalid). */

@@ -72,6 +72,15 @@ inline cudaError_t counted(cudaError_t e, long long n = 1) {
   return e;
 }
 
+// Page-locked host blocks from a process-wide pool (pass the same size to pinned_free).
+void* pinned_alloc(size_t bytes);
+void pinned_free(void* p, size_t bytes);
+
+// Device memory from the device's stream-ordered pool (no implicit device synchronization,
+// unlike cudaMalloc / cudaFree); the first call on a device keeps freed memory cached in the pool.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
 struct ProblemImpl;  // defined in hmg.cu
 
 }  // namespace hmg

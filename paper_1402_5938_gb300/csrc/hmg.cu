@@ -135,13 +135,15 @@ struct ProblemImpl {
   long long lkern[2][3] = {};
   bool capturing = false;
 
-  // Device allocation zeroed in order on the setup stream (the caller's stream may be a
-  // non-blocking stream that the legacy default stream does not order against).
+  // Device allocation from the stream-ordered pool, zeroed in order on the setup stream (the
+  // caller's stream may be a non-blocking stream that the legacy default stream does not order
+  // against); no implicit device synchronization, so setups overlap other streams' work.
   cudaStream_t setup_stream = nullptr;
+  cudaStream_t own = nullptr;  // private stream on which destruction returns the memory
   cudaError_t alloc(void** p, size_t nbytes) {
     *p = nullptr;
     if (nbytes == 0) nbytes = 16;
-    cudaError_t e = cudaMalloc(p, nbytes);
+    cudaError_t e = dev_alloc(p, nbytes, setup_stream);
     if (e != cudaSuccess) return e;
     dev_allocs.push_back(*p);
     bytes += nbytes;
@@ -154,12 +156,25 @@ struct ProblemImpl {
       for (int k = 0; k < 3; ++k)
         if (lexec[m][k]) cudaGraphExecDestroy(lexec[m][k]);
     }
-    if (cap_stream) cudaStreamDestroy(cap_stream);
-    for (void* p : dev_allocs) cudaFree(p);
-    if (hist) cudaFree(hist);
-    if (hostS) cudaFreeHost(hostS);
-    if (host_ctrl) cudaFreeHost(host_ctrl);
-    if (host_hist) cudaFreeHost(host_hist);
+    // callers finish their work on the problem first; work on the legacy default stream is
+    // waited for here, then the memory goes back to the pool without a device-wide barrier
+    cudaStreamSynchronize(nullptr);
+    if (cap_stream) {
+      cudaStreamSynchronize(cap_stream);
+      cudaStreamDestroy(cap_stream);
+    }
+    cudaStream_t fs = own;
+    for (void* p : dev_allocs) dev_free(p, fs);
+    dev_free(hist, fs);
+    if (fs) {
+      cudaStreamSynchronize(fs);
+      cudaStreamDestroy(fs);
+    } else {
+      cudaStreamSynchronize(nullptr);
+    }
+    pinned_free(hostS, 16 * sizeof(double));
+    pinned_free(host_ctrl, 4 * sizeof(int));
+    pinned_free(host_hist, (size_t)(hist_cap + 1) * sizeof(double));
   }
 };
 
@@ -512,12 +527,12 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
   std::vector<double*> V(m + 1, nullptr);
   double* Hd = nullptr;
   std::vector<void*> tmp;
-  auto cleanup = [&]() { for (void* p : tmp) cudaFree(p); };
+  auto cleanup = [&]() { for (void* p : tmp) dev_free(p, s); };
   for (int j = 0; j <= m; ++j) {
-    if (cudaMalloc((void**)&V[j], n * sizeof(double)) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
+    if (dev_alloc((void**)&V[j], n * sizeof(double), s) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
     tmp.push_back(V[j]);
   }
-  if (cudaMalloc((void**)&Hd, (m + 1) * m * sizeof(double)) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
+  if (dev_alloc((void**)&Hd, (m + 1) * m * sizeof(double), s) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
   tmp.push_back(Hd);
   hmg_status st = [&]() -> hmg_status {
     TRY(cudaMemsetAsync(Hd, 0, (m + 1) * m * sizeof(double), s));
@@ -679,12 +694,12 @@ hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
   TRY(cudaMemcpyAsync(l.gmap, gm.data(), nI * sizeof(long long), cudaMemcpyHostToDevice, s));
   TRY(launch_elem_dense(l.m, l.basis, l.G, l.Ainv, nI, s));
   double *rowk = nullptr, *colk = nullptr;
-  TRY(cudaMalloc((void**)&rowk, nI * sizeof(double)));
-  if (cudaMalloc((void**)&colk, nI * sizeof(double)) != cudaSuccess) { cudaFree(rowk); set_error("alloc"); return HMG_ENOMEM; }
+  TRY(dev_alloc((void**)&rowk, nI * sizeof(double), s));
+  if (dev_alloc((void**)&colk, nI * sizeof(double), s) != cudaSuccess) { dev_free(rowk, s); set_error("alloc"); return HMG_ENOMEM; }
   cudaError_t e = gauss_jordan_inverse(l.Ainv, nI, rowk, colk, s);
+  dev_free(rowk, s);
+  dev_free(colk, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaFree(rowk);
-  cudaFree(colk);
   TRY(e);
   TRY(e2);
   return HMG_OK;
@@ -693,6 +708,7 @@ hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
 hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   const hmg_desc& D = P.desc;
   P.setup_stream = s;
+  TRY(cudaStreamCreateWithFlags(&P.own, cudaStreamNonBlocking));
   std::vector<std::pair<std::vector<int>, int>> shapes;
   CHECK(level_shapes(D, shapes));
   P.L.resize(shapes.size());
@@ -717,7 +733,8 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   TRY(P.alloc((void**)&P.S, 64 * sizeof(double)));
   TRY(P.alloc((void**)&P.err, sizeof(int)));
   TRY(P.alloc((void**)&P.partial, kRedBlocks * sizeof(double)));
-  TRY(cudaMallocHost((void**)&P.hostS, 16 * sizeof(double)));
+  P.hostS = static_cast<double*>(pinned_alloc(16 * sizeof(double)));
+  if (!P.hostS) { set_error("pinned host allocation failed"); return HMG_ENOMEM; }
   TRY(P.alloc(&P.t1, max_tbuf * sizeof(double)));
   TRY(P.alloc(&P.t2, max_tbuf * sizeof(double)));
   const long long N0 = P.L[0].m.N;
@@ -728,16 +745,17 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   TRY(P.alloc((void**)&P.gb, N0 * sizeof(double)));
   TRY(P.alloc((void**)&P.gu, N0 * sizeof(double)));
   TRY(P.alloc((void**)&P.ctrl, 4 * sizeof(int)));
-  TRY(cudaMallocHost((void**)&P.host_ctrl, 4 * sizeof(int)));
+  P.host_ctrl = static_cast<int*>(pinned_alloc(4 * sizeof(int)));
+  if (!P.host_ctrl) { set_error("pinned host allocation failed"); return HMG_ENOMEM; }
 
   double* Jstage = nullptr;
   int* bad = nullptr;
-  TRY(cudaMalloc((void**)&Jstage, max_stage));
-  if (cudaMalloc((void**)&bad, sizeof(int)) != cudaSuccess) { cudaFree(Jstage); set_error("alloc"); return HMG_ENOMEM; }
+  TRY(dev_alloc((void**)&Jstage, max_stage, s));
+  if (dev_alloc((void**)&bad, sizeof(int), s) != cudaSuccess) { dev_free(Jstage, s); set_error("alloc"); return HMG_ENOMEM; }
   // user geometry / coefficient: finest coordinates, a coarse level's coordinates, Gauss points, mu
   std::vector<void*> tmp;
   auto talloc = [&](void** ptr, size_t bytes) -> hmg_status {
-    if (cudaMalloc(ptr, bytes) != cudaSuccess) { set_error("device allocation failed"); return HMG_ENOMEM; }
+    if (dev_alloc(ptr, bytes, s) != cudaSuccess) { set_error("device allocation failed"); return HMG_ENOMEM; }
     tmp.push_back(*ptr);
     return HMG_OK;
   };
@@ -834,10 +852,10 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
     TRY(cudaStreamSynchronize(s));
     return HMG_OK;
   }();
-  cudaStreamSynchronize(s);  // nothing may still read the temporaries or the host staging vectors
-  for (void* t : tmp) cudaFree(t);
-  cudaFree(Jstage);
-  cudaFree(bad);
+  for (void* t : tmp) dev_free(t, s);
+  dev_free(Jstage, s);
+  dev_free(bad, s);
+  cudaStreamSynchronize(s);  // nothing may still read the host staging vectors
   return st;
 }
 
@@ -894,10 +912,15 @@ hmg_status build_graph(ProblemImpl& P, int mode, int cap) {
       if (P.gexec[m]) { cudaGraphExecDestroy(P.gexec[m]); P.gexec[m] = nullptr; }
       if (P.graph[m]) { cudaGraphDestroy(P.graph[m]); P.graph[m] = nullptr; }
     }
-    if (P.hist) { TRY(cudaFree(P.hist)); P.hist = nullptr; }
-    if (P.host_hist) { TRY(cudaFreeHost(P.host_hist)); P.host_hist = nullptr; }
-    TRY(cudaMalloc((void**)&P.hist, (cap + 1) * sizeof(double)));
-    TRY(cudaMallocHost((void**)&P.host_hist, (cap + 1) * sizeof(double)));
+    if (!P.cap_stream) TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+    dev_free(P.hist, P.cap_stream);
+    P.hist = nullptr;
+    pinned_free(P.host_hist, (size_t)(P.hist_cap + 1) * sizeof(double));
+    P.host_hist = nullptr;
+    TRY(dev_alloc((void**)&P.hist, (cap + 1) * sizeof(double), P.cap_stream));
+    TRY(cudaStreamSynchronize(P.cap_stream));
+    P.host_hist = static_cast<double*>(pinned_alloc((size_t)(cap + 1) * sizeof(double)));
+    if (!P.host_hist) { set_error("pinned host allocation failed"); return HMG_ENOMEM; }
     P.hist_cap = cap;
   }
   if (!P.cap_stream) TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));

@@ -9,6 +9,8 @@
 // needs their memory. Every request records its latency from submit to completion.
 #include <string.h>
 
+#include "common.cuh"
+
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -169,12 +171,21 @@ void hmg_server::run(int w) {
     size_t grow = 0;
     if (!P) st = hmg_setup(&r->desc, W.stream, &P);
     if (st == HMG_OK && n > W.cap) {
-      if (W.d_f) { cudaFree(W.d_f); cudaFree(W.d_b); cudaFree(W.d_u); cudaFreeHost(W.h_f); cudaFreeHost(W.h_u); }
+      // stream-ordered device memory and pooled pinned memory: no implicit device barrier
+      if (W.d_f) {
+        hmg::dev_free(W.d_f, W.stream);
+        hmg::dev_free(W.d_b, W.stream);
+        hmg::dev_free(W.d_u, W.stream);
+        hmg::pinned_free(W.h_f, W.cap * 8);
+        hmg::pinned_free(W.h_u, W.cap * 8);
+      }
       W.d_f = W.d_b = W.d_u = W.h_f = W.h_u = nullptr;
       grow = (n - W.cap) * 3 * sizeof(double);
-      if (cudaMalloc(&W.d_f, n * 8) != cudaSuccess || cudaMalloc(&W.d_b, n * 8) != cudaSuccess ||
-          cudaMalloc(&W.d_u, n * 8) != cudaSuccess || cudaMallocHost(&W.h_f, n * 8) != cudaSuccess ||
-          cudaMallocHost(&W.h_u, n * 8) != cudaSuccess) {
+      W.h_f = static_cast<double*>(hmg::pinned_alloc(n * 8));
+      W.h_u = static_cast<double*>(hmg::pinned_alloc(n * 8));
+      if (hmg::dev_alloc((void**)&W.d_f, n * 8, W.stream) != cudaSuccess ||
+          hmg::dev_alloc((void**)&W.d_b, n * 8, W.stream) != cudaSuccess ||
+          hmg::dev_alloc((void**)&W.d_u, n * 8, W.stream) != cudaSuccess || !W.h_f || !W.h_u) {
         st = HMG_ENOMEM;
         W.cap = 0;
       } else {
@@ -350,8 +361,17 @@ hmg_status hmg_server_destroy(hmg_server* s) {
   cudaSetDevice(s->device);
   for (auto& c : s->cache) hmg_destroy(c.second.prob);
   for (auto& w : s->workers) {
-    if (w.d_f) { cudaFree(w.d_f); cudaFree(w.d_b); cudaFree(w.d_u); cudaFreeHost(w.h_f); cudaFreeHost(w.h_u); }
-    if (w.stream) cudaStreamDestroy(w.stream);
+    if (w.d_f) {
+      hmg::dev_free(w.d_f, w.stream);
+      hmg::dev_free(w.d_b, w.stream);
+      hmg::dev_free(w.d_u, w.stream);
+      hmg::pinned_free(w.h_f, w.cap * 8);
+      hmg::pinned_free(w.h_u, w.cap * 8);
+    }
+    if (w.stream) {
+      cudaStreamSynchronize(w.stream);
+      cudaStreamDestroy(w.stream);
+    }
   }
   cudaSetDevice(prev);
   delete s;
