@@ -519,38 +519,44 @@ hmg_status pcg_rho_beta(ProblemImpl& P, const double* z, const double* r, long l
   return dot_to(P, z, r, n, FIN_RHO_BETA, S_RHO, S_BETA, false, s);
 }
 
+// lambda_max of D^-1 A_k by m Arnoldi steps (Sec. 3.2.2). The orthogonalization is classical
+// Gram-Schmidt applied twice (CGS2: one fused multi-dot, one fused multi-axpy per pass), which
+// gives the Hessenberg matrix of modified Gram-Schmidt up to rounding with 6 launches per step
+// instead of 3 (j+1).
 hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
   Level& l = P.L[k];
   const int m = (int)std::min<long long>(P.desc.arnoldi_iters, l.nI);
   if (m < 1) { l.lam = 1.0; return HMG_OK; }
   const long long n = l.m.N;
-  std::vector<double*> V(m + 1, nullptr);
-  double* Hd = nullptr;
+  double *Vb = nullptr, *Hd = nullptr, *part = nullptr, *coef = nullptr;
   std::vector<void*> tmp;
   auto cleanup = [&]() { for (void* p : tmp) dev_free(p, s); };
-  for (int j = 0; j <= m; ++j) {
-    if (dev_alloc((void**)&V[j], n * sizeof(double), s) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
-    tmp.push_back(V[j]);
+  auto get = [&](double** ptr, size_t count) -> bool {
+    if (dev_alloc((void**)ptr, count * sizeof(double), s) != cudaSuccess) return false;
+    tmp.push_back(*ptr);
+    return true;
+  };
+  if (!get(&Vb, (size_t)(m + 1) * n) || !get(&Hd, (size_t)(m + 1) * m) ||
+      !get(&part, (size_t)(m + 1) * red_blocks(n)) || !get(&coef, (size_t)(m + 1))) {
+    cleanup();
+    set_error("arnoldi alloc");
+    return HMG_ENOMEM;
   }
-  if (dev_alloc((void**)&Hd, (m + 1) * m * sizeof(double), s) != cudaSuccess) { cleanup(); set_error("arnoldi alloc"); return HMG_ENOMEM; }
-  tmp.push_back(Hd);
+  auto V = [&](int j) { return Vb + (long long)j * n; };
   hmg_status st = [&]() -> hmg_status {
     TRY(cudaMemsetAsync(Hd, 0, (m + 1) * m * sizeof(double), s));
     const unsigned long long seed = (P.desc.arnoldi_seed ? P.desc.arnoldi_seed : 0x1402593800000000ull) + (unsigned long long)k;
-    TRY(start_vector(V[0], l.m, seed, s));
-    TRY(dot_partial(V[0], V[0], n, P.partial, s));
+    TRY(start_vector(V(0), l.m, seed, s));
+    TRY(dot_partial(V(0), V(0), n, P.partial, s));
     TRY(finish(P.partial, n, P.S, FIN_SQRT, S_TMP, 0, nullptr, s));
-    TRY(div_dev(V[0], V[0], n, P.S + S_TMP, s));
+    TRY(div_dev(V(0), V(0), n, P.S + S_TMP, s));
     for (int j = 0; j < m; ++j) {
-      double* w = V[j + 1];
+      double* w = V(j + 1);
       TRY(cudaMemsetAsync(w, 0, n * sizeof(double), s));
-      TRY(launch_apply_f64(l.m, l.basis, V[j], w, l.G, 1.0, P.err, s, l.v64));
+      TRY(launch_apply_f64(l.m, l.basis, V(j), w, l.G, 1.0, P.err, s, l.v64));
       TRY(scale_by(w, l.dinv, n, s));
-      for (int i = 0; i <= j; ++i) {
-        TRY(dot_partial(w, V[i], n, P.partial, s));
-        TRY(finish(P.partial, n, Hd, FIN_STORE, i * m + j, 0, nullptr, s));
-        TRY(axpy_dev(w, V[i], n, Hd + i * m + j, -1.0, s));
-      }
+      for (int pass = 0; pass < 2; ++pass)  // H[0..j][j] accumulates both passes
+        TRY(project_out(w, Vb, n, j + 1, n, part, coef, Hd + j, m, s));
       TRY(dot_partial(w, w, n, P.partial, s));
       TRY(finish(P.partial, n, Hd, FIN_SQRT, (j + 1) * m + j, 0, nullptr, s));
       if (j + 1 < m) TRY(div_dev(w, w, n, Hd + (j + 1) * m + j, s));
@@ -570,6 +576,8 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
 // For each level, time the kernel variants (block shapes, and for FP64 TMA staging) with CUDA events on the
 // level's own buffers and keep the fastest; results are cached per (device, dim, order, element
 // count, precision) for the process. HMG_AUTOTUNE=0 in the environment keeps variant 0.
+constexpr long long kTuneMinPoints = 32768;  // Gauss points below which a level is not tuned
+
 bool autotune_on() {
   static const bool on = [] {
     const char* v = getenv("HMG_AUTOTUNE");
@@ -614,6 +622,8 @@ void tune_cache_store(const TuneKey& k, int v) {
 
 hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   if (!autotune_on()) return HMG_OK;
+  // tiny levels run at the launch-latency floor whatever the block shape: keep variant 0
+  if (l.m.nelem * np_of(l.m) < kTuneMinPoints) return HMG_OK;
   static std::mutex mu;
   std::map<TuneKey, int>& cache = [&]() -> std::map<TuneKey, int>& {
     std::lock_guard<std::mutex> lk(mu);
@@ -1139,7 +1149,8 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     }
     max_stage = std::max(max_stage, gsz * D.dim * (D.dim + 1) * 8);
     if (D.smoother == HMG_SMOOTH_CHEB && k + 1 < ms.size())
-      arnoldi = std::max(arnoldi, (size_t)(std::min<long long>(D.arnoldi_iters, interior_count(m)) + 1) * n * 8);
+      arnoldi = std::max(arnoldi, (size_t)(std::min<long long>(D.arnoldi_iters, interior_count(m)) + 1) *
+                                      (n + kRedBlocks + 1 + (size_t)D.arnoldi_iters) * 8);
     if (k + 1 < ms.size()) {
       const Mesh& c = ms[k + 1];
       long long od[3] = {c.Nn[0], c.Nn[1], c.Nn[2]};

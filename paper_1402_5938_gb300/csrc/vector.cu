@@ -81,6 +81,43 @@ __global__ void __launch_bounds__(kThreads) k_finish(const double* __restrict__ 
   }
 }
 
+// Block-Gram-Schmidt helpers (Arnoldi): partial[i * gridDim.x + b] = sum over block b's range
+// of V_i . w for the cnt vectors V_i = V + i * ldv (blockIdx.y = i).
+__global__ void __launch_bounds__(kThreads) k_multi_dot(const double* __restrict__ V, long long ldv,
+                                                        const double* __restrict__ w, long long n,
+                                                        double* __restrict__ partial) {
+  const double* v = V + blockIdx.y * ldv;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)kThreads + threadIdx.x; t < n; t += (long long)gridDim.x * kThreads)
+    acc = fma(v[t], w[t], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// c[i] = sum_b partial[i * np + b] (fixed order); H[i * ldh] += c[i]  (blockIdx.x = i)
+__global__ void __launch_bounds__(kThreads) k_multi_finish(const double* __restrict__ partial, int np,
+                                                           double* __restrict__ c, double* __restrict__ H,
+                                                           int ldh) {
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < np; b += kThreads) acc += partial[blockIdx.x * np + b];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) {
+    c[blockIdx.x] = acc;
+    H[blockIdx.x * ldh] += acc;
+  }
+}
+
+// w -= sum_{i < cnt} c[i] V_i
+__global__ void __launch_bounds__(kThreads) k_multi_axpy(double* __restrict__ w, const double* __restrict__ V,
+                                                         long long ldv, int cnt, const double* __restrict__ c,
+                                                         long long n) {
+  for (long long t = blockIdx.x * (long long)kThreads + threadIdx.x; t < n; t += (long long)gridDim.x * kThreads) {
+    double acc = w[t];
+    for (int i = 0; i < cnt; ++i) acc = fma(-c[i], V[i * ldv + t], acc);
+    w[t] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_pcg_update(double* __restrict__ u, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ h,
                                                          long long n, const double* __restrict__ S,
@@ -453,6 +490,18 @@ cudaError_t start_vector(double* v, const Mesh& m, unsigned long long seed, cuda
   k_start<<<grid_for(m.N), kThreads, 0, s>>>(v, m, seed);
   return counted(cudaGetLastError());
 }
+cudaError_t project_out(double* w, const double* V, long long ldv, int cnt, long long n, double* partial,
+                        double* c, double* H, int ldh, cudaStream_t s) {
+  const int nb = red_blocks(n);
+  k_multi_dot<<<dim3(nb, cnt), kThreads, 0, s>>>(V, ldv, w, n, partial);
+  cudaError_t e = counted(cudaGetLastError());
+  if (e != cudaSuccess) return e;
+  k_multi_finish<<<cnt, kThreads, 0, s>>>(partial, nb, c, H, ldh);
+  if ((e = counted(cudaGetLastError())) != cudaSuccess) return e;
+  k_multi_axpy<<<grid_for(n), kThreads, 0, s>>>(w, V, ldv, cnt, c, n);
+  return counted(cudaGetLastError());
+}
+
 cudaError_t scale_by(double* w, const double* dinv, long long n, cudaStream_t s) {
   k_scale_by<<<grid_for(n), kThreads, 0, s>>>(w, dinv, n);
   return counted(cudaGetLastError());

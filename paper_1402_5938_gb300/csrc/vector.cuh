@@ -73,6 +73,10 @@ cudaError_t to_f64(double* dst, const float* src, long long n, cudaStream_t s);
 // Arnoldi helpers
 cudaError_t start_vector(double* v, const Mesh& m, unsigned long long seed, cudaStream_t s);
 cudaError_t scale_by(double* w, const double* dinv, long long n, cudaStream_t s);
+// One classical Gram-Schmidt pass against the cnt vectors V_i = V + i * ldv: c = V^T w,
+// H[i * ldh] += c[i], w -= V c (partial: cnt * red_blocks(n) doubles; c: cnt doubles).
+cudaError_t project_out(double* w, const double* V, long long ldv, int cnt, long long n, double* partial,
+                        double* c, double* H, int ldh, cudaStream_t s);
 cudaError_t axpy_dev(double* y, const double* x, long long n, const double* coef, double sign, cudaStream_t s);
 cudaError_t div_dev(double* y, const double* x, long long n, const double* den, cudaStream_t s);
 cudaError_t copy_scalar(double* dst, const double* src, cudaStream_t s);
