@@ -17,7 +17,7 @@ import sys, torch
 sys.path.insert(0, {root!r})
 import synth
 from paper_1402_5938_gb300 import Problem
-P = Problem(dict(synth.warped_var3d(4, 2, hier="p"), smooth_prec="fp16"))
+P = Problem(dict(synth.warped_var3d(16, 2, hier="p"), smooth_prec="fp16"))
 N = P.ndof(0)
 b = torch.zeros(N, dtype=torch.float64, device="cuda")
 P.rhs(torch.from_numpy(synth.nodal_field(5, N)).cuda(), b)
