@@ -4,9 +4,10 @@ launch configuration the solver uses. The oracle cannot assemble these operators
 
 * the FP64 apply is compared on sampled rows that the oracle evaluates one by one from
   the weak form (tolerance 1e-12 relative, as for the small cases);
-* the p-multigrid PCG solves (FP64 and FP32 V-cycle) are checked by properties that hold
-  at any size: FP64 residual <= 1e-8 recomputed with the FP64 operator, the mixed solve
-  within +1 iteration of the FP64 one, and the two solutions agreeing."""
+* the p-multigrid PCG solves (FP64, and FP32 / FP16 / BF16 V-cycles) are checked by
+  properties that hold at any size: FP64 residual <= 1e-8 recomputed with the FP64 operator,
+  the mixed solves within +1 iteration (FP32, FP16) or +3 (BF16) of the FP64 one, and the
+  solutions agreeing."""
 import numpy as np
 import pytest
 
@@ -56,6 +57,7 @@ def test_fullsize_apply_sampled_rows(hmg, E, p):
 
 @pytest.mark.parametrize("E,p", SWEEP, ids=lambda v: str(v))
 def test_fullsize_pmg_pcg_fp64_and_mixed(hmg, E, p):
+    """FP64 and every mixed-precision form reach the FP64 tolerance at the sweep's full size."""
     prob = synth.warped_var3d(E, p, hier="p")
     P64 = hmg.Problem(prob)
     P32 = hmg.Problem(dict(prob, smooth_prec="fp32"))
@@ -72,5 +74,16 @@ def test_fullsize_pmg_pcg_fp64_and_mixed(hmg, E, p):
         P64.apply(0, u, r)
         assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) <= 1.05e-8
     assert float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64)) <= 1e-5
-    P64.close()
     P32.close()
+    # the 16-bit tensor-core V-cycles (orders <= 7; FP32 above) with flexible PCG: FP16 keeps the
+    # FP64 count (+1), BF16's 8-bit mantissa may cost up to 3 more iterations
+    for prec, extra in (("fp16", 1), ("bf16", 3)):
+        Pl = hmg.Problem(dict(prob, smooth_prec=prec))
+        ul = torch.zeros_like(b)
+        stl, itl, _ = Pl.solve("pcg", b, ul, rtol=1e-8, maxit=500)
+        assert stl == 0 and itl <= it64 + extra, (prec, itl, it64)
+        P64.apply(0, ul, r)
+        assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) <= 1.05e-8
+        assert float(torch.linalg.norm(ul - u64) / torch.linalg.norm(u64)) <= 1e-5
+        Pl.close()
+    P64.close()
