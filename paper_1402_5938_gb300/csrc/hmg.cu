@@ -1511,7 +1511,10 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
   std::vector<double> r0(n, 0.0);
   auto hist_set = [&](int i, int k, double v) { if (res_hist && res_hist[i]) res_hist[i][k] = v; };
   // launch `k`-graphs of the problems in `which` over the pool, then join on s and synchronize
+  double t_enqueue = 0.0, t_wait = 0.0;  // host seconds (HMG_TRACE=1 prints them)
+  int nsteps = 0;
   auto step = [&](const std::vector<int>& which, int k0, int k1) -> hmg_status {
+    const auto c0 = std::chrono::steady_clock::now();
     TRY(cudaEventRecord(ev[used], s));
     for (int q = 0; q < used; ++q) TRY(cudaStreamWaitEvent(pool[dev][q], ev[used], 0));
     for (size_t w = 0; w < which.size(); ++w) {
@@ -1531,7 +1534,12 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
       TRY(cudaEventRecord(ev[q], pool[dev][q]));
       TRY(cudaStreamWaitEvent(s, ev[q], 0));
     }
+    const auto c1 = std::chrono::steady_clock::now();
     TRY(cudaStreamSynchronize(s));
+    const auto c2 = std::chrono::steady_clock::now();
+    t_enqueue += std::chrono::duration<double>(c1 - c0).count();
+    t_wait += std::chrono::duration<double>(c2 - c1).count();
+    ++nsteps;
     return HMG_OK;
   };
   hmg_status err = [&]() -> hmg_status {
@@ -1582,6 +1590,9 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
     return HMG_OK;
   }();
   for (auto& e : ev) cudaEventDestroy(e);
+  if (Phase::timing())
+    fprintf(stderr, "hmg batched: %d problems, %d steps, host enqueue %.3f s, wait for the device %.3f s\n", n,
+            nsteps, t_enqueue, t_wait);
   if (err != HMG_OK) return err;
   hmg_status first = HMG_OK;
   for (int i = 0; i < n; ++i) {
