@@ -80,13 +80,16 @@ struct Lowp<__nv_bfloat16> {
 // up to NPAD values (NPAD = 2, 4 or 8, the smallest power of two >= N): line L sits in row
 // L % H, slot L / H (H = 16 MT rows), value b at column slot * NPAD + b. The 1D tables enter the
 // MMA block-diagonally (one NPAD x NPAD block per slot), so one m16n8k8 contracts 16 LPR lines.
-template <int DIM, int N>
+template <int DIM, int N, int HALF = 0>
 struct Apply16Cfg {
   static constexpr int NP = Sh<DIM, N>::NP, NL = Sh<DIM, N>::NL, NC = Sh<DIM, N>::NC;
   static constexpr int NPAD = N <= 2 ? 2 : (N <= 4 ? 4 : 8);
   static constexpr int LPR = 8 / NPAD;  // lines per MMA row
+  // elements per warp group: >= 64 lines (HALF: about half of that, for meshes too small to give
+  // every warp a group)
   static constexpr int EW0 = LPR == 1 ? (64 + NL - 1) / NL : (32 * LPR) / NL;
-  static constexpr int EW = EW0 < 1 ? 1 : (EW0 > 32 ? 32 : EW0);  // elements per warp group
+  static constexpr int EW1 = HALF ? (EW0 + 1) / 2 : EW0;
+  static constexpr int EW = EW1 < 1 ? 1 : (EW1 > 32 ? 32 : EW1);
   static constexpr int NLG = EW * NL;                               // lines of a group along any direction
   static constexpr int MT = ((NLG + LPR - 1) / LPR + 15) / 16;      // 16-row MMA tiles
   static constexpr int H = MT * 16;
@@ -146,12 +149,12 @@ __device__ __forceinline__ void stC(uint16_t* buf, const float (&c)[4], short4 o
 
 }  // namespace lp
 
-template <int DIM, int N, typename T>
+template <int DIM, int N, typename T, int HALF>
 __global__ void __launch_bounds__(256)
 k_apply16(const float* __restrict__ x, float* __restrict__ y, const T* __restrict__ G16,
           const float* __restrict__ gsc, const Mesh m, const __grid_constant__ Tab16 tab, const float alpha,
           const long long ngroups, int* __restrict__ err) {
-  using C = Apply16Cfg<DIM, N>;
+  using C = Apply16Cfg<DIM, N, HALF>;
   using L = Lowp<T>;
   constexpr int NP = C::NP, NL = C::NL, NC = C::NC, EW = C::EW, NLG = C::NLG, MT = C::MT, BUF = C::BUF;
   constexpr int H = C::H, NPAD = C::NPAD;

@@ -622,8 +622,9 @@ void tune_cache_store(const TuneKey& k, int v) {
 
 hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   if (!autotune_on()) return HMG_OK;
-  // tiny levels run at the launch-latency floor whatever the block shape: keep variant 0
-  if (l.m.nelem * np_of(l.m) < kTuneMinPoints) return HMG_OK;
+  // tiny levels run at the launch-latency floor whatever the block shape: variant 0 unless the
+  // decision cache names one
+  const bool tiny = l.m.nelem * np_of(l.m) < kTuneMinPoints;
   static std::mutex mu;
   std::map<TuneKey, int>& cache = [&]() -> std::map<TuneKey, int>& {
     std::lock_guard<std::mutex> lk(mu);
@@ -643,6 +644,7 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
         continue;
       }
     }
+    if (tiny) continue;
     cudaEvent_t e0, e1;
     TRY(cudaEventCreate(&e0));
     TRY(cudaEventCreate(&e1));

@@ -20,8 +20,9 @@ cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, fl
 
 // y += alpha * A x with 16-bit geometric factors and tensor-core contractions (FP32 vectors),
 // for orders p <= 7; prec is HMG_PREC_FP16 (gsc: per-element factor scales) or HMG_PREC_BF16
-// (gsc unused). G16 needs >= 16 bytes of tail padding. variant 0..2 selects the warps per block.
-constexpr int kApply16Variants = 3;
+// (gsc unused). G16 needs >= 16 bytes of tail padding. variant 0..2 selects the warps per block,
+// 3 half-size element groups (more warps on small meshes).
+constexpr int kApply16Variants = 4;
 constexpr int kMaxOrder16 = 7;
 cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
                               const float* gsc, float alpha, int prec, int* err, cudaStream_t s, int variant = 0);

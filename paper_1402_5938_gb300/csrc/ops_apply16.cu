@@ -50,6 +50,24 @@ Tab16 make_tab16(const Basis1D& b) {
   return t;
 }
 
+template <int DIM, int N, typename T, int HALF>
+cudaError_t apply16_launch(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
+                           const float* gsc, float alpha, int* err, int wpb, cudaStream_t s) {
+  using C = Apply16Cfg<DIM, N, HALF>;
+  const size_t smem = C::smem(wpb);
+  auto kern = k_apply16<DIM, N, T, HALF>;
+  cudaError_t e = ensure_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const long long ngroups = (m.nelem + C::EW - 1) / C::EW;
+  if (ngroups == 0) return cudaSuccess;
+  const long long blocks = (ngroups + wpb - 1) / wpb;
+  const long long grid =
+      std::min<long long>(blocks, (long long)sm_count16() * resident16((const void*)kern, 32 * wpb, smem));
+  kern<<<(unsigned)grid, 32 * wpb, smem, s>>>(x, y, static_cast<const T*>(G16), gsc, m, make_tab16(b), alpha,
+                                              ngroups, err);
+  return counted(cudaGetLastError());
+}
+
 template <int DIM, typename T>
 cudaError_t apply16_dim(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
                         const float* gsc, float alpha, int* err, int variant, cudaStream_t s) {
@@ -59,21 +77,10 @@ cudaError_t apply16_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
     if constexpr (N > kMaxN16) {
       return cudaErrorInvalidValue;
     } else {
-      using C = Apply16Cfg<DIM, N>;
-      // variant 0: 4 warps per block, 1: 2 warps, 2: 8 warps
+      // variant 0: 4 warps per block, 1: 2 warps, 2: 8 warps, 3: 4 warps with half-size groups
+      if (variant == 3) return apply16_launch<DIM, N, T, 1>(m, b, x, y, G16, gsc, alpha, err, 4, s);
       const int wpb = variant == 1 ? 2 : (variant == 2 ? 8 : 4);
-      const size_t smem = C::smem(wpb);
-      auto kern = k_apply16<DIM, N, T>;
-      cudaError_t e = ensure_smem(kern, smem);
-      if (e != cudaSuccess) return e;
-      const long long ngroups = (m.nelem + C::EW - 1) / C::EW;
-      if (ngroups == 0) return cudaSuccess;
-      const long long blocks = (ngroups + wpb - 1) / wpb;
-      const long long grid =
-          std::min<long long>(blocks, (long long)sm_count16() * resident16((const void*)kern, 32 * wpb, smem));
-      kern<<<(unsigned)grid, 32 * wpb, smem, s>>>(x, y, static_cast<const T*>(G16), gsc, m, make_tab16(b), alpha,
-                                                  ngroups, err);
-      return counted(cudaGetLastError());
+      return apply16_launch<DIM, N, T, 0>(m, b, x, y, G16, gsc, alpha, err, wpb, s);
     }
   });
 }

@@ -168,3 +168,27 @@ def test_lowp_graph_and_batched_equal_host_loop(hmg, prec):
     assert float(torch.linalg.norm(ug - uh) / torch.linalg.norm(uh)) < 1e-6
     Pg.close()
     Ph.close()
+
+
+def test_lowp_half_group_variant_within_rounding_bound(tmp_path):
+    """The half-size element-group shape (variant 3, picked by the autotuner on small meshes)
+    passes the same rounding-bound parity: pinned for every case through the decision cache,
+    in a fresh process."""
+    import os
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cache = tmp_path / "tune16.txt"
+    lines = []
+    for case in CASES:
+        ne = int(np.prod(case["nelem"]))
+        for kind in (2, 3):                      # HMG_PREC_FP16, HMG_PREC_BF16
+            lines.append(f"0 {case['dim']} {case['order']} {ne} {kind} 3")
+    cache.write_text("\n".join(lines) + "\n")
+    env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(root, "tests", "test_gpu_lowp.py"), "-k", "apply_within_rounding_bound"],
+                         env=env, cwd=root, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stdout[-3000:]
