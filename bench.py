@@ -106,7 +106,8 @@ def cpu_baseline(hier):
 
 def solve_roofline_ms(P, iters, hbm_gbs, fp64_tflops, nu=(3, 3)):
     """Roofline time of one PCG + V-cycle solve (Sec. 4.2 cost model made explicit): every FP64
-    apply at max(flops / FP64 peak, bytes / HBM), plus the smoother updates (8 vectors per
+    apply at max(flops / FP64 peak, bytes / HBM) -- for orders 1-2 the smaller of the sum-
+    factorized and the dense-element-matrix roofs -- plus the smoother updates (8 vectors per
     step), residual copies, transfers and PCG vector work at HBM speed, and the dense
     coarsest GEMV. PCG with `iters` iterations runs `iters` V-cycles and `iters` extra
     finest-level applies."""
@@ -122,6 +123,9 @@ def solve_roofline_ms(P, iters, hbm_gbs, fp64_tflops, nu=(3, 3)):
         nc = 6 if dim == 3 else 3
         byts = E * n ** dim * nc * 8 + 16 * N
         t_apply = max(flops / (fp64_tflops * 1e12), byts / (hbm_gbs * 1e9))
+        if n <= 3:  # low orders may run from stored element matrices: the cheaper roof of the two
+            d_flops, d_byts = E * 2 * n ** (2 * dim), E * 8 * n ** (2 * dim) + 16 * N
+            t_apply = min(t_apply, max(d_flops / (fp64_tflops * 1e12), d_byts / (hbm_gbs * 1e9)))
         if k == L - 1:                                   # dense coarsest: one GEMV per V-cycle
             nI = 1
             for a in range(dim):
@@ -389,6 +393,8 @@ def run_sweep(args):
             ts.append(a.elapsed_time(b_))
         return statistics.median(ts), out
 
+    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     for E, p in [(64, 2), (32, 4), (16, 8), (8, 16)]:
         prob = synth.warped_var3d(E, p, hier="p")
         P64 = Problem(prob)
@@ -402,9 +408,20 @@ def run_sweep(args):
         s64, (_, it64, h64) = timed(lambda: P64.solve("pcg", b, u64, rtol=1e-8, maxit=500), 3)
         n = p + 1
         flops = E ** 3 * (24 * n ** 4 + 15 * n ** 3)
-        line = {"sweep": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_tflops": flops / t64 / 1e9,
-                "apply_fp64_frac_of_fp64_peak": flops / t64 / 1e9 / FP64_PEAK_TFLOPS,
+        v64, _ = P64.level_variants(0)
+        line = {"sweep": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_variant": v64,
+                "apply_fp64_tflops_algorithmic": flops / t64 / 1e9,
                 "pcg_fp64_ms": s64, "pcg_fp64_iters": it64, "setup_bytes_fp64": P64.device_bytes()}
+        if v64 == 4:
+            # stored dense element matrices: 2 n^6 flops and 8 n^6 bytes per element executed
+            # (fewer flops than the sum-factorized count above), so the roofline is its own
+            ex_flops, ex_bytes = E ** 3 * 2 * n ** 6, E ** 3 * 8 * n ** 6 + 16 * N
+            line.update({"apply_fp64_kernel": "dense element matrices",
+                         "apply_fp64_frac_of_fp64_peak": ex_flops / t64 / 1e9 / FP64_PEAK_TFLOPS,
+                         "apply_fp64_frac_of_hbm": ex_bytes / t64 / 1e6 / hbm_peak})
+        else:
+            line.update({"apply_fp64_kernel": "sum factorization",
+                         "apply_fp64_frac_of_fp64_peak": flops / t64 / 1e9 / FP64_PEAK_TFLOPS})
         # V-cycle precisions: FP32, and FP16 / BF16 tensor-core applies (orders <= 7) with flexible PCG
         for prec, gbytes in (("fp32", 4), ("fp16", 2), ("bf16", 2)):
             Pm = Problem(dict(prob, smooth_prec=prec))

@@ -140,8 +140,14 @@ int hmg_nlevels(const hmg_problem* prob);
 size_t hmg_ndof(const hmg_problem* prob, int level);
 hmg_status hmg_level_info(const hmg_problem* prob, int level, int* nelem3, int* order, size_t* ndof);
 size_t hmg_device_bytes(const hmg_problem* prob);
+/* Apply block shapes the setup's autotuner chose on a level (no counterpart in the paper):
+ * FP64 operator (0-2 block shapes, 3 with TMA-staged factors, 4 stored dense element matrices
+ * for orders 1-2) and the mixed V-cycle's operator (FP32: 0-2 tile sizes; FP16/BF16: 0-2 warps
+ * per block, 3 half-size element groups). */
+hmg_status hmg_level_variants(const hmg_problem* prob, int level, int* v_fp64, int* v_vcycle);
 
-/* Physical node coordinates of a level, written as xyz_dev[c * N + node], c < dim. */
+/* Physical node coordinates of a level, written as xyz_dev[c * N + node], c < dim (the warp map,
+ * or with node_xyz the given finest coordinates and the finest isoparametric map on coarser levels). */
 hmg_status hmg_node_coords(hmg_problem* prob, int level, double* xyz_dev, void* stream);
 
 /* Load vector b_j = (f_h, phi_j) for the nodal interpolant f_h of f (all N nodal values used),

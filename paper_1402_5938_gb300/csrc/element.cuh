@@ -480,6 +480,50 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
 }
 
 // ---------------------------------------------------------------------------------------
+// FP64 apply with stored element matrices, y += alpha * A x: for low orders (N <= 3) the dense
+// element matvec, 2 N^{2d} flops, is cheaper than the 24 N^4 + 15 N^3 of sum factorization (at
+// N = 3: 1,458 against 2,349) for 8 N^{2d} bytes per element. A block holds EPB elements, one
+// thread per element row: the element's x in shared memory (boundary nodes as 0), then
+// y_a = sum_b K[b][a] x_b with K column-major so that a warp reads consecutive rows of one
+// column, then a scatter-add to interior nodes.
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__global__ void __launch_bounds__(256)
+k_apply_dense64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ Ke,
+                const Mesh m, const double alpha) {
+  constexpr int NP = Sh<DIM, N>::NP;
+  constexpr int EPB = 256 / NP;
+  __shared__ double xs[EPB * NP];
+  __shared__ long long ebase[EPB];
+  __shared__ int eflag[EPB];
+  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
+  const long long ngroups = (m.nelem + EPB - 1) / EPB;
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const long long e0 = grp * EPB;
+    const int ne = (int)min((long long)EPB, m.nelem - e0);
+    if (threadIdx.x < ne) elem_base(m, e0 + threadIdx.x, &ebase[threadIdx.x], &eflag[threadIdx.x]);
+    __syncthreads();
+    const int e = threadIdx.x / NP, a = threadIdx.x - e * NP;
+    bool bd = true;
+    long long gn = 0;
+    if (e < ne) {
+      gn = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
+      xs[threadIdx.x] = bd ? 0.0 : x[gn];
+    }
+    __syncthreads();
+    if (e < ne && !bd) {
+      const double* k = Ke + (e0 + e) * NP * NP + a;
+      const double* xe = xs + e * NP;
+      double acc = 0.0;
+#pragma unroll
+      for (int b = 0; b < NP; ++b) acc = fma(k[b * NP], xe[b], acc);
+      atomicAdd(y + gn, alpha * acc);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Geometry, stage 1: node coordinates of every element node -- x = X + amp prod sin(pi X), or
 // the given coords[c][global node] -- interpolated to the Gauss points (x_q) and
 // differentiated (dx_c/dxi_d), written to J[e][c*(DIM+1) + s][NP] with s = 0 for x_q and
@@ -746,12 +790,14 @@ k_mass(const double* __restrict__ f, double* __restrict__ b, const double* __res
 // Dense interior operator of a (small, coarsest) level: every tile of a block is one
 // (element e, local column b) pair; the element operator is applied to the unit vector
 // e_b by the same sum-factorized phases as k_apply (column b of K_e), and K_e[a][b] is
-// added into A[ia*nI + ib] for interior a and b (interior numbering, x fastest).
+// added into A[ia*nI + ib] for interior a and b (interior numbering, x fastest); or, with
+// Ke != nullptr, stored as the element matrix Ke[(e * NP + b) * NP + a] (column-major).
 // ---------------------------------------------------------------------------------------
 template <int DIM, int N>
 __global__ void __launch_bounds__(256)
 k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
-             const __grid_constant__ Tab<N, double> tab, const long long nI, const int epb) {
+             const __grid_constant__ Tab<N, double> tab, const long long nI, const int epb,
+             double* __restrict__ Ke) {
   constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* U = reinterpret_cast<double*>(smem_raw);
@@ -805,6 +851,10 @@ k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
     const int e = t / NP, a = t - e * NP;
     const long long el = (t0 + e) / NP;
     const int b = (int)((t0 + e) % NP);
+    if (Ke != nullptr) {
+      Ke[(el * NP + b) * NP + a] = U[t];
+      continue;
+    }
     bool bda, bdb;
     const long long ga = elem_node<DIM, N>(m, el, a, bda);
     const long long gb = elem_node<DIM, N>(m, el, b, bdb);

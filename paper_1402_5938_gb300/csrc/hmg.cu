@@ -91,6 +91,7 @@ struct Level {
   double* dinv = nullptr;
   float* G32 = nullptr;
   void* G16 = nullptr;    // 16-bit factors of the FP16/BF16 V-cycle operator (orders <= 7)
+  double* Ke = nullptr;   // element matrices of a low-order FP64 level (dense-apply variant)
   float* gsc = nullptr;   // FP16: per-element power-of-two factor scales
   float* dinv32 = nullptr;
   double lam = 0.0;       // Chebyshev bound
@@ -108,6 +109,7 @@ struct ProblemImpl {
   int device = 0;
   std::vector<Level> L;
   double* S = nullptr;        // device scalars
+  double* X0 = nullptr;       // user node coordinates of the finest level [dim][N0] (node_xyz), else null
   int* err = nullptr;         // device error flag written by bounded waits in kernels
   double* partial = nullptr;  // reduction partials
   double* hostS = nullptr;    // pinned host copy of a scalar
@@ -345,7 +347,7 @@ template <> struct Acc<float> {
 hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, P.err, s, l.v64));
+  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, P.err, s, l.v64, l.Ke));
   return HMG_OK;
 }
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
@@ -553,7 +555,7 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
     for (int j = 0; j < m; ++j) {
       double* w = V(j + 1);
       TRY(cudaMemsetAsync(w, 0, n * sizeof(double), s));
-      TRY(launch_apply_f64(l.m, l.basis, V(j), w, l.G, 1.0, P.err, s, l.v64));
+      TRY(launch_apply_f64(l.m, l.basis, V(j), w, l.G, 1.0, P.err, s, l.v64, l.Ke));
       TRY(scale_by(w, l.dinv, n, s));
       for (int pass = 0; pass < 2; ++pass)  // H[0..j][j] accumulates both passes
         TRY(project_out(w, Vb, n, j + 1, n, part, coef, Hd + j, m, s));
@@ -651,10 +653,10 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     float best = 1e30f;
     int bv = 0;
     cudaError_t err = cudaSuccess;
-    const int nvar = prec == 0 ? kApply64Variants : (l.G16 ? kApply16Variants : kApply32Variants);
+    const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : (l.G16 ? kApply16Variants : kApply32Variants);
     for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
       auto run = [&]() {
-        if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v);
+        if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v, l.Ke);
         if (l.G16)
           return launch_apply_lowp(l.m, l.basis, l.x32, l.r32, l.G16, l.gsc, 1.0f, P.desc.smooth_prec, P.err, s, v);
         return launch_apply_f32(l.m, l.basis, l.x32, l.r32, l.G32, 1.0f, P.err, s, v);
@@ -776,7 +778,8 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
   hmg_status st = [&]() -> hmg_status {
     const long long nq0 = P.L[0].m.nelem * np_of(P.L[0].m);
     if (D.node_xyz) {
-      CHECK(talloc((void**)&X0, (size_t)D.dim * N0 * sizeof(double)));
+      TRY(P.alloc((void**)&X0, (size_t)D.dim * N0 * sizeof(double)));  // kept: hmg_node_coords
+      P.X0 = X0;
       CHECK(talloc((void**)&Xk, (size_t)D.dim * N0 * sizeof(double)));
       TRY(cudaMemcpyAsync(X0, D.node_xyz, (size_t)D.dim * N0 * sizeof(double), cudaMemcpyHostToDevice, s));
     }
@@ -826,6 +829,13 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       if (hbad) { set_error("non-positive Jacobian determinant: the mapped mesh is folded"); return HMG_EINVAL; }
       // diagonal -> D^-1 (the diagonal is accumulated in l.r, then cleared)
       TRY(launch_diag(l.m, l.basis, l.G, l.r, s));
+      // low orders, FP64 applies of a V-cycle level (all levels in FP64; the finest otherwise):
+      // element matrices for the dense-apply variant, which the autotuner may pick
+      if (l.m.p + 1 <= kMaxNDense && k + 1 < P.L.size() && (k == 0 || D.smooth_prec == HMG_PREC_FP64)) {
+        const long long np = np_of(l.m);
+        TRY(P.alloc((void**)&l.Ke, (size_t)l.m.nelem * np * np * sizeof(double)));
+        TRY(launch_elem_mats(l.m, l.basis, l.G, l.Ke, s));
+      }
       TRY(dinv_from_diag(l.r, l.dinv, n, s));
       TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));
       if (mixed) {
@@ -1140,6 +1150,8 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     const size_t gsz = (size_t)(m.nelem * np_of(m)), n = (size_t)m.N;
     add(gsz * nc_of(D.dim) * 8 + 256); add(gsz * 8);
     for (int v = 0; v < 5; ++v) add(n * 8);
+    if (m.p + 1 <= kMaxNDense && k + 1 < ms.size() && (k == 0 || !mixed))
+      add((size_t)m.nelem * np_of(m) * np_of(m) * 8);  // element matrices (dense-apply variant)
     if (mixed) {
       if (lowp && m.p <= kMaxOrder16) {
         add(gsz * nc_of(D.dim) * 2 + 256);
@@ -1177,7 +1189,7 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   res += allocs * 512;                    // allocation granularity
   size_t custom = 0;  // setup temporaries of user geometry / coefficient
   const size_t nq0 = (size_t)(ms[0].nelem * np_of(ms[0]));
-  if (D.node_xyz) custom += 2 * (size_t)D.dim * N0 * 8;
+  if (D.node_xyz) { custom += (size_t)D.dim * N0 * 8; res += (size_t)D.dim * N0 * 8 + 512; }
   if (D.mu_fn) custom += (size_t)(D.dim + 1) * nq0 * 8;
   const size_t temp = std::max(max_stage + 16 + custom, std::max(arnoldi, (size_t)nI * 16));
   if (resident) *resident = res;
@@ -1279,10 +1291,26 @@ hmg_status hmg_level_info(const hmg_problem* p, int level, int* nelem3, int* ord
 
 size_t hmg_device_bytes(const hmg_problem* p) { return p ? p->impl.bytes : 0; }
 
+hmg_status hmg_level_variants(const hmg_problem* p, int level, int* v_fp64, int* v_vcycle) {
+  if (!level_ok(p, level)) return HMG_EINVAL;
+  const Level& l = p->impl.L[level];
+  if (v_fp64) *v_fp64 = (l.v64 == kApply64Dense && !l.Ke) ? 0 : l.v64;
+  if (v_vcycle) *v_vcycle = l.v32;
+  return HMG_OK;
+}
+
 hmg_status hmg_node_coords(hmg_problem* p, int level, double* xyz, void* stream) {
   if (!level_ok(p, level) || !xyz) { set_error("null argument"); return HMG_EINVAL; }
   const Level& l = p->impl.L[level];
-  TRY(node_coords(xyz, l.m, l.basis.r, p->impl.desc.warp_amp, (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->impl.X0) {  // user geometry: the finest coordinates, or the finest map at this level's nodes
+    if (level == 0)
+      TRY(cudaMemcpyAsync(xyz, p->impl.X0, (size_t)l.m.dim * l.m.N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else
+      TRY(launch_level_coords(p->impl.L[0].m, p->impl.L[0].basis, p->impl.X0, l.m, l.basis, xyz, s));
+    return HMG_OK;
+  }
+  TRY(node_coords(xyz, l.m, l.basis.r, p->impl.desc.warp_amp, s));
   return HMG_OK;
 }
 

@@ -13,8 +13,16 @@ namespace hmg {
 // picks it per level by timing (autotuning).
 constexpr int kApply64Variants = 4;
 constexpr int kApply32Variants = 3;
+// FP64 variant kApply64Dense: stored element matrices Ke (launch_elem_mats) instead of sum
+// factorization, for orders with N <= kMaxNDense; other variants ignore Ke.
+constexpr int kApply64Dense = 4;
+constexpr int kMaxNDense = 3;
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
-                             const double* G, double alpha, int* err, cudaStream_t s, int variant = 0);
+                             const double* G, double alpha, int* err, cudaStream_t s, int variant = 0,
+                             const double* Ke = nullptr);
+// Ke[(e * NP + b) * NP + a] = K_e[a][b], the element stiffness matrices (all nodes; the apply
+// masks the boundary), by sum-factorized unit columns.
+cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, double* Ke, cudaStream_t s);
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
                              const float* G, float alpha, int* err, cudaStream_t s, int variant = 0);
 

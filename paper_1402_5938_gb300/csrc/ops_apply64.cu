@@ -1,4 +1,6 @@
 // Instantiation and launch of the FP64 operator-apply kernel (all orders, three block shapes).
+#include <algorithm>
+
 #include "dispatch.cuh"
 #include "ops.cuh"
 
@@ -35,8 +37,30 @@ cudaError_t apply64_dim(const Mesh& m, const Basis1D& b, const double* x, double
 
 }  // namespace
 
+template <int DIM>
+cudaError_t apply_dense64_dim(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* Ke,
+                              double alpha, cudaStream_t s) {
+  if (b.n > kMaxNDense) return cudaErrorInvalidValue;
+  return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
+    constexpr int N = decltype(nc)::value;
+    if constexpr (N > kMaxNDense) {
+      return cudaErrorInvalidValue;
+    } else {
+      constexpr int EPB = 256 / Sh<DIM, N>::NP;
+      const long long groups = (m.nelem + EPB - 1) / EPB;
+      if (groups == 0) return cudaSuccess;
+      const unsigned grid = (unsigned)std::min<long long>(groups, 152LL * 8);
+      k_apply_dense64<DIM, N><<<grid, 256, 0, s>>>(x, y, Ke, m, alpha);
+      return counted(cudaGetLastError());
+    }
+  });
+}
+
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
-                             const double* G, double alpha, int* err, cudaStream_t s, int variant) {
+                             const double* G, double alpha, int* err, cudaStream_t s, int variant,
+                             const double* Ke) {
+  if (variant == kApply64Dense && Ke != nullptr)
+    return m.dim == 3 ? apply_dense64_dim<3>(m, b, x, y, Ke, alpha, s) : apply_dense64_dim<2>(m, b, x, y, Ke, alpha, s);
   return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, err, variant, s)
                     : apply64_dim<2>(m, b, x, y, G, alpha, err, variant, s);
 }

@@ -84,7 +84,7 @@ cudaError_t mass_dim(const Mesh& m, const Basis1D& b, const double* f, double* o
 
 template <int DIM>
 cudaError_t dense_dim(const Mesh& m, const Basis1D& b, const double* G, double* A, long long nI,
-                      cudaStream_t s) {
+                      double* Ke, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
     constexpr int NP = Sh<DIM, N>::NP;
@@ -94,7 +94,7 @@ cudaError_t dense_dim(const Mesh& m, const Basis1D& b, const double* G, double* 
     cudaError_t e = ensure_smem(k, per * epb);
     if (e != cudaSuccess) return e;
     const long long blocks = (m.nelem * NP + epb - 1) / epb;
-    k<<<(unsigned)blocks, 256, per * epb, s>>>(G, A, m, make_tab<N, double>(b), nI, epb);
+    k<<<(unsigned)blocks, 256, per * epb, s>>>(G, A, m, make_tab<N, double>(b), nI, epb, Ke);
     return counted(cudaGetLastError());
   });
 }
@@ -142,7 +142,11 @@ cudaError_t launch_mass(const Mesh& m, const Basis1D& b, const double* f, double
 
 cudaError_t launch_elem_dense(const Mesh& m, const Basis1D& b, const double* G, double* A,
                               long long nI, cudaStream_t s) {
-  return m.dim == 3 ? dense_dim<3>(m, b, G, A, nI, s) : dense_dim<2>(m, b, G, A, nI, s);
+  return m.dim == 3 ? dense_dim<3>(m, b, G, A, nI, nullptr, s) : dense_dim<2>(m, b, G, A, nI, nullptr, s);
+}
+
+cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, double* Ke, cudaStream_t s) {
+  return m.dim == 3 ? dense_dim<3>(m, b, G, nullptr, 0, Ke, s) : dense_dim<2>(m, b, G, nullptr, 0, Ke, s);
 }
 
 }  // namespace hmg

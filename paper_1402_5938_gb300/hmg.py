@@ -55,6 +55,7 @@ _SIGS = {
     "hmg_destroy": (_I, [_P]),
     "hmg_nlevels": (_I, [_P]),
     "hmg_ndof": (ctypes.c_size_t, [_P, _I]),
+    "hmg_level_variants": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "hmg_level_info": (_I, [_P, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_size_t)]),
     "hmg_device_bytes": (ctypes.c_size_t, [_P]),
@@ -208,6 +209,12 @@ class Problem:
 
     def device_bytes(self):
         return lib().hmg_device_bytes(self.h)
+
+    def level_variants(self, level):
+        """(FP64 apply variant, V-cycle operator variant) the autotuner chose on `level`."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(lib().hmg_level_variants(self.h, level, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def fine_applies(self):
         return lib().hmg_fine_applies(self.h)

@@ -59,6 +59,12 @@ def test_custom_geometry_and_coefficient_match_oracle(hmg, prob):
         want = H.levels[k].A @ x[d.interior]
         got = y.cpu().numpy()[d.interior]
         assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max(), k
+    for k in range(P.nlevels()):  # the coordinates the library reports are the ones it used
+        d = H.levels[k].disc
+        buf = torch.zeros(prob["dim"] * d.N, dtype=torch.float64, device=DEV)
+        P.node_coords(k, buf)
+        xyz = buf.cpu().numpy().reshape(prob["dim"], d.N)
+        assert np.abs(xyz - d.node_coords().T).max() < 1e-13, k
     d = H.fine.disc
     f = synth.nodal_field(41, d.N)
     b = torch.zeros(d.N, dtype=torch.float64, device=DEV)
