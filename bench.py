@@ -281,7 +281,7 @@ def run_gpu(args):
     # ---- the same problem with the mixed-precision V-cycles inside FP64 PCG (context; the
     # headline value above is plain FP64): median of 5 L2-flushed solves, true FP64 residual
     mixed = {}
-    for prec in ("fp32", "fp16", "bf16"):
+    for prec in (() if args.host_loop else ("fp32", "fp16", "bf16")):  # not in launch-list runs
         Pm = Problem(dict(prob, smooth_prec=prec))
         um = torch.zeros_like(b)
         for _ in range(2):
