@@ -7,6 +7,8 @@ TEST INFRASTRUCTURE ONLY. Follows the paper:
   every level is rediscretized (mu evaluated at that level's quadrature points).
 * Sec. 3.2.1 / 3.2.2: point-Jacobi with omega = 2/3; Chebyshev-accelerated Jacobi
   targeting [lambda_max/4, lambda_max] of D^-1 A, lambda_max from 10 Arnoldi iterations.
+* Sec. 4.4 (Table 7): the l1-Jacobi point smoother, x += omega D_l1^-1 (b - A x) with the
+  damping of all its experiments (omega = 2/3).
 * Sec. 3.2.2 / 4.3: V-cycle with nu_pre / nu_post smoothing steps and an exact solve
   on the coarsest grid; MG as solver until the residual norm drops by 1e8.
 * Algorithm 1: MG-preconditioned CG, one V-cycle per iteration.
@@ -22,6 +24,9 @@ Readings where the paper is silent or garbled (the CUDA library follows the same
   r0 = b - A u0, z0 = V(r0), p0 = z0, then alpha = (z,r)/(p,Ap), ..., beta = (z',r')/(z,r).
 * Stopping: ||r||_2 <= rtol * ||r_0||_2 over interior unknowns, u0 = 0.
 * Coarsest grid: dense Cholesky factorization (exact solve).
+* l1-Jacobi: the added diagonal is the rest of the row's l1 norm, D_l1 = diag(sum_j |a_ij|)
+  over the interior unknowns (the paper cites Baker, Falgout, Kolev and Yang 2011 without
+  fixing which couplings enter; on one process the full row is the one that changes the method).
 """
 from __future__ import annotations
 
@@ -68,10 +73,13 @@ def level_shapes(prob):
 
 
 class Level:
-    def __init__(self, disc: Discretization):
+    def __init__(self, disc: Discretization, l1=False):
         self.disc = disc
         self.A = disc.stiffness()
-        self.dinv = 1.0 / self.A.diagonal()
+        if l1:   # l1-Jacobi: D_l1 = diag(sum_j |a_ij|)
+            self.dinv = 1.0 / np.asarray(abs(self.A).sum(axis=1)).ravel()
+        else:
+            self.dinv = 1.0 / self.A.diagonal()
         self.P = None          # prolongation from the next coarser level to this one
         self.lam = None
         self.chol = None
@@ -93,7 +101,7 @@ class Hierarchy:
             disc = Discretization(prob["dim"], E, p, warp_amp=prob["warp_amp"],
                                   mu_a=prob["mu_a"], mu_b=prob["mu_b"], mu_k=prob["mu_k"],
                                   node_xyz=xyz, mu_fn=prob.get("mu_fn"))
-            self.levels.append(Level(disc))
+            self.levels.append(Level(disc, l1=prob["smoother"] == "l1jacobi"))
         for k in range(len(self.levels) - 1):
             self.levels[k].P = prolongation(self.levels[k].disc, self.levels[k + 1].disc)
         last = self.levels[-1]
@@ -143,7 +151,7 @@ class Hierarchy:
     def smooth(self, k, b, x, steps):
         if steps == 0:
             return np.zeros_like(b) if x is None else x
-        if self.prob["smoother"] == "jacobi":
+        if self.prob["smoother"] in ("jacobi", "l1jacobi"):
             return self.jacobi(k, b, x, steps)
         return self.chebyshev(k, b, x, steps)
 

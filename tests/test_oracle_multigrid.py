@@ -148,3 +148,37 @@ def test_iteration_counts_match_paper_tables_loosely(tab, key, p):
     _, it, hist, ok = solve(b)
     assert ok
     assert abs(it - t[key][str(p)]) <= 2, (it, t[key][str(p)])
+
+
+# ---- l1-Jacobi (Table 7) ------------------------------------------------------------------
+
+def test_l1_jacobi_diagonal_is_the_row_l1_norm():
+    """D_l1 = diag(sum_j |a_ij|) of the interior matrix, against a dense row sum."""
+    prob = synth.problem(2, 3, 3, warp_amp=0.1, mu_b=1e3, hier="h", n_hlevels=1, smoother="l1jacobi")
+    H = multigrid.Hierarchy(prob)
+    A = H.fine.A.toarray()
+    assert np.allclose(1.0 / H.fine.dinv, np.abs(A).sum(axis=1), rtol=1e-14, atol=0)
+    assert np.all(1.0 / H.fine.dinv >= np.diag(A))          # never below the Jacobi diagonal
+
+
+@pytest.mark.slow
+def test_l1_jacobi_counts_follow_table7():
+    """2d-const 32x32, p = 8, h-MG V(3,3), omega = 2/3 (Table 7): the l1-Jacobi counts over the
+    point-Jacobi counts are the paper's ratios (MG 51/17, PCG 16/9) within 15 %, and each count is
+    within 15 % (MG) / 2 (PCG) of the printed one (the paper's right-hand side is not given)."""
+    gold = GOLDEN["table7_l1_2d_const"]
+    counts = {}
+    for sm in ("jacobi", "l1jacobi"):
+        prob = synth.problem(2, 32, 8, hier="h", n_hlevels=3, smoother=sm, nu_pre=3, nu_post=3)
+        H = multigrid.Hierarchy(prob)
+        b = H.fine.disc.rhs(synth.nodal_field(7, H.fine.disc.N))
+        _, it_mg, _, ok1 = H.solve_mg(b)
+        _, it_pcg, _, ok2 = H.solve_pcg(b)
+        assert ok1 and ok2
+        counts[sm] = (it_mg, it_pcg)
+    mg_l1, pcg_l1 = counts["l1jacobi"]
+    mg_pt, pcg_pt = counts["jacobi"]
+    assert abs(mg_l1 / mg_pt - gold["l1"]["MG"]["8"] / gold["pt"]["MG"]["8"]) <= 0.15 * gold["l1"]["MG"]["8"] / gold["pt"]["MG"]["8"]
+    assert abs(pcg_l1 / pcg_pt - gold["l1"]["PCG"]["8"] / gold["pt"]["PCG"]["8"]) <= 0.15 * gold["l1"]["PCG"]["8"] / gold["pt"]["PCG"]["8"]
+    assert abs(mg_l1 - gold["l1"]["MG"]["8"]) <= 0.15 * gold["l1"]["MG"]["8"]
+    assert abs(pcg_l1 - gold["l1"]["PCG"]["8"]) <= 2
