@@ -43,7 +43,7 @@ typedef enum {
 } hmg_status;
 
 typedef enum { HMG_HIER_H = 0, HMG_HIER_P = 1 } hmg_hier;
-typedef enum { HMG_SMOOTH_JACOBI = 0, HMG_SMOOTH_CHEB = 1 } hmg_smoother;
+typedef enum { HMG_SMOOTH_JACOBI = 0, HMG_SMOOTH_CHEB = 1, HMG_SMOOTH_L1JACOBI = 2 } hmg_smoother;
 typedef enum { HMG_MODE_MG = 0, HMG_MODE_PCG = 1 } hmg_mode;
 typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC_BF16 = 3 } hmg_prec;
 
@@ -58,8 +58,11 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC
  *   hier, n_hlevels    : h-multigrid (Sec. 3.1.1): n_hlevels meshes at fixed p, each halving the
  *                        elements per axis. p-multigrid (Sec. 3.1.2): p, p/2, ..., 1 on the fine
  *                        mesh, then n_hlevels-1 mesh halvings at p = 1.
- *   smoother, nu_pre, nu_post, omega : point-Jacobi x += omega D^-1 (b - A x) or Chebyshev-
- *                        accelerated Jacobi of degree nu (Sec. 3.2.1); omega only for Jacobi.
+ *   smoother, nu_pre, nu_post, omega : point-Jacobi x += omega D^-1 (b - A x), Chebyshev-
+ *                        accelerated Jacobi of degree nu (Sec. 3.2.1), or l1-Jacobi (Sec. 4.4,
+ *                        Table 7): the Jacobi step with D_l1 = diag(sum_j |a_ij|) over the interior
+ *                        unknowns, computed at setup by probing A with (2p+1)^d color classes;
+ *                        omega for the Jacobi forms only.
  *   arnoldi_iters, cheb_lo_frac, cheb_safety : Chebyshev interval [lo_frac*s*lam, s*lam] with
  *                        lam the largest Ritz value of D^-1 A after arnoldi_iters Arnoldi steps
  *                        (Sec. 3.2.2: [lam/4, lam], 10 iterations).

@@ -264,7 +264,10 @@ hmg_status validate(const hmg_desc* d) {
   for (int a = 0; a < d->dim; ++a)
     if (d->nelem[a] < 1 || d->nelem[a] > (1 << 20)) { set_error("nelem out of range"); return HMG_EINVAL; }
   if (d->n_hlevels < 1 || d->n_hlevels > 30) { set_error("n_hlevels must be >= 1"); return HMG_EINVAL; }
-  if (d->smoother != HMG_SMOOTH_JACOBI && d->smoother != HMG_SMOOTH_CHEB) { set_error("bad smoother"); return HMG_EINVAL; }
+  if (d->smoother != HMG_SMOOTH_JACOBI && d->smoother != HMG_SMOOTH_CHEB && d->smoother != HMG_SMOOTH_L1JACOBI) {
+    set_error("bad smoother");
+    return HMG_EINVAL;
+  }
   if (d->nu_pre < 0 || d->nu_post < 0 || d->nu_pre > 64 || d->nu_post > 64) { set_error("bad nu"); return HMG_EINVAL; }
   if (!(fabs(d->warp_amp) * M_PI < 1.0)) { set_error("|warp_amp| * pi must be < 1"); return HMG_EINVAL; }
   if (!(d->mu_a > 0.0) || !(d->mu_a + (d->mu_b < 0 ? d->mu_b * d->dim : 0.0) > 0.0)) {
@@ -420,7 +423,7 @@ hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero,
     if (!r_is_b) TRY(cudaMemcpyAsync(r, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return apply_level(P, k, x, r, (T)-1, s);
   };
-  if (D.smoother == HMG_SMOOTH_JACOBI) {
+  if (D.smoother == HMG_SMOOTH_JACOBI || D.smoother == HMG_SMOOTH_L1JACOBI) {  // same step, other D
     const T w = (T)D.omega;
     for (int st = 0; st < steps; ++st) {
       const bool reset = st + 1 < steps || leave_r_b;
@@ -688,11 +691,15 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   return HMG_OK;
 }
 
+// Largest coarsest level for the dense exact inverse: the paper's order-16 h-hierarchy on a 32^2
+// mesh ends on 127^2 = 16,129 unknowns (a 2.1 GB matrix, ~4e12 flops of Gauss-Jordan at setup).
+constexpr long long kMaxCoarse = 20000;
+
 hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
   const long long nI = l.nI;
   if (nI == 0) return HMG_OK;
-  if (nI > 12000) {
-    set_error("coarsest level has " + std::to_string(nI) + " unknowns; the dense exact solve allows 12000: add levels");
+  if (nI > kMaxCoarse) {
+    set_error("coarsest level has " + std::to_string(nI) + " unknowns; the dense exact solve allows " + std::to_string(kMaxCoarse) + ": add levels");
     return HMG_EINVAL;
   }
   TRY(P.alloc((void**)&l.Ainv, (size_t)nI * nI * sizeof(double)));
@@ -835,6 +842,25 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         const long long np = np_of(l.m);
         TRY(P.alloc((void**)&l.Ke, (size_t)l.m.nelem * np * np * sizeof(double)));
         TRY(launch_elem_mats(l.m, l.basis, l.G, l.Ke, s));
+      }
+      if (D.smoother == HMG_SMOOTH_L1JACOBI && k + 1 < P.L.size()) {
+        // l1 row norms sum_j |a_ij|: along an axis a row couples at most 2p+1 consecutive nodes,
+        // so the nodes of one color class (indices mod 2p+1) meet each row at most once, and
+        // y = A (indicator of the class) holds one entry a_ij per row
+        TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));
+        const int period = 2 * l.m.p + 1;
+        int pc[3] = {1, 1, 1};
+        for (int a = 0; a < D.dim; ++a) pc[a] = (int)std::min<long long>(period, l.m.Nn[a]);
+        for (int c2 = 0; c2 < pc[2]; ++c2)
+          for (int c1 = 0; c1 < pc[1]; ++c1)
+            for (int c0 = 0; c0 < pc[0]; ++c0) {
+              TRY(color_indicator(l.x, l.m, period, c0, c1, c2, s));
+              TRY(cudaMemsetAsync(l.d, 0, n * sizeof(double), s));
+              TRY(launch_apply_f64(l.m, l.basis, l.x, l.d, l.G, 1.0, P.err, s, 0));
+              TRY(accum_abs(l.r, l.d, n, s));
+            }
+        TRY(cudaMemsetAsync(l.x, 0, n * sizeof(double), s));
+        TRY(cudaMemsetAsync(l.d, 0, n * sizeof(double), s));
       }
       TRY(dinv_from_diag(l.r, l.dinv, n, s));
       TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));

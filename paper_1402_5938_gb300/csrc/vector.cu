@@ -189,6 +189,25 @@ __global__ void k_dinv(const double* __restrict__ diag, double* __restrict__ din
     dinv[i] = diag[i] != 0.0 ? 1.0 / diag[i] : 0.0;
 }
 
+// Probe of one color class for the l1 row norms: v[g] = 1 where g is an interior node whose axis
+// indices are congruent to (c0, c1, c2) modulo `period`, else 0.
+__global__ void k_color_indicator(double* __restrict__ v, const Mesh m, int period, int c0, int c1, int c2) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < m.N; g += (long long)gridDim.x * blockDim.x) {
+    const long long I = g % m.Nn[0];
+    const long long r = g / m.Nn[0];
+    const long long J = r % m.Nn[1];
+    const long long K = m.dim == 3 ? r / m.Nn[1] : 0;
+    bool in = I > 0 && I < m.Nn[0] - 1 && J > 0 && J < m.Nn[1] - 1;
+    if (m.dim == 3) in = in && K > 0 && K < m.Nn[2] - 1;
+    v[g] = (in && I % period == c0 && J % period == c1 && K % period == c2) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_accum_abs(double* __restrict__ acc, const double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    acc[i] += fabs(y[i]);
+}
+
 __device__ __forceinline__ bool on_boundary(long long g, const Mesh& m) {
   const long long I = g % m.Nn[0];
   const long long r = g / m.Nn[0];
@@ -465,6 +484,16 @@ template cudaError_t cheb_step<double>(double*, double*, double*, const double*,
                                        double, int, cudaStream_t);
 template cudaError_t cheb_step<float>(float*, float*, float*, const float*, const float*, long long, float, float,
                                       int, cudaStream_t);
+
+cudaError_t color_indicator(double* v, const Mesh& m, int period, int c0, int c1, int c2, cudaStream_t s) {
+  k_color_indicator<<<grid_for(m.N), kThreads, 0, s>>>(v, m, period, c0, c1, c2);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t accum_abs(double* acc, const double* y, long long n, cudaStream_t s) {
+  k_accum_abs<<<grid_for(n), kThreads, 0, s>>>(acc, y, n);
+  return counted(cudaGetLastError());
+}
 
 cudaError_t dinv_from_diag(const double* diag, double* dinv, long long n, cudaStream_t s) {
   k_dinv<<<grid_for(n), kThreads, 0, s>>>(diag, dinv, n);

@@ -73,6 +73,10 @@ cudaError_t to_f64(double* dst, const float* src, long long n, cudaStream_t s);
 // Arnoldi helpers
 cudaError_t start_vector(double* v, const Mesh& m, unsigned long long seed, cudaStream_t s);
 cudaError_t scale_by(double* w, const double* dinv, long long n, cudaStream_t s);
+// l1 row norms by probing: v = indicator of the interior nodes in one color class (axis indices
+// congruent to (c0, c1, c2) mod period), and acc += |y| after y = A v.
+cudaError_t color_indicator(double* v, const Mesh& m, int period, int c0, int c1, int c2, cudaStream_t s);
+cudaError_t accum_abs(double* acc, const double* y, long long n, cudaStream_t s);
 // One classical Gram-Schmidt pass against the cnt vectors V_i = V + i * ldv: c = V^T w,
 // H[i * ldh] += c[i], w -= V c (partial: cnt * red_blocks(n) doubles; c: cnt doubles).
 cudaError_t project_out(double* w, const double* V, long long ldv, int cnt, long long n, double* partial,
