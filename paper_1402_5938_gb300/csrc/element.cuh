@@ -280,6 +280,126 @@ k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __res
 }
 
 // ---------------------------------------------------------------------------------------
+// FP32 apply, warp-group form (orders p <= 8): each warp owns a group of EW elements (about 128
+// lines per direction) and runs the same sum-factorized phases as k_apply32 on its own
+// shared-memory tiles, one line per lane at a time with the line in registers and the 1D table
+// entries as uniform kernel-parameter operands, separated by __syncwarp only (no block-wide
+// barriers); the geometric factors are read straight from global memory, consecutive lanes on
+// consecutive points of an element (coalesced).
+// ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+struct Apply32wCfg {
+  static constexpr int NP = Sh<DIM, N>::NP, NL = Sh<DIM, N>::NL, NC = Sh<DIM, N>::NC;
+  static constexpr int EW0 = (128 + NL / 2) / NL;
+  static constexpr int EW = EW0 < 1 ? 1 : EW0;  // elements per warp group
+  static constexpr int TILE = EW * NP;            // floats per tile
+  // per warp: U, DIM gradient tiles, then (16-byte aligned) element bases (8 B) and face bits (4 B)
+  static constexpr size_t OFF_BASE = ((size_t)(1 + DIM) * TILE * 4 + 15) / 16 * 16;
+  static constexpr size_t WARP_BYTES = (OFF_BASE + (size_t)EW * 12 + 15) / 16 * 16;
+};
+
+// dst (=, or += if ACC) the table contraction of src along `dir` for the ne elements of a warp
+// group, lane by lane (src may equal dst: a lane reads its whole line before writing it)
+template <int DIM, int N, bool TRN, bool ACC>
+__device__ __forceinline__ void contract_w(const float* src, float* dst, const float* M, int dir, int ne, int lane) {
+  constexpr int NP = Sh<DIM, N>::NP, NL = Sh<DIM, N>::NL;
+  const int total = ne * NL;
+  for (int t = lane; t < total; t += 32) {
+    const int e = t / NL, l = t - e * NL;
+    int base, stride;
+    line_of<DIM, N>(dir, l, base, stride);
+    base += e * NP;
+    float in[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) in[q] = src[base + q * stride];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float s = (TRN ? M[i] : M[i * N]) * in[0];
+#pragma unroll
+      for (int q = 1; q < N; ++q) s = fmaf(TRN ? M[q * N + i] : M[i * N + q], in[q], s);
+      if (ACC) dst[base + i * stride] += s;
+      else dst[base + i * stride] = s;
+    }
+  }
+}
+
+template <int DIM, int N>
+__global__ void __launch_bounds__(128)
+k_apply32w(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ G, const Mesh m,
+           const __grid_constant__ Tab<N, float> tab, const float alpha, const long long ngroups) {
+  using C = Apply32wCfg<DIM, N>;
+  constexpr int NP = C::NP, NC = C::NC, EW = C::EW, TILE = C::TILE;
+  extern __shared__ __align__(128) unsigned char smem_w[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* ws = smem_w + warp * C::WARP_BYTES;
+  float* U = reinterpret_cast<float*>(ws);
+  float* V = U + TILE;  // DIM tiles
+  long long* ebase = reinterpret_cast<long long*>(ws + C::OFF_BASE);
+  int* eflag = reinterpret_cast<int*>(ebase + EW);
+  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
+  const long long gstride = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long grp = (long long)blockIdx.x * (blockDim.x >> 5) + warp; grp < ngroups; grp += gstride) {
+    const long long e0 = grp * EW;
+    const int ne = (int)min((long long)EW, m.nelem - e0);
+    for (int e = lane; e < ne; e += 32) elem_base(m, e0 + e, &ebase[e], &eflag[e]);  // EW may exceed 32
+    __syncwarp();
+    for (int i = lane; i < ne * NP; i += 32) {
+      const int e = i / NP, a = i - e * NP;
+      bool bd;
+      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
+      U[i] = bd ? 0.0f : x[g];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      contract_w<DIM, N, false, false>(U, U, tab.B, d, ne, lane);
+      __syncwarp();
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) contract_w<DIM, N, false, false>(U, V + d * TILE, tab.D, d, ne, lane);
+    __syncwarp();
+    const float* Gg = G + e0 * NC * NP;
+    for (int i = lane; i < ne * NP; i += 32) {
+      const int e = i / NP, q = i - e * NP;
+      const float* g = Gg + (long long)e * NC * NP + q;
+      if (DIM == 3) {
+        const float u0 = V[i], u1 = V[TILE + i], u2 = V[2 * TILE + i];
+        const float g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
+        V[i] = g00 * u0 + g01 * u1 + g02 * u2;
+        V[TILE + i] = g01 * u0 + g11 * u1 + g12 * u2;
+        V[2 * TILE + i] = g02 * u0 + g12 * u1 + g22 * u2;
+      } else {
+        const float u0 = V[i], u1 = V[TILE + i];
+        const float g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
+        V[i] = g00 * u0 + g01 * u1;
+        V[TILE + i] = g01 * u0 + g11 * u1;
+      }
+    }
+    __syncwarp();
+    contract_w<DIM, N, true, false>(V, U, tab.D, 0, ne, lane);
+    __syncwarp();
+    contract_w<DIM, N, true, true>(V + TILE, U, tab.D, 1, ne, lane);
+    __syncwarp();
+    if (DIM == 3) {
+      contract_w<DIM, N, true, true>(V + 2 * TILE, U, tab.D, 2, ne, lane);
+      __syncwarp();
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      contract_w<DIM, N, true, false>(U, U, tab.B, d, ne, lane);
+      __syncwarp();
+    }
+    for (int i = lane; i < ne * NP; i += 32) {
+      const int e = i / NP, a = i - e * NP;
+      bool bd;
+      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
+      if (!bd) atomicAdd(y + g, alpha * U[i]);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // FP64 apply, y += alpha * A x. On GB300 a warp-wide DFMA occupies the SM's FP64 pipe
 // for ~16 cycles while shared-memory loads and integer work issue elsewhere, so this
 // variant optimizes for full warps and balanced SMs rather than for few loads: one

@@ -9,10 +9,12 @@ namespace hmg {
 // y += alpha * A x (FP64 or FP32 data; G in the same precision). Both kernels stage G with
 // bulk TMA copies (FP64: when the slab fits in shared memory) and need G allocated with >= 16
 // bytes of tail padding; a timed-out wait sets *err (device int) to a nonzero code.
-// `variant` selects the block shape (FP64: 0..3, 3 = TMA-staged G; FP32: 0..2 tile sizes); setup
+// `variant` selects the block shape (FP64: 0..3, 3 = TMA-staged G; FP32: 0..2 tile sizes, 3 warp
+// groups without block barriers); setup
 // picks it per level by timing (autotuning).
 constexpr int kApply64Variants = 4;
-constexpr int kApply32Variants = 3;
+constexpr int kApply32Variants = 4;  // 0-2 block tiles, 3 warp groups (orders <= 8; else as 0)
+constexpr int kMaxNWarp32 = 9;
 // FP64 variant kApply64Dense: stored element matrices Ke (launch_elem_mats) instead of sum
 // factorization, for orders with N <= kMaxNDense; other variants ignore Ke.
 constexpr int kApply64Dense = 4;

@@ -45,6 +45,22 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
                         int* err, int variant, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
+    if constexpr (N <= kMaxNWarp32) {
+      if (variant == 3) {  // warp-group form
+        using W = Apply32wCfg<DIM, N>;
+        const int wpb = 4;
+        const size_t smem = (size_t)wpb * W::WARP_BYTES;
+        auto kw = k_apply32w<DIM, N>;
+        cudaError_t e = ensure_smem(kw, smem);
+        if (e != cudaSuccess) return e;
+        const long long ngroups = (m.nelem + W::EW - 1) / W::EW;
+        if (ngroups == 0) return cudaSuccess;
+        const long long grid = std::min<long long>((ngroups + wpb - 1) / wpb,
+                                                   (long long)sm_count() * blocks_per_sm((const void*)kw, 32 * wpb, smem));
+        kw<<<(unsigned)grid, 32 * wpb, smem, s>>>(x, y, G, m, make_tab<N, float>(b), alpha, ngroups);
+        return counted(cudaGetLastError());
+      }
+    }
     constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
     constexpr int NBUF = (DIM == 2 || NP <= 3200) ? 2 : 1;
     using C = Apply32Cfg<DIM, N, NBUF>;

@@ -40,6 +40,7 @@ CASES = [
     dict(dim=3, nelem=(1, 1, 1), order=16),
     dict(dim=2, nelem=(7, 5), order=3),
     dict(dim=2, nelem=(3, 2), order=16),
+    dict(dim=2, nelem=(20, 16), order=1),   # 64 elements per warp group in the warp-group form
 ]
 
 
@@ -121,3 +122,26 @@ def test_mixed_vcycle_close_to_fp64_vcycle(hmg):
     assert e32 < 1e-4          # FP32 V-cycle: rounding of ~30 operator applications
     P64.close()
     P32.close()
+
+
+def test_fp32_warp_group_variant_matches_oracle(tmp_path):
+    """The warp-group FP32 apply (variant 3, orders <= 8, picked by the autotuner where faster)
+    passes the same parity as the block form: pinned for every case through the decision cache,
+    in a fresh process."""
+    import os
+    import subprocess
+    import sys
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lines = []
+    for case in CASES:
+        ne = int(np.prod(case["nelem"]))
+        lines.append(f"0 {case['dim']} {case['order']} {ne} 1 3")   # kind 1 = HMG_PREC_FP32
+    cache = tmp_path / "tune32.txt"
+    cache.write_text("\n".join(lines) + "\n")
+    env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          os.path.join(root, "tests", "test_gpu_mixed.py"), "-k", "fp32_apply_matches_oracle"],
+                         env=env, cwd=root, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stdout[-3000:]
