@@ -659,20 +659,26 @@ def run_paper_tables(args):
                 worst = max(worst, abs((it if it is not None else 10 ** 6) - ref))
                 cells += 1
             print(f"| {p} | " + " | ".join(row) + " |", flush=True)
-    # Table 7, 2d-const rows: point Jacobi vs l1-Jacobi, h-multigrid on 32^2, MG and PCG
+    # Table 7, 2d-const rows: point, element-block and l1-Jacobi, h-multigrid on 32^2, MG and PCG;
+    # beside the counts, the GPU time to solution of each (graph solve, median of 3)
     import torch
 
     import synth
     from paper_1402_5938_gb300 import Problem
     t7 = gold["table7_l1_2d_const"]
-    print("\ntable7_l1_2d_const (GPU / paper)\n")
-    print("| p | pt MG | pt PCG | l1 MG | l1 PCG |")
-    print("|---|---|---|---|---|")
-    ratios = {}
+    t7b = gold["table7_block_2d_const"]
+    print("\ntable7_2d_const (GPU / paper; GPU ms to 1e-8)\n")
+    print("| p | pt MG | pt PCG | blk MG | blk PCG | l1 MG | l1 PCG | PCG ms pt / blk / l1 | setup ms pt / blk / l1 |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    ratios, bratios, times = {}, {}, {}
     for p in (8, 16):
-        got = {}
-        for sm, col in (("jacobi", "pt"), ("l1jacobi", "l1")):
+        got, ms, setup = {}, {}, {}
+        for sm, col in (("jacobi", "pt"), ("blockjacobi", "blk"), ("l1jacobi", "l1")):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             P = Problem(synth.problem(2, 32, p, hier="h", n_hlevels=3, smoother=sm, nu_pre=3, nu_post=3))
+            torch.cuda.synchronize()
+            setup[col] = (time.perf_counter() - t0) * 1e3
             N = P.ndof(0)
             b = torch.zeros(N, dtype=torch.float64, device="cuda")
             P.rhs(torch.from_numpy(synth.nodal_field(7, N)).cuda(), b)
@@ -680,13 +686,97 @@ def run_paper_tables(args):
                 u = torch.zeros_like(b)
                 st, it, _ = P.solve(mode.lower(), b, u, rtol=1e-8, maxit=1000)
                 got[(col, mode)] = it if st == 0 else None
+            tt = []
+            for _ in range(3):
+                u = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                P.solve("pcg", b, u, rtol=1e-8, maxit=1000)
+                torch.cuda.synchronize()
+                tt.append((time.perf_counter() - t0) * 1e3)
+            ms[col] = sorted(tt)[1]
             P.close()
-        print(f"| {p} | " + " | ".join(f"{got[(c_, m)]} / {t7[c_][m][str(p)]}"
-                                        for c_, m in (("pt", "MG"), ("pt", "PCG"), ("l1", "MG"), ("l1", "PCG"))) + " |",
+        gold_of = lambda c_, m: (t7b if c_ == "blk" else t7)[c_][m][str(p)]
+        print(f"| {p} | " + " | ".join(f"{got[(c_, m)]} / {gold_of(c_, m)}"
+                                        for c_ in ("pt", "blk", "l1") for m in ("MG", "PCG")) +
+              f" | {ms['pt']:.2f} / {ms['blk']:.2f} / {ms['l1']:.2f} | {setup['pt']:.0f} / {setup['blk']:.0f} / {setup['l1']:.0f} |",
               flush=True)
         ratios[p] = {m: [got[("l1", m)] / got[("pt", m)], t7["l1"][m][str(p)] / t7["pt"][m][str(p)]] for m in ("MG", "PCG")}
+        bratios[p] = {m: [got[("blk", m)] / got[("pt", m)], t7b["blk"][m][str(p)] / t7b["pt"][m][str(p)]]
+                      for m in ("MG", "PCG")}
+        times[p] = {"pcg_ms": ms, "setup_ms": setup}
     print(json.dumps({"paper_tables": "Tables 1, 4 and 7", "cells": cells, "max_abs_diff": worst,
-                      "table7_l1_over_point_ratios_gpu_vs_paper": ratios}), flush=True)
+                      "table7_l1_over_point_ratios_gpu_vs_paper": ratios,
+                      "table7_block_over_point_ratios_gpu_vs_paper": bratios,
+                      "table7_times_gpu": times}), flush=True)
+    return 0
+
+
+def run_block_jacobi(args):
+    """Element-block Jacobi on the GPU: the zero-guess smoothing step (block inverses on element
+    interiors + point step on shared nodes) against the HBM roofline, and PCG time to 1e-8 with
+    block, point Jacobi and Chebyshev smoothing on the same problems. One JSON line per problem."""
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1402_5938_gb300 import Problem
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    cases = [("2d-const 128^2 Q8, h-MG 5 levels", synth.problem(2, 128, 8, hier="h", n_hlevels=5)),
+             ("2d-const 32^2 Q16, h-MG 3 levels", synth.problem(2, 32, 16, hier="h", n_hlevels=3)),
+             ("3d-var warped 16^3 Q4, p-MG", synth.warped_var3d(16, 4, hier="p")),
+             ("3d-var warped 8^3 Q8, p-MG", synth.warped_var3d(8, 8, hier="p"))]
+    for name, base in cases:
+        out = {"block_jacobi": name}
+        for sm in ("blockjacobi", "jacobi", "cheb"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P = Problem(dict(base, smoother=sm))
+            torch.cuda.synchronize()
+            setup_ms = (time.perf_counter() - t0) * 1e3
+            N = P.ndof(0)
+            b = torch.zeros(N, dtype=torch.float64, device="cuda")
+            P.rhs(torch.from_numpy(synth.nodal_field(3, N)).cuda(), b)
+            u = torch.zeros_like(b)
+            st, it, _ = P.solve("pcg", b, u, rtol=1e-8, maxit=1000)
+            tt = []
+            for _ in range(5):
+                u.zero_()
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                P.solve("pcg", b, u, rtol=1e-8, maxit=1000)
+                torch.cuda.synchronize()
+                tt.append((time.perf_counter() - t0) * 1e3)
+            out[sm] = {"pcg_iterations": it, "status": st, "pcg_ms": statistics.median(tt), "setup_ms": setup_ms}
+            if sm == "blockjacobi":
+                # one zero-guess step on the finest level: x = omega (D_s^-1 b + blockdiag(K_II^-1) b)
+                d, E, p = base["dim"], 1, base["order"]
+                for e in base["nelem"]:
+                    E *= e
+                mi = (p - 1) ** d
+                byts = E * mi * mi * 8 + E * mi * 24 + N * 24   # block inverses, interior gather/RMW, point step
+                x = torch.zeros_like(b)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ts = []
+                for _ in range(10):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    ev[0].record()
+                    P.smooth(0, b, x, 1, zero_guess=True)
+                    ev[1].record()
+                    torch.cuda.synchronize()
+                    ts.append(ev[0].elapsed_time(ev[1]))
+                step_ms = statistics.median(ts[3:])
+                out["block_step"] = {"ms": step_ms, "bytes": byts, "block_bytes": E * mi * mi * 8,
+                                     "achieved_gbs": byts / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                                     "frac": byts / (step_ms * 1e-3) / 1e9 / hbm,
+                                     "kernels": "k_jacobi_first + k_block_smooth (zero guess, 1 step)"}
+            P.close()
+        print(json.dumps(out), flush=True)
     return 0
 
 
@@ -774,6 +864,7 @@ def main():
     ap.add_argument("--mesh-independence", action="store_true",
                     help="Table 6 setting: iterations vs fine mesh at a fixed 2x2 coarsest grid")
     ap.add_argument("--batched", action="store_true", help="512-solve batched workload vs FP64 one at a time")
+    ap.add_argument("--block-jacobi", action="store_true", help="element-block Jacobi: step roofline, solve times")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="Poisson-arrival serving workload")
     ap.add_argument("--requests", type=int, default=200)
@@ -791,6 +882,8 @@ def main():
         return run_paper_tables(args)
     if args.mesh_independence:
         return run_mesh_independence(args)
+    if args.block_jacobi:
+        return run_block_jacobi(args)
     if args.serve:
         return run_serve(args)
     if args.profile_apply:

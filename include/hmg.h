@@ -43,7 +43,12 @@ typedef enum {
 } hmg_status;
 
 typedef enum { HMG_HIER_H = 0, HMG_HIER_P = 1 } hmg_hier;
-typedef enum { HMG_SMOOTH_JACOBI = 0, HMG_SMOOTH_CHEB = 1, HMG_SMOOTH_L1JACOBI = 2 } hmg_smoother;
+typedef enum {
+  HMG_SMOOTH_JACOBI = 0,
+  HMG_SMOOTH_CHEB = 1,
+  HMG_SMOOTH_L1JACOBI = 2,
+  HMG_SMOOTH_BLOCKJACOBI = 3
+} hmg_smoother;
 typedef enum { HMG_MODE_MG = 0, HMG_MODE_PCG = 1 } hmg_mode;
 typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC_BF16 = 3 } hmg_prec;
 
@@ -62,6 +67,12 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC
  *                        accelerated Jacobi of degree nu (Sec. 3.2.1), or l1-Jacobi (Sec. 4.4,
  *                        Table 7): the Jacobi step with D_l1 = diag(sum_j |a_ij|) over the interior
  *                        unknowns, computed at setup by probing A with (2p+1)^d color classes;
+ *                        or element-block Jacobi (Sec. 3.2.3, Sec. 4.4, Table 7): the damped step
+ *                        x += omega M^-1 (b - A x) with M block diagonal, the exact element
+ *                        matrix on each element's (p-1)^d interior nodes (inverted at setup) and
+ *                        the diagonal on the nodes elements share; FP64 only (smooth_prec
+ *                        HMG_PREC_FP64) and (p-1)^d <= 1000 (E * (p-1)^(2d) doubles per level);
+ *                        p = 1 levels have no interior nodes and take the point step.
  *                        omega for the Jacobi forms only.
  *   arnoldi_iters, cheb_lo_frac, cheb_safety : Chebyshev interval [lo_frac*s*lam, s*lam] with
  *                        lam the largest Ritz value of D^-1 A after arnoldi_iters Arnoldi steps

@@ -911,23 +911,37 @@ k_mass(const double* __restrict__ f, double* __restrict__ b, const double* __res
 // (element e, local column b) pair; the element operator is applied to the unit vector
 // e_b by the same sum-factorized phases as k_apply (column b of K_e), and K_e[a][b] is
 // added into A[ia*nI + ib] for interior a and b (interior numbering, x fastest); or, with
-// Ke != nullptr, stored as the element matrix Ke[(e * NP + b) * NP + a] (column-major).
+// Ke != nullptr, stored as the element matrix Ke[(e * NP + b) * NP + a] (column-major); or,
+// with Kb != nullptr, only the columns and rows of the element-interior local nodes (all
+// local indices in 1..N-2, MI = (N-2)^DIM of them, x fastest) are formed and stored as the
+// element's interior block Kb[(e * MI + c) * MI + r]. An element-interior node belongs to
+// no other element, so this block of K_e is also the block of the assembled operator.
 // ---------------------------------------------------------------------------------------
+template <int DIM, int N>
+__device__ __forceinline__ int interior_local(int c) {  // c-th element-interior local node
+  constexpr int M = N > 2 ? N - 2 : 1;  // (N = 2 has no interior nodes and never gets here)
+  const int i = c % M + 1, j = (c / M) % M + 1;
+  return DIM == 3 ? (c / (M * M) + 1) * N * N + j * N + i : j * N + i;
+}
+
 template <int DIM, int N>
 __global__ void __launch_bounds__(256)
 k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
              const __grid_constant__ Tab<N, double> tab, const long long nI, const int epb,
-             double* __restrict__ Ke) {
+             double* __restrict__ Ke, double* __restrict__ Kb) {
   constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
+  constexpr int MI = DIM == 3 ? (N - 2) * (N - 2) * (N - 2) : (N - 2) * (N - 2);
+  const int ncol = Kb != nullptr ? MI : NP;  // columns (tiles) per element
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* U = reinterpret_cast<double*>(smem_raw);
   double* V = U + epb * NP;
   const long long t0 = (long long)blockIdx.x * epb;
-  const long long ntiles = m.nelem * NP;
+  const long long ntiles = m.nelem * ncol;
   const int ne = (int)min((long long)epb, ntiles - t0);
   for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
     const int e = t / NP, a = t - e * NP;
-    const int b = (int)((t0 + e) % NP);
+    const int c = (int)((t0 + e) % ncol);
+    const int b = Kb != nullptr ? interior_local<DIM, N>(c) : c;
     U[t] = (a == b) ? 1.0 : 0.0;
   }
   __syncthreads();
@@ -939,7 +953,7 @@ k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
   __syncthreads();
   for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
     const int e = t / NP, q = t - e * NP;
-    const long long el = (t0 + e) / NP;
+    const long long el = (t0 + e) / ncol;
     const double* g = G + el * NC * NP + q;
     if (DIM == 3) {
       const double u0 = V[t], u1 = V[epb * NP + t], u2 = V[2 * epb * NP + t];
@@ -969,8 +983,17 @@ k_elem_dense(const double* __restrict__ G, double* __restrict__ A, const Mesh m,
   }
   for (int t = threadIdx.x; t < ne * NP; t += blockDim.x) {
     const int e = t / NP, a = t - e * NP;
-    const long long el = (t0 + e) / NP;
-    const int b = (int)((t0 + e) % NP);
+    const long long el = (t0 + e) / ncol;
+    const int b = (int)((t0 + e) % ncol);
+    if (Kb != nullptr) {  // interior rows of interior column b (here the column index c)
+      constexpr int M = N - 2;
+      const int i = a % N, j = (a / N) % N, k = DIM == 3 ? a / (N * N) : 1;
+      if (i >= 1 && i <= M && j >= 1 && j <= M && k >= 1 && k <= M) {
+        const int r = (i - 1) + M * (j - 1) + (DIM == 3 ? M * M * (k - 1) : 0);
+        Kb[(el * MI + b) * MI + r] = U[t];
+      }
+      continue;
+    }
     if (Ke != nullptr) {
       Ke[(el * NP + b) * NP + a] = U[t];
       continue;

@@ -9,6 +9,7 @@
 #include <functional>
 #include <map>
 #include <tuple>
+#include <type_traits>
 #include <mutex>
 #include <set>
 #include <new>
@@ -92,6 +93,8 @@ struct Level {
   float* G32 = nullptr;
   void* G16 = nullptr;    // 16-bit factors of the FP16/BF16 V-cycle operator (orders <= 7)
   double* Ke = nullptr;   // element matrices of a low-order FP64 level (dense-apply variant)
+  double* Kb = nullptr;   // block Jacobi: inverses of the element-interior blocks [E][MI][MI]
+  double* dinv_s = nullptr;  // block Jacobi: D^-1 on shared nodes, 0 at element-interior nodes
   float* gsc = nullptr;   // FP16: per-element power-of-two factor scales
   float* dinv32 = nullptr;
   double lam = 0.0;       // Chebyshev bound
@@ -257,6 +260,9 @@ hmg_status level_shapes(const hmg_desc& d, std::vector<std::pair<std::vector<int
   return HMG_OK;
 }
 
+// Largest element-interior block of the block Jacobi smoother ((p-1)^d unknowns: 3D p <= 11).
+constexpr long long kMaxBlock = 1000;
+
 hmg_status validate(const hmg_desc* d) {
   if (!d) { set_error("null descriptor"); return HMG_EINVAL; }
   if (d->dim != 2 && d->dim != 3) { set_error("dim must be 2 or 3"); return HMG_EINVAL; }
@@ -264,9 +270,20 @@ hmg_status validate(const hmg_desc* d) {
   for (int a = 0; a < d->dim; ++a)
     if (d->nelem[a] < 1 || d->nelem[a] > (1 << 20)) { set_error("nelem out of range"); return HMG_EINVAL; }
   if (d->n_hlevels < 1 || d->n_hlevels > 30) { set_error("n_hlevels must be >= 1"); return HMG_EINVAL; }
-  if (d->smoother != HMG_SMOOTH_JACOBI && d->smoother != HMG_SMOOTH_CHEB && d->smoother != HMG_SMOOTH_L1JACOBI) {
+  if (d->smoother != HMG_SMOOTH_JACOBI && d->smoother != HMG_SMOOTH_CHEB && d->smoother != HMG_SMOOTH_L1JACOBI &&
+      d->smoother != HMG_SMOOTH_BLOCKJACOBI) {
     set_error("bad smoother");
     return HMG_EINVAL;
+  }
+  if (d->smoother == HMG_SMOOTH_BLOCKJACOBI) {
+    if (d->smooth_prec != HMG_PREC_FP64) { set_error("block Jacobi smoothing runs in FP64 only"); return HMG_EINVAL; }
+    long long mi = 1;
+    for (int a = 0; a < d->dim; ++a) mi *= d->order - 1;
+    if (mi > kMaxBlock) {
+      set_error("block Jacobi: (p-1)^d = " + std::to_string(mi) + " interior nodes per element exceeds " +
+                std::to_string(kMaxBlock));
+      return HMG_EINVAL;
+    }
   }
   if (d->nu_pre < 0 || d->nu_post < 0 || d->nu_pre > 64 || d->nu_post > 64) { set_error("bad nu"); return HMG_EINVAL; }
   if (!(fabs(d->warp_amp) * M_PI < 1.0)) { set_error("|warp_amp| * pi must be < 1"); return HMG_EINVAL; }
@@ -436,6 +453,30 @@ hmg_status smooth(ProblemImpl& P, int k, const T* b, T* x, int steps, bool zero,
       r_is_b = reset;
     }
     return HMG_OK;
+  }
+  if (D.smoother == HMG_SMOOTH_BLOCKJACOBI) {
+    if constexpr (std::is_same<T, double>::value) {
+      // element-interior blocks (inverses in Kb) and the diagonal on shared nodes touch disjoint
+      // unknowns; the block part reads r before the point step resets it to b
+      const double w = D.omega;
+      const double* ds = l.Kb ? l.dinv_s : l.dinv;
+      for (int st = 0; st < steps; ++st) {
+        const bool reset = st + 1 < steps || leave_r_b;
+        if (st == 0 && zero) {
+          TRY(jacobi_first<double>(x, b, ds, n, w, s, reset ? r : nullptr));
+          if (l.Kb) TRY(launch_block_smooth(l.m, l.Kb, b, x, w, s));
+        } else {
+          CHECK(residual());
+          if (l.Kb) TRY(launch_block_smooth(l.m, l.Kb, r, x, w, s));
+          TRY(jacobi_step<double>(x, r, b, ds, n, w, reset ? 1 : 0, s));
+        }
+        r_is_b = reset;
+      }
+      return HMG_OK;
+    } else {
+      set_error("block Jacobi smoothing runs in FP64 only");
+      return HMG_EINVAL;
+    }
   }
   // Chebyshev acceleration of Jacobi on [lo, hi] (Saad, Iterative Methods, Alg. 12.1)
   const double hi = D.cheb_safety * l.lam, lo = D.cheb_lo_frac * hi;
@@ -864,6 +905,21 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       }
       TRY(dinv_from_diag(l.r, l.dinv, n, s));
       TRY(cudaMemsetAsync(l.r, 0, n * sizeof(double), s));
+      if (D.smoother == HMG_SMOOTH_BLOCKJACOBI && k + 1 < P.L.size() && block_size_of(l.m) > 0) {
+        // element-interior blocks of K_e, inverted in place; D^-1 kept on the shared nodes only
+        const int MI = block_size_of(l.m);
+        TRY(P.alloc((void**)&l.Kb, (size_t)l.m.nelem * MI * MI * sizeof(double)));
+        TRY(P.alloc((void**)&l.dinv_s, n * sizeof(double)));
+        TRY(launch_elem_blocks(l.m, l.basis, l.G, l.Kb, s));
+        TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        TRY(launch_block_invert(l.Kb, l.m.nelem, MI, bad, s));
+        TRY(cudaMemcpyAsync(l.dinv_s, l.dinv, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        TRY(launch_mask_elem_interior(l.dinv_s, l.m, s));
+        int hb = 0;
+        TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TRY(cudaStreamSynchronize(s));
+        if (hb) { set_error("block Jacobi: an element-interior block is not positive definite"); return HMG_EINVAL; }
+      }
       if (mixed) {
         if (lowp && l.m.p <= kMaxOrder16) {
           TRY(P.alloc((void**)&l.G16, gsz * nc_of(D.dim) * 2 + 256));  // TMA tail padding
@@ -1178,6 +1234,11 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     for (int v = 0; v < 5; ++v) add(n * 8);
     if (m.p + 1 <= kMaxNDense && k + 1 < ms.size() && (k == 0 || !mixed))
       add((size_t)m.nelem * np_of(m) * np_of(m) * 8);  // element matrices (dense-apply variant)
+    if (D.smoother == HMG_SMOOTH_BLOCKJACOBI && k + 1 < ms.size() && block_size_of(m) > 0) {
+      const size_t mi = (size_t)block_size_of(m);
+      add((size_t)m.nelem * mi * mi * 8);  // inverted element-interior blocks
+      add(n * 8);                          // D^-1 on shared nodes
+    }
     if (mixed) {
       if (lowp && m.p <= kMaxOrder16) {
         add(gsz * nc_of(D.dim) * 2 + 256);

@@ -84,17 +84,20 @@ cudaError_t mass_dim(const Mesh& m, const Basis1D& b, const double* f, double* o
 
 template <int DIM>
 cudaError_t dense_dim(const Mesh& m, const Basis1D& b, const double* G, double* A, long long nI,
-                      double* Ke, cudaStream_t s) {
+                      double* Ke, double* Kb, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
     constexpr int NP = Sh<DIM, N>::NP;
+    constexpr long long MI = DIM == 3 ? (N - 2) * (N - 2) * (N - 2) : (N - 2) * (N - 2);
+    const long long ncol = Kb != nullptr ? MI : NP;
+    if (ncol == 0) return cudaSuccess;
     const size_t per = (size_t)(1 + DIM) * NP * sizeof(double);
     const int epb = epb_for(per);
     auto k = k_elem_dense<DIM, N>;
     cudaError_t e = ensure_smem(k, per * epb);
     if (e != cudaSuccess) return e;
-    const long long blocks = (m.nelem * NP + epb - 1) / epb;
-    k<<<(unsigned)blocks, 256, per * epb, s>>>(G, A, m, make_tab<N, double>(b), nI, epb, Ke);
+    const long long blocks = (m.nelem * ncol + epb - 1) / epb;
+    k<<<(unsigned)blocks, 256, per * epb, s>>>(G, A, m, make_tab<N, double>(b), nI, epb, Ke, Kb);
     return counted(cudaGetLastError());
   });
 }
@@ -142,11 +145,18 @@ cudaError_t launch_mass(const Mesh& m, const Basis1D& b, const double* f, double
 
 cudaError_t launch_elem_dense(const Mesh& m, const Basis1D& b, const double* G, double* A,
                               long long nI, cudaStream_t s) {
-  return m.dim == 3 ? dense_dim<3>(m, b, G, A, nI, nullptr, s) : dense_dim<2>(m, b, G, A, nI, nullptr, s);
+  return m.dim == 3 ? dense_dim<3>(m, b, G, A, nI, nullptr, nullptr, s)
+                    : dense_dim<2>(m, b, G, A, nI, nullptr, nullptr, s);
 }
 
 cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, double* Ke, cudaStream_t s) {
-  return m.dim == 3 ? dense_dim<3>(m, b, G, nullptr, 0, Ke, s) : dense_dim<2>(m, b, G, nullptr, 0, Ke, s);
+  return m.dim == 3 ? dense_dim<3>(m, b, G, nullptr, 0, Ke, nullptr, s)
+                    : dense_dim<2>(m, b, G, nullptr, 0, Ke, nullptr, s);
+}
+
+cudaError_t launch_elem_blocks(const Mesh& m, const Basis1D& b, const double* G, double* Kb, cudaStream_t s) {
+  return m.dim == 3 ? dense_dim<3>(m, b, G, nullptr, 0, nullptr, Kb, s)
+                    : dense_dim<2>(m, b, G, nullptr, 0, nullptr, Kb, s);
 }
 
 }  // namespace hmg

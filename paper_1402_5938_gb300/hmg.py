@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "libhmg.so")
 
 HMG_OK, HMG_EINVAL, HMG_ENOMEM, HMG_ENOCONV, HMG_EDEVICE, HMG_ETIMEOUT, HMG_EBUSY, HMG_ENAN = 0, -1, -2, -3, -4, -5, -6, -7
 HIER = {"h": 0, "p": 1}
-SMOOTHER = {"jacobi": 0, "cheb": 1, "l1jacobi": 2}
+SMOOTHER = {"jacobi": 0, "cheb": 1, "l1jacobi": 2, "blockjacobi": 3}
 MODE = {"mg": 0, "pcg": 1}
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 

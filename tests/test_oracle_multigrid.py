@@ -182,3 +182,77 @@ def test_l1_jacobi_counts_follow_table7():
     assert abs(pcg_l1 / pcg_pt - gold["l1"]["PCG"]["8"] / gold["pt"]["PCG"]["8"]) <= 0.15 * gold["l1"]["PCG"]["8"] / gold["pt"]["PCG"]["8"]
     assert abs(mg_l1 - gold["l1"]["MG"]["8"]) <= 0.15 * gold["l1"]["MG"]["8"]
     assert abs(pcg_l1 - gold["l1"]["PCG"]["8"]) <= 2
+
+
+# ---- element-block Jacobi (Table 7) --------------------------------------------------------
+
+def test_block_jacobi_on_one_element_is_the_exact_solve():
+    """One element: every unknown is element-interior, so M = A and one undamped block-Jacobi
+    step from zero solves A x = b (Sec. 3.2.3: exact local solves)."""
+    for dim, p in ((2, 5), (3, 3)):
+        prob = synth.problem(dim, 1, p, warp_amp=0.1, mu_b=1e3, hier="h", n_hlevels=1,
+                             smoother="blockjacobi", omega=1.0)
+        H = multigrid.Hierarchy(prob)
+        A = H.fine.A.toarray()
+        b = synth.uniform_pm1(5, A.shape[0])
+        x = H.jacobi(0, b, None, 1)
+        assert np.linalg.norm(A @ x - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_block_of_assembled_matrix_is_the_element_matrix_block():
+    """The block of the assembled interior matrix on an element's interior nodes equals the
+    element matrix K_e (dense quadrature, fem.element_matrices) on its interior local nodes."""
+    d = fem.Discretization(2, (3, 2), 4, warp_amp=0.1, mu_b=1e3)
+    L = multigrid.Level(d, block=True)
+    n = d.n
+    loc = np.indices((n, n)).reshape(2, -1)
+    inner = np.all((loc > 0) & (loc < n - 1), axis=0)
+    K = d.element_matrices(np.arange(d.n_elem))
+    for e in range(d.n_elem):
+        Ke = K[e][np.ix_(inner, inner)]
+        assert np.allclose(np.linalg.inv(L.blk_inv[e]), Ke, rtol=1e-10, atol=1e-10 * np.abs(Ke).max())
+    # blocks of different elements are disjoint and never touch the Dirichlet boundary
+    idx = L.blk_idx.ravel()
+    assert len(np.unique(idx)) == len(idx) == d.n_elem * (d.p - 1) ** 2
+
+
+def test_block_jacobi_is_point_jacobi_at_order_one():
+    """p = 1 has no element-interior nodes: block Jacobi takes the point-Jacobi step exactly."""
+    sols = []
+    for sm in ("jacobi", "blockjacobi"):
+        prob = synth.problem(2, 8, 1, warp_amp=0.1, mu_b=10.0, hier="h", n_hlevels=3, smoother=sm)
+        H = multigrid.Hierarchy(prob)
+        b = H.fine.disc.rhs(synth.nodal_field(3, H.fine.disc.N))
+        sols.append(H.vcycle(b))
+    assert np.array_equal(sols[0], sols[1])
+
+
+def test_block_jacobi_preconditioner_symmetric_positive_definite():
+    """M^-1 (block inverses plus D^-1 on shared nodes) is symmetric positive definite, so the
+    V(3,3) cycle with it is a symmetric preconditioner for PCG."""
+    prob = synth.problem(2, 3, 4, warp_amp=0.1, mu_b=1e3, hier="h", n_hlevels=1, smoother="blockjacobi")
+    L = multigrid.Hierarchy(prob).fine
+    n = L.A.shape[0]
+    Minv = np.stack([L.block_precondition(np.eye(n)[:, j]) for j in range(n)], axis=1)
+    assert np.allclose(Minv, Minv.T, rtol=0, atol=1e-12 * np.abs(Minv).max())
+    assert np.linalg.eigvalsh(0.5 * (Minv + Minv.T)).min() > 0
+
+
+@pytest.mark.slow
+def test_block_jacobi_counts_follow_table7():
+    """2d-const 32x32, p = 8, h-MG V(3,3), omega = 2/3 (Table 7): block Jacobi needs no more
+    iterations than point Jacobi, and its counts are within 1 (MG) / 1 (PCG) of the printed
+    16 / 8 (the paper's right-hand side is not given)."""
+    gold = GOLDEN["table7_block_2d_const"]
+    counts = {}
+    for sm in ("jacobi", "blockjacobi"):
+        prob = synth.problem(2, 32, 8, hier="h", n_hlevels=3, smoother=sm, nu_pre=3, nu_post=3)
+        H = multigrid.Hierarchy(prob)
+        b = H.fine.disc.rhs(synth.nodal_field(7, H.fine.disc.N))
+        _, it_mg, _, ok1 = H.solve_mg(b)
+        _, it_pcg, _, ok2 = H.solve_pcg(b)
+        assert ok1 and ok2
+        counts[sm] = (it_mg, it_pcg)
+    assert counts["blockjacobi"][0] <= counts["jacobi"][0] and counts["blockjacobi"][1] <= counts["jacobi"][1]
+    assert abs(counts["blockjacobi"][0] - gold["blk"]["MG"]["8"]) <= 1
+    assert abs(counts["blockjacobi"][1] - gold["blk"]["PCG"]["8"]) <= 1
