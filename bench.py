@@ -729,7 +729,9 @@ def run_block_jacobi(args):
              ("2d-const 32^2 Q16, h-MG 3 levels", synth.problem(2, 32, 16, hier="h", n_hlevels=3)),
              ("3d-var warped 16^3 Q4, p-MG", synth.warped_var3d(16, 4, hier="p")),
              ("3d-var warped 8^3 Q8, p-MG", synth.warped_var3d(8, 8, hier="p"))]
-    for name, base in cases:
+    for ci, (name, base) in enumerate(cases):
+        if args.block_case >= 0 and ci != args.block_case:
+            continue
         out = {"block_jacobi": name}
         for sm in ("blockjacobi", "jacobi", "cheb"):
             torch.cuda.synchronize()
@@ -758,12 +760,18 @@ def run_block_jacobi(args):
                 for e in base["nelem"]:
                     E *= e
                 mi = (p - 1) ** d
-                byts = E * mi * mi * 8 + E * mi * 24 + N * 24   # block inverses, interior gather/RMW, point step
+                # block inverses (packed, column pairs), interior gather / x read-modify-write, point step
+                byts = E * ((mi + 1) // 2) * 2 * mi * 8 + E * mi * 24 + N * 24
+                flops = 2 * E * mi * mi + 2 * N
+                # the GEMV does 2 flops per 8-byte entry, above GB300's FP64 ridge (~0.19 flop/B):
+                # its roof is the FP64 pipe unless the bytes take longer
+                t_hbm = byts / (hbm * 1e9)
+                t_fp64 = flops / (FP64_PEAK_TFLOPS * 1e12)
                 x = torch.zeros_like(b)
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 ts = []
                 for _ in range(10):
-                    flush.zero_()
+                    flush.sum()   # evict by reading: no dirty lines left to write back in the timed region
                     torch.cuda.synchronize()
                     ev[0].record()
                     P.smooth(0, b, x, 1, zero_guess=True)
@@ -771,9 +779,13 @@ def run_block_jacobi(args):
                     torch.cuda.synchronize()
                     ts.append(ev[0].elapsed_time(ev[1]))
                 step_ms = statistics.median(ts[3:])
-                out["block_step"] = {"ms": step_ms, "bytes": byts, "block_bytes": E * mi * mi * 8,
+                out["block_step"] = {"ms": step_ms, "bytes": byts, "flops": flops,
+                                     "bound": "fp64" if t_fp64 >= t_hbm else "hbm",
+                                     "roof_ms": max(t_hbm, t_fp64) * 1e3,
+                                     "frac": max(t_hbm, t_fp64) / (step_ms * 1e-3),
                                      "achieved_gbs": byts / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm,
-                                     "frac": byts / (step_ms * 1e-3) / 1e9 / hbm,
+                                     "achieved_tflops": flops / (step_ms * 1e-3) / 1e12,
+                                     "peak_tflops": FP64_PEAK_TFLOPS,
                                      "kernels": "k_jacobi_first + k_block_smooth (zero guess, 1 step)"}
             P.close()
         print(json.dumps(out), flush=True)
@@ -865,6 +877,7 @@ def main():
                     help="Table 6 setting: iterations vs fine mesh at a fixed 2x2 coarsest grid")
     ap.add_argument("--batched", action="store_true", help="512-solve batched workload vs FP64 one at a time")
     ap.add_argument("--block-jacobi", action="store_true", help="element-block Jacobi: step roofline, solve times")
+    ap.add_argument("--block-case", type=int, default=-1, help="--block-jacobi: run only this problem (0..3)")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="Poisson-arrival serving workload")
     ap.add_argument("--requests", type=int, default=200)

@@ -29,7 +29,7 @@ Readings where the paper is silent or garbled (the CUDA library follows the same
 * l1-Jacobi: the added diagonal is the rest of the row's l1 norm, D_l1 = diag(sum_j |a_ij|)
   over the interior unknowns (the paper cites Baker, Falgout, Kolev and Yang 2011 without
   fixing which couplings enter; on one process the full row is the one that changes the method).
-* Block Jacobi: the paper inverts "the element matrices" exactly without saying how blocks of
+* Block Jacobi: the paper inverts the element matrices exactly without saying how blocks of
   elements that share nodes combine. Read as: one block per element on its element-interior
   nodes (local indices 1..p-1 on every axis; such a node belongs to that element alone, so the
   block of the assembled matrix is the element matrix's block), and point Jacobi on the nodes

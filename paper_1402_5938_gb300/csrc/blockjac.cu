@@ -3,7 +3,8 @@
 // share (faces, edges, vertices).
 //
 // Blocks: Kb holds, per element, the MI x MI block (MI = (p-1)^d) of K_e on the element-interior
-// local nodes, x fastest; k_block_invert replaces it in place by its inverse. An element-interior
+// local nodes, x fastest; k_block_invert replaces it in place by its inverse, and k_block_pack
+// lays the inverses out for the smoother's 16-byte loads (Kp). An element-interior
 // node belongs to that element alone, so the block is the assembled operator's block as well,
 // and the blocks of different elements touch disjoint unknowns: the smoother's update
 //   x_I(e) += omega * Kb_e^-1 r_I(e)   (every element),   x_s += omega * r_s / a_ss   (shared s)
@@ -64,32 +65,59 @@ __device__ __forceinline__ long long interior_node(const Mesh& m, long long e, i
   return (r1 * m.p + j) * m.Nn[0] + ex * m.p + i;
 }
 
-// x_I(e) += omega * Kinv_e src_I(e) for EPC elements per thread block, TPE threads per element.
-// Kinv_e is read column by column (Kb[(e * MI + c) * MI + r]), consecutive threads on
-// consecutive rows r (coalesced).
+// Repack the inverses for the smoother: column pairs interleaved per row,
+//   Kp[((e * C2 + c2) * MI + r) * 2 + h] = Kinv_e[r][2 c2 + h]   (C2 = ceil(MI/2), 0 past MI),
+// so that one 16-byte load per thread gives two entries of a row and consecutive threads
+// (rows) read consecutive 16-byte pairs. Kb holds the Gauss-Jordan result, whose [c][r]
+// entry (column-major reading) is Kinv_e[r][c].
+__global__ void k_block_pack(const double* __restrict__ Kb, double* __restrict__ Kp, const long long nelem,
+                             const int MI) {
+  const int C2 = (MI + 1) / 2;
+  const long long tot = nelem * C2 * MI * 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int h = (int)(t & 1);
+    const long long q = t >> 1;
+    const int r = (int)(q % MI);
+    const long long q2 = q / MI;
+    const int c2 = (int)(q2 % C2);
+    const long long e = q2 / C2;
+    const int col = 2 * c2 + h;
+    Kp[t] = col < MI ? Kb[(e * MI + col) * MI + r] : 0.0;
+  }
+}
+
+// x_I(e) += omega * Kinv_e src_I(e) for `epc` consecutive elements per thread block: src on
+// their interior nodes is staged in shared memory (zero-padded to an even length), then the
+// block's threads walk the flattened (element, row) pairs, each a dot product over the row's
+// column pairs with 16-byte loads of Kp and of the staged vector.
 template <int DIM>
-__global__ void __launch_bounds__(256)
-k_block_smooth(const double* __restrict__ Kb, const double* __restrict__ src, double* __restrict__ x,
-               const Mesh m, const int MI, const int tpe, const double omega) {
+__global__ void __launch_bounds__(1024)
+k_block_smooth(const double* __restrict__ Kp, const double* __restrict__ src, double* __restrict__ x,
+               const Mesh m, const int MI, const int epc, const double omega) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int epc = blockDim.x / tpe;
-  const int le = threadIdx.x / tpe, lt = threadIdx.x - le * tpe;
-  double* sv = reinterpret_cast<double*>(smem_raw) + le * MI;
-  const long long e = (long long)blockIdx.x * epc + le;
-  const bool live = le < epc && e < m.nelem;
-  if (live)
-    for (int r = lt; r < MI; r += tpe) sv[r] = src[interior_node<DIM>(m, e, r)];
+  const int C2 = (MI + 1) / 2, MIp = 2 * C2;
+  double* sv = reinterpret_cast<double*>(smem_raw);
+  const long long e0 = (long long)blockIdx.x * epc;
+  const int ne = (int)min((long long)epc, m.nelem - e0);
+  for (int t = threadIdx.x; t < ne * MIp; t += blockDim.x) {
+    const int le = t / MIp, r = t - le * MIp;
+    sv[t] = r < MI ? src[interior_node<DIM>(m, e0 + le, r)] : 0.0;
+  }
   __syncthreads();
-  if (!live) return;
-  const double* K = Kb + e * (long long)MI * MI;
-  for (int r = lt; r < MI; r += tpe) {
-    double z0 = 0.0, z1 = 0.0;  // two independent chains
-    int c = 0;
-    for (; c + 1 < MI; c += 2) {
-      z0 = fma(K[(long long)c * MI + r], sv[c], z0);
-      z1 = fma(K[(long long)(c + 1) * MI + r], sv[c + 1], z1);
+  const double2* K2 = reinterpret_cast<const double2*>(Kp);
+  for (int t = threadIdx.x; t < ne * MI; t += blockDim.x) {
+    const int le = t / MI, r = t - le * MI;
+    const long long e = e0 + le;
+    const double2* Kr = K2 + e * (long long)C2 * MI + r;  // pair c2 of row r at Kr[c2 * MI]
+    const double2* s2 = reinterpret_cast<const double2*>(sv + le * MIp);
+    double z0 = 0.0, z1 = 0.0;
+#pragma unroll 4
+    for (int c2 = 0; c2 < C2; ++c2) {
+      const double2 k = Kr[(long long)c2 * MI];
+      const double2 v = s2[c2];
+      z0 = fma(k.x, v.x, z0);
+      z1 = fma(k.y, v.y, z1);
     }
-    if (c < MI) z0 = fma(K[(long long)c * MI + r], sv[c], z0);
     const long long g = interior_node<DIM>(m, e, r);
     x[g] = fma(omega, z0 + z1, x[g]);
   }
@@ -123,18 +151,27 @@ cudaError_t launch_block_invert(double* Kb, long long nelem, int MI, int* bad, c
   return counted(cudaGetLastError());
 }
 
-cudaError_t launch_block_smooth(const Mesh& m, const double* Kb, const double* src, double* x, double omega,
+long long packed_block_doubles(long long nelem, int MI) { return nelem * ((MI + 1) / 2) * MI * 2; }
+
+cudaError_t launch_block_pack(const double* Kb, double* Kp, long long nelem, int MI, cudaStream_t s) {
+  if (MI <= 0 || nelem <= 0) return cudaSuccess;
+  long long g = (packed_block_doubles(nelem, MI) + 255) / 256;
+  if (g > 152LL * 32) g = 152LL * 32;
+  k_block_pack<<<(unsigned)g, 256, 0, s>>>(Kb, Kp, nelem, MI);
+  return counted(cudaGetLastError());
+}
+
+cudaError_t launch_block_smooth(const Mesh& m, const double* Kp, const double* src, double* x, double omega,
                                 cudaStream_t s) {
   const int MI = block_size_of(m);
   if (MI <= 0) return cudaSuccess;
-  int tpe = ((MI + 31) / 32) * 32;
-  if (tpe > 256) tpe = 256;
-  const int epc = 256 / tpe;
+  const int epc = MI >= 256 ? 1 : 256 / MI;  // about 256 rows per block
+  int threads = ((epc * MI + 31) / 32) * 32;
+  if (threads > 1024) threads = 1024;
   const long long blocks = (m.nelem + epc - 1) / epc;
-  const size_t smem = (size_t)epc * MI * sizeof(double);
-  if (smem > 48 * 1024) return cudaErrorInvalidValue;  // MI <= 1000 gives <= 8 KB per element
-  if (m.dim == 3) k_block_smooth<3><<<(unsigned)blocks, epc * tpe, smem, s>>>(Kb, src, x, m, MI, tpe, omega);
-  else k_block_smooth<2><<<(unsigned)blocks, epc * tpe, smem, s>>>(Kb, src, x, m, MI, tpe, omega);
+  const size_t smem = (size_t)epc * (2 * ((MI + 1) / 2)) * sizeof(double);  // <= 8 KB
+  if (m.dim == 3) k_block_smooth<3><<<(unsigned)blocks, threads, smem, s>>>(Kp, src, x, m, MI, epc, omega);
+  else k_block_smooth<2><<<(unsigned)blocks, threads, smem, s>>>(Kp, src, x, m, MI, epc, omega);
   return counted(cudaGetLastError());
 }
 

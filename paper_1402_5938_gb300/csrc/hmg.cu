@@ -908,16 +908,21 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       if (D.smoother == HMG_SMOOTH_BLOCKJACOBI && k + 1 < P.L.size() && block_size_of(l.m) > 0) {
         // element-interior blocks of K_e, inverted in place; D^-1 kept on the shared nodes only
         const int MI = block_size_of(l.m);
-        TRY(P.alloc((void**)&l.Kb, (size_t)l.m.nelem * MI * MI * sizeof(double)));
+        double* Kw = nullptr;  // blocks and their in-place inversion (setup temporary)
+        CHECK(talloc((void**)&Kw, (size_t)l.m.nelem * MI * MI * sizeof(double)));
+        TRY(P.alloc((void**)&l.Kb, (size_t)packed_block_doubles(l.m.nelem, MI) * sizeof(double)));
         TRY(P.alloc((void**)&l.dinv_s, n * sizeof(double)));
-        TRY(launch_elem_blocks(l.m, l.basis, l.G, l.Kb, s));
+        TRY(launch_elem_blocks(l.m, l.basis, l.G, Kw, s));
         TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
-        TRY(launch_block_invert(l.Kb, l.m.nelem, MI, bad, s));
+        TRY(launch_block_invert(Kw, l.m.nelem, MI, bad, s));
+        TRY(launch_block_pack(Kw, l.Kb, l.m.nelem, MI, s));
         TRY(cudaMemcpyAsync(l.dinv_s, l.dinv, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
         TRY(launch_mask_elem_interior(l.dinv_s, l.m, s));
         int hb = 0;
         TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         TRY(cudaStreamSynchronize(s));
+        tmp.erase(std::find(tmp.begin(), tmp.end(), (void*)Kw));
+        dev_free(Kw, s);
         if (hb) { set_error("block Jacobi: an element-interior block is not positive definite"); return HMG_EINVAL; }
       }
       if (mixed) {
@@ -1225,7 +1230,7 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   const bool lowp = D.smooth_prec == HMG_PREC_FP16 || D.smooth_prec == HMG_PREC_BF16;
   std::vector<Mesh> ms;
   for (auto& sh : shapes) ms.push_back(make_mesh(D.dim, sh.first.data(), sh.second));
-  size_t res = 0, allocs = 0, max_stage = 0, max_tbuf = 0, arnoldi = 0;
+  size_t res = 0, allocs = 0, max_stage = 0, max_tbuf = 0, arnoldi = 0, blk_temp = 0;
   auto add = [&](size_t b) { res += std::max<size_t>(b, 16); ++allocs; };
   for (size_t k = 0; k < ms.size(); ++k) {
     const Mesh& m = ms[k];
@@ -1235,9 +1240,10 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     if (m.p + 1 <= kMaxNDense && k + 1 < ms.size() && (k == 0 || !mixed))
       add((size_t)m.nelem * np_of(m) * np_of(m) * 8);  // element matrices (dense-apply variant)
     if (D.smoother == HMG_SMOOTH_BLOCKJACOBI && k + 1 < ms.size() && block_size_of(m) > 0) {
-      const size_t mi = (size_t)block_size_of(m);
-      add((size_t)m.nelem * mi * mi * 8);  // inverted element-interior blocks
-      add(n * 8);                          // D^-1 on shared nodes
+      const int mi = block_size_of(m);
+      add((size_t)packed_block_doubles(m.nelem, mi) * 8);  // inverted element-interior blocks
+      add(n * 8);                                          // D^-1 on shared nodes
+      blk_temp = std::max(blk_temp, (size_t)m.nelem * mi * mi * 8 + 512);
     }
     if (mixed) {
       if (lowp && m.p <= kMaxOrder16) {
@@ -1278,7 +1284,7 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   const size_t nq0 = (size_t)(ms[0].nelem * np_of(ms[0]));
   if (D.node_xyz) { custom += (size_t)D.dim * N0 * 8; res += (size_t)D.dim * N0 * 8 + 512; }
   if (D.mu_fn) custom += (size_t)(D.dim + 1) * nq0 * 8;
-  const size_t temp = std::max(max_stage + 16 + custom, std::max(arnoldi, (size_t)nI * 16));
+  const size_t temp = std::max(max_stage + 16 + custom + blk_temp, std::max(arnoldi, (size_t)nI * 16));
   if (resident) *resident = res;
   if (peak) *peak = res + temp;
   return HMG_OK;

@@ -69,13 +69,16 @@ cudaError_t launch_elem_dense(const Mesh& m, const Basis1D& b, const double* G, 
 // Element-block Jacobi (blockjac.cu). block_size_of: MI = (p-1)^d element-interior nodes per
 // element (0 for p = 1). launch_elem_blocks: Kb[(e * MI + c) * MI + r] = K_e on the interior
 // nodes (x fastest). launch_block_invert: each block replaced in place by its inverse; *bad
-// (device int) set to 1 on a non-positive pivot. launch_block_smooth: x_I(e) += omega *
-// Kb_e src_I(e) on every element's interior nodes (Kb holding the inverses).
+// (device int) set to 1 on a non-positive pivot. launch_block_pack: the inverses re-laid out
+// into Kp (packed_block_doubles(nelem, MI) doubles, column pairs interleaved per row).
+// launch_block_smooth: x_I(e) += omega * Kinv_e src_I(e) on every element's interior nodes.
 // launch_mask_elem_interior: dinv = 0 at element-interior nodes.
 int block_size_of(const Mesh& m);
+long long packed_block_doubles(long long nelem, int MI);
 cudaError_t launch_elem_blocks(const Mesh& m, const Basis1D& b, const double* G, double* Kb, cudaStream_t s);
 cudaError_t launch_block_invert(double* Kb, long long nelem, int MI, int* bad, cudaStream_t s);
-cudaError_t launch_block_smooth(const Mesh& m, const double* Kb, const double* src, double* x, double omega,
+cudaError_t launch_block_pack(const double* Kb, double* Kp, long long nelem, int MI, cudaStream_t s);
+cudaError_t launch_block_smooth(const Mesh& m, const double* Kp, const double* src, double* x, double omega,
                                 cudaStream_t s);
 cudaError_t launch_mask_elem_interior(double* dinv, const Mesh& m, cudaStream_t s);
 
