@@ -792,6 +792,73 @@ def run_block_jacobi(args):
     return 0
 
 
+def run_spectral(args):
+    """The paper's smoother / two-grid spectral study (Figs. 2-3) on the GPU: for 2d-const and
+    2d-var at p = 1, 4, 16 (961 interior unknowns each), the interior matrix A is assembled by
+    applying the GPU operator to unit vectors and its eigenvectors v_i taken with numpy; then the
+    error propagators of six smoothing steps (hmg_smooth) and of one two-grid cycle (hmg_vcycle
+    on two h-levels, exact coarse solve) are applied to every v_i on the GPU. Reported per
+    smoother: ||S V_upper||_2 (damping of the upper half of the spectrum), the number of singular
+    values of S below 0.1, the two-grid spectral radius rho(T), and the figures' own data -- the
+    largest coefficient of T sum_i v_i and how many exceed 1 -- with each v_i's largest entry made
+    positive (that data depends on such a choice; the other three do not)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import synth
+    __graft_entry__.build()
+    from paper_1402_5938_gb300 import Problem
+    smoothers = ("jacobi", "cheb", "l1jacobi", "blockjacobi")
+    summary = {}
+    print("\n| problem | p | smoother | \\|\\|S V_upper\\|\\| | #sigma(S) < 0.1 | rho(T) two-grid | "
+          "max \\|c\\| of T sum v_i | #\\|c\\| > 1 |")
+    print("|---|---|---|---|---|---|---|---|")
+    for kind in ("2d-const", "2d-var"):
+        for p in (1, 4, 16):
+            for sm in smoothers:
+                P = Problem(synth.spectral_problem(kind, p, sm))
+                N = P.ndof(0)
+                n1 = round(N ** 0.5)
+                interior = np.arange(N).reshape(n1, n1)[1:-1, 1:-1].ravel()
+                idx = torch.from_numpy(interior).cuda()
+                n = len(interior)
+                A = np.empty((n, n))
+                x = torch.zeros(N, dtype=torch.float64, device="cuda")
+                y, z, zero = torch.zeros_like(x), torch.zeros_like(x), torch.zeros_like(x)
+                for j, g in enumerate(interior):
+                    x.zero_()
+                    x[int(g)] = 1.0
+                    P.apply(0, x, y)
+                    A[:, j] = y[idx].cpu().numpy()
+                lam, V = np.linalg.eigh(0.5 * (A + A.T))
+                V *= np.where(V[np.abs(V).argmax(axis=0), np.arange(n)] < 0, -1.0, 1.0)[None, :]
+                S, T = np.empty((n, n)), np.empty((n, n))
+                for j in range(n):
+                    x.zero_()
+                    x[idx] = torch.from_numpy(V[:, j]).cuda()
+                    P.apply(0, x, y)
+                    z.zero_()
+                    P.vcycle(-y, z)
+                    T[:, j] = (x + z)[idx].cpu().numpy()
+                    P.smooth(0, zero, x, 6)
+                    S[:, j] = x[idx].cpu().numpy()
+                Ms, Mt = V.T @ S, V.T @ T
+                c = Mt @ np.ones(n)
+                row = {"smooth_norm_upper": float(np.linalg.norm(Ms[:, n // 2:], 2)),
+                       "smooth_sigma_below_0.1": int(np.sum(np.linalg.svd(Ms, compute_uv=False) < 0.1)),
+                       "twogrid_rho": float(np.abs(np.linalg.eigvals(Mt)).max()),
+                       "figure_max_coef": float(np.abs(c).max()), "figure_coefs_above_1": int(np.sum(np.abs(c) > 1.0))}
+                summary[f"{kind} p{p} {sm}"] = row
+                print(f"| {kind} | {p} | {sm} | {row['smooth_norm_upper']:.3f} | {row['smooth_sigma_below_0.1']} | "
+                      f"{row['twogrid_rho']:.3f} | {row['figure_max_coef']:.3f} | {row['figure_coefs_above_1']} |",
+                      flush=True)
+                P.close()
+    print(json.dumps({"spectral": "Figs. 2-3 setting, 961 unknowns, 6 smoothing steps / two-grid V(3,3)",
+                      "cases": summary}), flush=True)
+    return 0
+
+
 def run_mesh_independence(args):
     """Mesh independence (the paper's Table 6 setting with this library's smoothers): PCG with an
     h-multigrid V(3,3) down to 2 x 2 elements on 2D meshes E x E, E = 4..256, orders 1..16, for
@@ -877,6 +944,7 @@ def main():
                     help="Table 6 setting: iterations vs fine mesh at a fixed 2x2 coarsest grid")
     ap.add_argument("--batched", action="store_true", help="512-solve batched workload vs FP64 one at a time")
     ap.add_argument("--block-jacobi", action="store_true", help="element-block Jacobi: step roofline, solve times")
+    ap.add_argument("--spectral", action="store_true", help="the paper's Figs. 2-3 smoother / two-grid spectral study")
     ap.add_argument("--block-case", type=int, default=-1, help="--block-jacobi: run only this problem (0..3)")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="Poisson-arrival serving workload")
@@ -897,6 +965,8 @@ def main():
         return run_mesh_independence(args)
     if args.block_jacobi:
         return run_block_jacobi(args)
+    if args.spectral:
+        return run_spectral(args)
     if args.serve:
         return run_serve(args)
     if args.profile_apply:

@@ -88,6 +88,17 @@ def mesh_independence_problem(kind, E, order, smoother="cheb"):
     return problem(2, E, order, **base)
 
 
+def spectral_problem(kind, order, smoother="jacobi"):
+    """Smoother / two-grid spectral study (the paper's Figs. 2-3 setting): 2D, 961 interior
+    unknowns for every order (E = 32 / p elements per axis, p in {1, 2, 4, 8, 16}), two h-levels
+    (the coarse grid solved exactly), V(3,3). kind "2d-const": unit square, mu = 1; "2d-var":
+    warped square, mu = 1 + 1e6 sum cos^2(2 pi x_i)."""
+    base = dict(hier="h", n_hlevels=2, smoother=smoother, nu_pre=3, nu_post=3)
+    if kind == "2d-var":
+        base.update(warp_amp=0.1, mu_a=1.0, mu_b=1e6, mu_k=2.0)
+    return problem(2, 32 // order, order, **base)
+
+
 # Seeds of the nodal right-hand sides for the 3D workloads.
 SEED_WARPED_VAR3D = 2
 SEED_PSWEEP3D = 3
