@@ -454,11 +454,26 @@ __device__ __forceinline__ double pt_dot(const double* __restrict__ M, const dou
   for (int m = 1; m < N; ++m) s = fma(TRN ? M[m * N + idx] : M[idx * N + m], src[base + m * stride], s);
   return s;
 }
+// acc + the same sum (one FMA chain: no separate add per direction)
+template <int N, bool TRN>
+__device__ __forceinline__ double pt_dot_acc(const double* __restrict__ M, const double* src, int idx, int base,
+                                             int stride, double acc) {
+#pragma unroll
+  for (int m = 0; m < N; ++m) acc = fma(TRN ? M[m * N + idx] : M[idx * N + m], src[base + m * stride], acc);
+  return acc;
+}
+
+// Scale of the scatter-add: y += alpha * A x with alpha = +1 and -1 (every solver call) taken as
+// a plain or negated add, so that no FP64 multiply is issued per node.
+enum : int { kAlphaOne = 0, kAlphaMinusOne = 1, kAlphaOther = 2 };
+inline int alpha_mode(double alpha) {
+  return alpha == 1.0 ? kAlphaOne : (alpha == -1.0 ? kAlphaMinusOne : kAlphaOther);
+}
 
 template <int DIM, int N, int V>
 __global__ void __launch_bounds__(Apply64Cfg<DIM, N, V>::GT)
 k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ G, const Mesh m,
-          const __grid_constant__ Tab<N, double> tab, const double alpha, int* __restrict__ err) {
+          const __grid_constant__ Tab<N, double> tab, const double alpha, const int amode, int* __restrict__ err) {
   using C = Apply64Cfg<DIM, N, V>;
   constexpr int NP = C::NP, NEG = C::NEG, W = C::W, NC = Sh<DIM, N>::NC;
   constexpr int S1 = N, S2 = N * N;
@@ -569,10 +584,10 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     const int a = t % NP;
     const int i = a % N, j = (a / N) % N;
-    double s = pt_dot<N, true>(sD, V0, i, t - i, 1) + pt_dot<N, true>(sD, V1, j, t - j * S1, S1);
+    double s = pt_dot_acc<N, true>(sD, V1, j, t - j * S1, S1, pt_dot<N, true>(sD, V0, i, t - i, 1));
     if (DIM == 3) {
       const int k = a / (N * N);
-      s += pt_dot<N, true>(sD, V2, k, t - k * S2, S2);
+      s = pt_dot_acc<N, true>(sD, V2, k, t - k * S2, S2, s);
     }
     cur[t] = s;
   }
@@ -595,7 +610,10 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
   for (int t = threadIdx.x; t < nt; t += blockDim.x) {
     bool bd;
     const long long g = node(t, bd);
-    if (!bd) atomicAdd(y + g, alpha * cur[t]);
+    if (!bd) {
+      const double v = cur[t];
+      atomicAdd(y + g, amode == kAlphaOne ? v : (amode == kAlphaMinusOne ? -v : alpha * v));
+    }
   }
 }
 

@@ -17,7 +17,7 @@ cudaError_t apply64_variant(const Mesh& m, const Basis1D& b, const double* x, do
   if (e != cudaSuccess) return e;
   const long long blocks = (m.nelem + C::NEG - 1) / C::NEG;
   if (blocks == 0) return cudaSuccess;
-  kern<<<(unsigned)blocks, C::GT, C::smem, s>>>(x, y, G, m, make_tab<N, double>(b), alpha, err);
+  kern<<<(unsigned)blocks, C::GT, C::smem, s>>>(x, y, G, m, make_tab<N, double>(b), alpha, alpha_mode(alpha), err);
   return counted(cudaGetLastError());
 }
 
