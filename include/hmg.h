@@ -225,6 +225,20 @@ hmg_status hmg_vcycle(hmg_problem* prob, const double* r_dev, double* z_dev, voi
 hmg_status hmg_solve(hmg_problem* prob, int mode, const double* b_dev, double* u_dev, double rtol,
                      int maxit, int* iters, double* res_hist, void* stream);
 
+/* PCG on prob's finest operator A_p (Algorithm 1's loop, from u = 0, to ||r|| <= rtol ||b||)
+ * preconditioned by the low-order operator on the same nodes (Sec. 3.1.3; Sec. 4.2's
+ * "low-order MG pCG" column): `low` is a problem of order 1 on the mesh of order * nelem
+ * elements per axis whose node_xyz are prob's finest node coordinates (hmg_node_coords) and
+ * whose coefficient is prob's, so that both share the node grid and its lexicographic
+ * numbering; each M^-1 r is low's own multigrid-preconditioned CG solve to inner_rtol (the
+ * paper factors the low-order matrix; a tight inner_rtol stands in for that exact solve).
+ * iters: outer CG iterations; inner_iters (may be NULL): inner CG iterations in total;
+ * res_hist as for hmg_solve. HMG_EINVAL if the node grids differ or low is not of order 1.
+ * Synchronizes `stream`. */
+hmg_status hmg_solve_low_order(hmg_problem* prob, hmg_problem* low, const double* b_dev, double* u_dev,
+                               double rtol, int maxit, double inner_rtol, int* iters, long long* inner_iters,
+                               double* res_hist, void* stream);
+
 /* n independent solves (different meshes, orders and coefficients allowed) as one call: every
  * problem's solve is the same device-side graph as hmg_solve's, launched concurrently on a pool
  * of streams forked from and joined back to `stream`, which is synchronized on return.

@@ -14,6 +14,9 @@ TEST INFRASTRUCTURE ONLY. Follows the paper:
 * Sec. 3.2.2 / 4.3: V-cycle with nu_pre / nu_post smoothing steps and an exact solve
   on the coarsest grid; MG as solver until the residual norm drops by 1e8.
 * Algorithm 1: MG-preconditioned CG, one V-cycle per iteration.
+* Sec. 3.1.3 / 4.2 (the "low-order MG pCG" column): CG on the order-p system preconditioned by
+  the exact inverse of the low-order operator -- Q1 elements on the order-p nodes -- which the
+  paper applies by a factorization (here a sparse LU).
 
 Readings where the paper is silent or garbled (the CUDA library follows the same):
 * Chebyshev: the three-term recurrence of Saad, "Iterative Methods for Sparse Linear
@@ -41,6 +44,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
+import scipy.sparse.linalg as spla
 
 from .fem import Discretization
 from .transfer import prolongation
@@ -267,3 +271,37 @@ def arnoldi_lambda_max(L: Level, iters: int, seed: int):
             V.append(w / H[j + 1, j])
     ritz = np.linalg.eigvals(H[:m, :m])
     return float(np.max(ritz.real))
+
+
+def low_order_discretization(disc: Discretization) -> Discretization:
+    """Q1 elements whose nodes are disc's nodes (Sec. 3.1.3): p * E elements per axis, the same
+    node grid and numbering, node coordinates disc's physical ones, disc's coefficient."""
+    return Discretization(disc.dim, tuple(e * disc.p for e in disc.E), 1, mu_a=disc.mu_a, mu_b=disc.mu_b,
+                          mu_k=disc.mu_k, node_xyz=disc.node_coords().T, mu_fn=disc.mu_fn)
+
+
+def solve_pcg_low_order(disc: Discretization, b, rtol=1e-8, maxit=1000):
+    """PCG on disc's interior system A_p from u = 0, preconditioned by the exact inverse of the
+    low-order interior operator A_1 (sparse LU), stopping at ||r|| <= rtol ||r_0||."""
+    A = disc.stiffness()
+    lu = spla.splu(low_order_discretization(disc).stiffness().tocsc())
+    u = np.zeros_like(b)
+    r = b.copy()
+    r0 = np.linalg.norm(r)
+    hist = [r0]
+    z = lu.solve(r)
+    p = z.copy()
+    rho = z @ r
+    for it in range(1, maxit + 1):
+        h = A @ p
+        alpha = rho / (p @ h)
+        u = u + alpha * p
+        r = r - alpha * h
+        hist.append(np.linalg.norm(r))
+        if hist[-1] <= rtol * r0:
+            return u, it, np.array(hist), True
+        z = lu.solve(r)
+        rho_new = z @ r
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+    return u, maxit, np.array(hist), False

@@ -1489,8 +1489,10 @@ hmg_status hmg_vcycle(hmg_problem* p, const double* r, double* z, void* stream) 
   return precondition(P, P.pr, z, s);
 }
 
+// z = M^-1 r of a solve that does not take the problem's own V-cycle (nullptr: the V-cycle)
+using Precond = std::function<hmg_status(const double* r, double* z)>;
 static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit,
-                             int* iters, double* res_hist, void* stream);
+                             int* iters, double* res_hist, void* stream, const Precond& pre = nullptr);
 
 // Reads (and clears) the device error flag set by bounded waits inside kernels.
 static hmg_status device_error(ProblemImpl& P, cudaStream_t s) {
@@ -1528,8 +1530,43 @@ hmg_status hmg_solve(hmg_problem* p, int mode, const double* b, double* u, doubl
   return st;
 }
 
+hmg_status hmg_solve_low_order(hmg_problem* p, hmg_problem* low, const double* b, double* u, double rtol,
+                               int maxit, double inner_rtol, int* iters, long long* inner_iters, double* res_hist,
+                               void* stream) {
+  if (!level_ok(p, 0) || !level_ok(low, 0) || p == low) { set_error("bad problem handles"); return HMG_EINVAL; }
+  const Mesh& mh = p->impl.L[0].m;
+  const Mesh& ml = low->impl.L[0].m;
+  bool same = mh.dim == ml.dim && ml.p == 1;
+  for (int a = 0; a < mh.dim; ++a) same = same && ml.Nn[a] == mh.Nn[a];
+  if (!same) {
+    set_error("the low-order problem must be of order 1 on the same node grid (nelem = order * nelem)");
+    return HMG_EINVAL;
+  }
+  if (!(inner_rtol > 0.0) || !(inner_rtol < 1.0)) { set_error("inner_rtol must be in (0, 1)"); return HMG_EINVAL; }
+  long long inner = 0;
+  if (inner_iters) *inner_iters = 0;
+  // M^-1 r: the low-order system solved by its own multigrid-preconditioned CG to inner_rtol
+  Precond pre = [&](const double* r, double* z) -> hmg_status {
+    int it = 0;
+    const hmg_status st = hmg_solve(low, HMG_MODE_PCG, r, z, inner_rtol, 10000, &it, nullptr, stream);
+    inner += it;
+    if (st != HMG_OK) {
+      set_error(std::string("low-order solve: ") + hmg_last_error());
+      return st == HMG_ENOCONV ? HMG_ENOCONV : st;
+    }
+    return HMG_OK;
+  };
+  hmg_status st = solve_impl(p, HMG_MODE_PCG, b, u, rtol, maxit, iters, res_hist, stream, pre);
+  if (inner_iters) *inner_iters = inner;
+  if (st == HMG_OK || st == HMG_ENOCONV || st == HMG_ENAN) {
+    hmg_status de = device_error(p->impl, (cudaStream_t)stream);
+    if (de != HMG_OK) return de;
+  }
+  return st;
+}
+
 static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* u, double rtol, int maxit,
-                             int* iters, double* res_hist, void* stream) {
+                             int* iters, double* res_hist, void* stream, const Precond& pre) {
   if (!level_ok(p, 0) || !b || !u || maxit < 0 || !(rtol >= 0.0)) { set_error("bad argument"); return HMG_EINVAL; }
   if (mode != HMG_MODE_MG && mode != HMG_MODE_PCG) { set_error("bad mode"); return HMG_EINVAL; }
   ProblemImpl& P = p->impl;
@@ -1552,7 +1589,7 @@ static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* 
     double* bm = P.ph;  // masked copy of b
     TRY(cudaMemcpyAsync(bm, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     for (int it = 1; it <= maxit; ++it) {
-      CHECK(precondition(P, r, z, s));  // z = B (b - A u)
+      CHECK(pre ? pre(r, z) : precondition(P, r, z, s));  // z = B (b - A u)
       TRY(axpy(u, z, n, 1.0, s));       // u += z
       TRY(cudaMemcpyAsync(r, bm, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
       CHECK(apply_level(P, 0, u, r, -1.0, s));
@@ -1570,7 +1607,7 @@ static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* 
   // PCG (Algorithm 1, read as standard preconditioned CG from u0 = 0)
   double* pp = P.pp;
   double* h = P.ph;
-  CHECK(precondition(P, r, z, s));
+  CHECK(pre ? pre(r, z) : precondition(P, r, z, s));
   TRY(cudaMemcpyAsync(pp, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CHECK(dot_to(P, z, r, n, FIN_STORE, S_RHO, 0, false, s));
   for (int it = 1; it <= maxit; ++it) {
@@ -1585,7 +1622,7 @@ static hmg_status solve_impl(hmg_problem* p, int mode, const double* b, double* 
     if (iters) *iters = it;
     if (!isfinite(rn)) { set_error("non-finite residual"); return HMG_ENAN; }
     if (rn <= tol) return HMG_OK;
-    CHECK(precondition(P, r, z, s));
+    CHECK(pre ? pre(r, z) : precondition(P, r, z, s));
     CHECK(pcg_rho_beta(P, z, r, n, s));
     TRY(pcg_direction(pp, z, n, P.S, s));
   }

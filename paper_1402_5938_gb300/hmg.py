@@ -70,6 +70,8 @@ _SIGS = {
     "hmg_smooth": (_I, [_P, _I, _V, _V, _I, _I, _V]),
     "hmg_vcycle": (_I, [_P, _V, _V, _V]),
     "hmg_solve": (_I, [_P, _I, _V, _V, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _V]),
+    "hmg_solve_low_order": (_I, [_P, _P, _V, _V, _D, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(_D), _V]),
     "hmg_restrict_noalloc": (_I, [_I, ctypes.POINTER(ctypes.c_int), _I, _I, _I, _V, _V, _V]),
     "hmg_solve_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_V), ctypes.POINTER(_V), _D, _I,
                                ctypes.POINTER(_I), ctypes.POINTER(ctypes.POINTER(_D)), ctypes.POINTER(_I), _V]),
@@ -272,6 +274,21 @@ class Problem:
         if st not in (HMG_OK, HMG_ENOCONV, HMG_ENAN) or (raise_on_noconv and st != HMG_OK):
             _check(st)
         return st, it.value, np.array(hist[: it.value + 1])
+
+
+    def solve_low_order(self, low, b, u, rtol=1e-8, maxit=1000, inner_rtol=1e-12, stream=None):
+        """hmg_solve_low_order: PCG preconditioned by the low-order problem `low` (a Problem of
+        order 1 on this problem's nodes). Returns (status, iterations, inner iterations, history)."""
+        n = self.ndof(0)
+        it = ctypes.c_int()
+        inner = ctypes.c_longlong()
+        hist = (ctypes.c_double * (maxit + 1))()
+        st = lib().hmg_solve_low_order(self.h, low.h, _ptr(b, n), _ptr(u, n), float(rtol), int(maxit),
+                                       float(inner_rtol), ctypes.byref(it), ctypes.byref(inner), hist,
+                                       _stream(stream))
+        if st not in (HMG_OK, HMG_ENOCONV, HMG_ENAN):
+            _check(st)
+        return st, it.value, inner.value, np.array(hist[: it.value + 1])
 
 
 def solve_batched(problems, mode, bs, us, rtol=1e-8, maxit=1000, stream=None):

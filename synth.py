@@ -99,6 +99,22 @@ def spectral_problem(kind, order, smoother="jacobi"):
     return problem(2, 32 // order, order, **base)
 
 
+def low_order_problem(prob, node_xyz, max_coarse=4000):
+    """The low-order problem on the nodes of `prob` (Sec. 3.1.3): order 1 on order * nelem
+    elements per axis, node coordinates node_xyz ([dim][N], prob's finest nodes), prob's
+    coefficient; h-multigrid with Chebyshev V(3,3), halving the mesh while every axis stays even
+    and the coarsest grid has more than max_coarse interior unknowns."""
+    E = [e * prob["order"] for e in prob["nelem"]]
+    cur, levels = list(E), 1
+    while all(c % 2 == 0 and c >= 4 for c in cur) and int(np.prod([c - 1 for c in cur])) > max_coarse:
+        cur = [c // 2 for c in cur]
+        levels += 1
+    out = problem(prob["dim"], tuple(E), 1, mu_a=prob.get("mu_a", 1.0), mu_b=prob.get("mu_b", 0.0),
+                  mu_k=prob.get("mu_k", 2.0), hier="h", n_hlevels=levels, smoother="cheb")
+    out["node_xyz"] = np.ascontiguousarray(node_xyz, dtype=np.float64)
+    return out
+
+
 # Seeds of the nodal right-hand sides for the 3D workloads.
 SEED_WARPED_VAR3D = 2
 SEED_PSWEEP3D = 3

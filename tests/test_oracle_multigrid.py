@@ -256,3 +256,42 @@ def test_block_jacobi_counts_follow_table7():
     assert counts["blockjacobi"][0] <= counts["jacobi"][0] and counts["blockjacobi"][1] <= counts["jacobi"][1]
     assert abs(counts["blockjacobi"][0] - gold["blk"]["MG"]["8"]) <= 1
     assert abs(counts["blockjacobi"][1] - gold["blk"]["PCG"]["8"]) <= 1
+
+
+# ---- low-order preconditioner (Sec. 3.1.3, Table 1's last column) -------------------------
+
+def test_low_order_discretization_shares_the_node_grid():
+    """Q1 on the order-p nodes: same node count, numbering, interior and physical coordinates."""
+    d = fem.Discretization(2, (3, 2), 4, warp_amp=0.1, mu_b=1e3)
+    lo = multigrid.low_order_discretization(d)
+    assert lo.p == 1 and lo.N == d.N and np.array_equal(lo.interior, d.interior)
+    assert np.allclose(lo.node_coords(), d.node_coords(), rtol=0, atol=1e-15)
+    # on affine elements with mu = 1 both operators annihilate nothing but agree on linears:
+    # a(phi_i, x) is the same boundary-flux functional for the linear function x
+    d2 = fem.Discretization(2, (2, 2), 3)
+    lo2 = multigrid.low_order_discretization(d2)
+    x = d2.node_coords()[:, 0]
+    Ah = d2.assemble()
+    Al = lo2.assemble()
+    assert np.allclose((Ah @ x)[d2.interior], 0.0, atol=1e-12)
+    assert np.allclose((Al @ x)[d2.interior], 0.0, atol=1e-12)
+
+
+def test_low_order_preconditioner_is_exact_at_order_one():
+    """At p = 1 the low-order operator is the operator: preconditioned CG takes one iteration."""
+    d = fem.Discretization(2, 8, 1, warp_amp=0.1, mu_b=1e3)
+    b = d.rhs(synth.nodal_field(5, d.N))
+    _, it, _, ok = multigrid.solve_pcg_low_order(d, b)
+    assert ok and it == 1
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p", [2, 3, 4, 8])
+def test_low_order_pcg_counts_follow_table1(p):
+    """2d-const 32x32: CG preconditioned by the factored low-order operator takes the printed
+    number of iterations within 1 (the paper's right-hand side is not given)."""
+    gold = GOLDEN["table1_low_order_2d_const"]["PCG"][str(p)]
+    d = fem.Discretization(2, 32, p)
+    b = d.rhs(synth.nodal_field(7, d.N))
+    _, it, _, ok = multigrid.solve_pcg_low_order(d, b)
+    assert ok and abs(it - gold) <= 1, (p, it, gold)
