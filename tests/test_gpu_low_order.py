@@ -37,7 +37,7 @@ def _low(hmg, P, prob):
 
 
 CASES = [synth.problem(2, 32, 4, hier="h"),
-         synth.problem(2, (8, 6), 6, warp_amp=0.1, mu_b=1e3, hier="p"),
+         synth.problem(2, (8, 6), 6, warp_amp=0.1, mu_b=1e3, hier="p", n_hlevels=2),
          synth.problem(2, 4, 16, warp_amp=0.1, mu_b=10.0, hier="p", n_hlevels=2),
          synth.problem(3, 4, 4, warp_amp=0.1, mu_b=1e3, hier="p"),
          synth.problem(3, (4, 2, 2), 3, warp_amp=0.1, mu_b=1e3, hier="h", n_hlevels=2)]
