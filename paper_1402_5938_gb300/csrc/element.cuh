@@ -156,7 +156,7 @@ struct Apply32Cfg {
 };
 
 template <int DIM, int N, int NBUF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ G, const Mesh m,
           const __grid_constant__ Tab<N, float> tab, const float alpha, const int epb, const long long ntiles,
           int* __restrict__ err) {

@@ -1644,10 +1644,10 @@ hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const d
       if (probs[j] == probs[i]) { set_error("a handle appears twice in the batch"); return HMG_EINVAL; }
   }
   for (int i = 0; i < n; ++i) CHECK(build_lockstep(probs[i]->impl, mode));
-  // streams in the fan-out (HMG_BATCH_STREAMS, 1..64, default 16)
+  // streams in the fan-out (HMG_BATCH_STREAMS, 1..64, default 32)
   static const int K = [] {
     const char* v = getenv("HMG_BATCH_STREAMS");
-    const int k = v ? atoi(v) : 16;
+    const int k = v ? atoi(v) : 32;
     return k < 1 ? 1 : (k > 64 ? 64 : k);
   }();
   static std::mutex pool_mu;

@@ -77,8 +77,14 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
     if (e != cudaSuccess) return e;
     const long long ntiles = (m.nelem + epb - 1) / epb;
     if (ntiles == 0) return cudaSuccess;
-    const long long grid = std::min<long long>(ntiles, (long long)sm_count() * blocks_per_sm((const void*)kern, 256, smem));
-    kern<<<(unsigned)grid, 256, smem, s>>>(x, y, G, m, make_tab<N, float>(b), alpha, epb, ntiles, err);
+    // one thread per line of a contraction phase (epb * N^(d-1) lines), rounded up to whole
+    // warps; tiles with fewer lines keep 256 threads for their point-parallel phases
+    constexpr int NL = Sh<DIM, N>::NL;
+    const int lines = epb * NL;
+    const int threads = lines >= 160 ? std::min(512, (lines + 31) / 32 * 32) : 256;
+    const long long grid =
+        std::min<long long>(ntiles, (long long)sm_count() * blocks_per_sm((const void*)kern, threads, smem));
+    kern<<<(unsigned)grid, threads, smem, s>>>(x, y, G, m, make_tab<N, float>(b), alpha, epb, ntiles, err);
     return counted(cudaGetLastError());
   });
 }
