@@ -34,7 +34,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_apply64<3,n> launch on this workload,
 # from the ncu capture summarized in profiles/apply64_fp64_q4_16cube.md (n = p + 1)
-APPLY_TRAFFIC = {5: 28.736768e6}
+APPLY_TRAFFIC = {5: 28.744704e6}
 
 
 def workload(hier):
