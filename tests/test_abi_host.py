@@ -71,3 +71,21 @@ def test_status_strings(hmg):
     lib = hmg.lib()
     for s in range(-7, 1):
         assert lib.hmg_status_string(s)
+
+
+def test_workload_builders_for_the_paper_studies():
+    """Host logic of the study workloads: the spectral problems have 961 interior unknowns at
+    every order, and the low-order problem is order 1 on order * nelem elements with an h-hierarchy
+    whose coarsest grid is small (or the finest grid itself when it cannot be halved)."""
+    import numpy as np
+    import synth
+    for p in (1, 2, 4, 8, 16):
+        pr = synth.spectral_problem("2d-var", p, "cheb")
+        assert pr["n_hlevels"] == 2 and ((pr["nelem"][0] * p) - 1) ** 2 == 961
+    for prob, levels in ((synth.problem(2, 32, 8), 3), (synth.problem(2, 32, 3), 2),
+                         (synth.problem(3, 4, 4), 1), (synth.problem(2, (7, 5), 3), 1)):
+        N = int(np.prod([e * prob["order"] + 1 for e in prob["nelem"]]))
+        lo = synth.low_order_problem(prob, np.zeros((prob["dim"], N)))
+        assert lo["order"] == 1 and list(lo["nelem"]) == [e * prob["order"] for e in prob["nelem"]]
+        assert lo["n_hlevels"] == levels, (prob["nelem"], prob["order"], lo["n_hlevels"])
+        assert lo["node_xyz"].shape == (prob["dim"], N)
