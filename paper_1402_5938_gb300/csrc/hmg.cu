@@ -391,8 +391,7 @@ constexpr double kFuseRow = 32.0;
 bool fuse_transfer(const Axis1D* M, int dim, const long long out_dim[3]) {
   double row = 1.0;
   for (int a = 0; a < dim; ++a) row *= (double)M[a].nnz / std::max(1, M[a].n_out);
-  return row <= kFuseRow && row * out_dim[0] * out_dim[1] * out_dim[2] <= kFuseTerms &&
-         transfer3_smem(M, dim, false) <= 48 * 1024;
+  return row <= kFuseRow && row * out_dim[0] * out_dim[1] * out_dim[2] <= kFuseTerms;
 }
 
 // x_f (=, or += if acc) P x_c between level k (fine) and k+1 (coarse).

@@ -384,48 +384,15 @@ struct Rows3 {
   const int* rowptr[3];
   const int* col[3];
   const V* val[3];
-  int n_out[3];
-  int nnz[3];
 };
 
-// One output node per thread (32-bit indices: the fused form is only taken on small levels).
-// The block first copies the three 1D stencils (row pointers, columns, values) into shared
-// memory, so the triple loop reads no dependent global addresses.
 template <typename T, typename V>
-__global__ void k_transfer3(const T* __restrict__ in, T* __restrict__ out, const Rows3<V> R, const int ix,
-                            const int iy, const int iz, const int ox, const int oy, const int oz, const int dim,
-                            const int acc) {
-  extern __shared__ __align__(16) unsigned char smem_t3[];
-  V* sval[3];
-  int* srow[3];
-  int* scol[3];
-  {
-    V* pv = reinterpret_cast<V*>(smem_t3);
-    for (int a = 0; a < dim; ++a) { sval[a] = pv; pv += R.nnz[a]; }
-    int* pi = reinterpret_cast<int*>(pv);
-    for (int a = 0; a < dim; ++a) {
-      srow[a] = pi;
-      pi += R.n_out[a] + 1;
-      scol[a] = pi;
-      pi += R.nnz[a];
-    }
-    for (int a = dim; a < 3; ++a) {  // 2D: the third axis is never read; keep its pointers valid
-      sval[a] = sval[0];
-      srow[a] = srow[0];
-      scol[a] = scol[0];
-    }
-    for (int a = 0; a < dim; ++a) {
-      for (int t = threadIdx.x; t <= R.n_out[a]; t += blockDim.x) srow[a][t] = R.rowptr[a][t];
-      for (int t = threadIdx.x; t < R.nnz[a]; t += blockDim.x) {
-        scol[a][t] = R.col[a][t];
-        sval[a][t] = R.val[a][t];
-      }
-    }
-  }
-  __syncthreads();
-  const int tot = ox * oy * oz;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x) {
-    const int I = t % ox, J = (t / ox) % oy, K = t / (ox * oy);
+__global__ void k_transfer3(const T* __restrict__ in, T* __restrict__ out, const Rows3<V> R, const long long ix,
+                            const long long iy, const long long iz, const long long ox, const long long oy,
+                            const long long oz, const int dim, const int acc) {
+  const long long tot = ox * oy * oz;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long I = t % ox, J = (t / ox) % oy, K = t / (ox * oy);
     bool obd = (I == 0) | (I == ox - 1) | (J == 0) | (J == oy - 1);
     if (dim == 3) obd |= (K == 0) | (K == oz - 1);
     if (obd) {
@@ -433,20 +400,20 @@ __global__ void k_transfer3(const T* __restrict__ in, T* __restrict__ out, const
       continue;
     }
     T s = T(0);
-    const int kz0 = dim == 3 ? srow[2][K] : 0, kz1 = dim == 3 ? srow[2][K + 1] : 1;
+    const int kz0 = dim == 3 ? R.rowptr[2][K] : 0, kz1 = dim == 3 ? R.rowptr[2][K + 1] : 1;
     for (int a = kz0; a < kz1; ++a) {
-      const int k = dim == 3 ? scol[2][a] : 0;
+      const long long k = dim == 3 ? R.col[2][a] : 0;
       if (dim == 3 && (k == 0 || k == iz - 1)) continue;
-      const T wz = dim == 3 ? (T)sval[2][a] : T(1);
-      for (int b = srow[1][J]; b < srow[1][J + 1]; ++b) {
-        const int j = scol[1][b];
+      const T wz = dim == 3 ? (T)R.val[2][a] : T(1);
+      for (int b = R.rowptr[1][J]; b < R.rowptr[1][J + 1]; ++b) {
+        const long long j = R.col[1][b];
         if (j == 0 || j == iy - 1) continue;
-        const T w = wz * (T)sval[1][b];
-        const T* row = in + ((long long)k * iy + j) * ix;
-        for (int c = srow[0][I]; c < srow[0][I + 1]; ++c) {
-          const int i = scol[0][c];
+        const T w = wz * (T)R.val[1][b];
+        const T* row = in + (k * iy + j) * ix;
+        for (int c = R.rowptr[0][I]; c < R.rowptr[0][I + 1]; ++c) {
+          const long long i = R.col[0][c];
           if (i == 0 || i == ix - 1) continue;
-          s = fma(w * (T)sval[0][c], row[i], s);
+          s = fma(w * (T)R.val[0][c], row[i], s);
         }
       }
     }
@@ -663,33 +630,20 @@ cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, cons
                                                           M.col, M.val, mask_in, mask_out, accumulate);
   return counted(cudaGetLastError());
 }
-size_t transfer3_smem(const Axis1D* M, int dim, bool fp32) {
-  size_t b = 0;
-  for (int a = 0; a < dim; ++a) b += (size_t)M[a].nnz * (fp32 ? 4 : 8) + (size_t)(M[a].n_out + 1 + M[a].nnz) * 4;
-  return (b + 15) & ~(size_t)15;
-}
-
 template <typename T>
 cudaError_t transfer3(const T* in, T* out, const long long in_dim[3], const long long out_dim[3], const Axis1D* M,
                       int dim, int accumulate, cudaStream_t s) {
   const long long tot = out_dim[0] * out_dim[1] * out_dim[2];
-  const bool fp32 = std::is_same<T, float>::value;
-  const size_t smem = transfer3_smem(M, dim, fp32);
-  if (tot >= (1LL << 31) || smem > 48 * 1024) return cudaErrorInvalidValue;  // callers check fits first
-  const int ix = (int)in_dim[0], iy = (int)in_dim[1], iz = (int)in_dim[2];
-  const int ox = (int)out_dim[0], oy = (int)out_dim[1], oz = (int)out_dim[2];
-  if (fp32) {
+  if (std::is_same<T, float>::value) {
     Rows3<float> R{};
-    for (int a = 0; a < dim; ++a) {
-      R.rowptr[a] = M[a].rowptr; R.col[a] = M[a].col; R.val[a] = M[a].val32; R.n_out[a] = M[a].n_out; R.nnz[a] = M[a].nnz;
-    }
-    k_transfer3<T, float><<<grid_for(tot), kThreads, smem, s>>>(in, out, R, ix, iy, iz, ox, oy, oz, dim, accumulate);
+    for (int a = 0; a < dim; ++a) { R.rowptr[a] = M[a].rowptr; R.col[a] = M[a].col; R.val[a] = M[a].val32; }
+    k_transfer3<T, float><<<grid_for(tot), kThreads, 0, s>>>(in, out, R, in_dim[0], in_dim[1], in_dim[2], out_dim[0],
+                                                             out_dim[1], out_dim[2], dim, accumulate);
   } else {
     Rows3<double> R{};
-    for (int a = 0; a < dim; ++a) {
-      R.rowptr[a] = M[a].rowptr; R.col[a] = M[a].col; R.val[a] = M[a].val; R.n_out[a] = M[a].n_out; R.nnz[a] = M[a].nnz;
-    }
-    k_transfer3<T, double><<<grid_for(tot), kThreads, smem, s>>>(in, out, R, ix, iy, iz, ox, oy, oz, dim, accumulate);
+    for (int a = 0; a < dim; ++a) { R.rowptr[a] = M[a].rowptr; R.col[a] = M[a].col; R.val[a] = M[a].val; }
+    k_transfer3<T, double><<<grid_for(tot), kThreads, 0, s>>>(in, out, R, in_dim[0], in_dim[1], in_dim[2],
+                                                              out_dim[0], out_dim[1], out_dim[2], dim, accumulate);
   }
   return counted(cudaGetLastError());
 }

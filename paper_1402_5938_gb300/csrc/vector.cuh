@@ -100,8 +100,6 @@ cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, cons
 // input boundary nodes skipped, output boundary nodes zero (or left alone when accumulating).
 // Equal to the dim axis passes of axis_pass up to rounding; worth it where the product rows are
 // short and the levels small (the launches saved outweigh the extra terms).
-// Shared memory transfer3 needs for the stencils M[0..dim-1] (<= 48 KB to launch).
-size_t transfer3_smem(const Axis1D* M, int dim, bool fp32);
 template <typename T>
 cudaError_t transfer3(const T* in, T* out, const long long in_dim[3], const long long out_dim[3], const Axis1D* M,
                       int dim, int accumulate, cudaStream_t s);
