@@ -381,17 +381,14 @@ hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float al
   return HMG_OK;
 }
 
-// Whether a transfer with 1D factors M onto out_dim nodes runs as one fused launch: when each
-// output's terms (the product of the average 1D row lengths) stay few enough for one thread's
-// serial loop (kFuseRow) and all terms under kFuseTerms, about what the FP64 pipe does in the
-// time of the two launches the axis passes would add. Prolongations qualify on small levels;
-// restrictions, whose coarse rows are long, only where the coarse grid is small.
+// Whether a transfer with 1D factors M onto out_dim nodes runs as one fused launch: when its
+// terms (outputs x the product of the average 1D row lengths) stay under kFuseTerms, about what
+// the FP64 pipe does in the time of the two launches the axis passes would add.
 constexpr double kFuseTerms = 5.0e5;
-constexpr double kFuseRow = 32.0;
 bool fuse_transfer(const Axis1D* M, int dim, const long long out_dim[3]) {
-  double row = 1.0;
-  for (int a = 0; a < dim; ++a) row *= (double)M[a].nnz / std::max(1, M[a].n_out);
-  return row <= kFuseRow && row * out_dim[0] * out_dim[1] * out_dim[2] <= kFuseTerms;
+  double terms = (double)out_dim[0] * out_dim[1] * out_dim[2];
+  for (int a = 0; a < dim; ++a) terms *= (double)M[a].nnz / std::max(1, M[a].n_out);
+  return terms <= kFuseTerms;
 }
 
 // x_f (=, or += if acc) P x_c between level k (fine) and k+1 (coarse).
