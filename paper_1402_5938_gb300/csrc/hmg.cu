@@ -329,7 +329,6 @@ hmg_status build_axis(ProblemImpl& P, const Level& f, const Level& c, int a, Axi
     }
     out->n_out = (int)R.size();
     out->n_in = n_in;
-    out->nnz = (int)ci.size();
     TRY(P.alloc((void**)&out->rowptr, rp.size() * sizeof(int)));
     TRY(P.alloc((void**)&out->col, ci.size() * sizeof(int)));
     TRY(P.alloc((void**)&out->val, v.size() * sizeof(double)));
@@ -381,26 +380,12 @@ hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float al
   return HMG_OK;
 }
 
-// Whether a transfer with 1D factors M onto out_dim nodes runs as one fused launch: when its
-// terms (outputs x the product of the average 1D row lengths) stay under kFuseTerms, about what
-// the FP64 pipe does in the time of the two launches the axis passes would add.
-constexpr double kFuseTerms = 5.0e5;
-bool fuse_transfer(const Axis1D* M, int dim, const long long out_dim[3]) {
-  double terms = (double)out_dim[0] * out_dim[1] * out_dim[2];
-  for (int a = 0; a < dim; ++a) terms *= (double)M[a].nnz / std::max(1, M[a].n_out);
-  return terms <= kFuseTerms;
-}
-
 // x_f (=, or += if acc) P x_c between level k (fine) and k+1 (coarse).
 template <typename T>
 hmg_status prolong(ProblemImpl& P, int k, const T* xc, T* xf, bool acc, cudaStream_t s) {
   Level& f = P.L[k];
   Level& c = P.L[k + 1];
   const int dim = f.m.dim;
-  if (fuse_transfer(f.P, dim, f.m.Nn)) {
-    TRY(transfer3<T>(xc, xf, c.m.Nn, f.m.Nn, f.P, dim, acc ? 1 : 0, s));
-    return HMG_OK;
-  }
   long long od[3] = {c.m.Nn[0], c.m.Nn[1], c.m.Nn[2]};
   const T* in = xc;
   T* bufs[2] = {(T*)P.t1, (T*)P.t2};
@@ -420,10 +405,6 @@ hmg_status restrict_(ProblemImpl& P, int k, const T* rf, T* rc, cudaStream_t s) 
   Level& f = P.L[k];
   Level& c = P.L[k + 1];
   const int dim = f.m.dim;
-  if (fuse_transfer(f.PT, dim, c.m.Nn)) {
-    TRY(transfer3<T>(rf, rc, f.m.Nn, c.m.Nn, f.PT, dim, 0, s));
-    return HMG_OK;
-  }
   long long od[3] = {f.m.Nn[0], f.m.Nn[1], f.m.Nn[2]};
   const T* in = rf;
   T* bufs[2] = {(T*)P.t1, (T*)P.t2};

@@ -147,7 +147,7 @@ extern "C" hmg_status hmg_restrict_noalloc(int dim, const int nelem_fine[3], int
     return HMG_EDEVICE;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  Axis1D ax[3]{};
+  Axis1D ax[3];
   for (int a = 0; a < dim; ++a) {
     std::vector<int> rp, ci;
     std::vector<double> v;

@@ -379,49 +379,6 @@ __global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, long long 
   }
 }
 
-template <typename V>
-struct Rows3 {
-  const int* rowptr[3];
-  const int* col[3];
-  const V* val[3];
-};
-
-template <typename T, typename V>
-__global__ void k_transfer3(const T* __restrict__ in, T* __restrict__ out, const Rows3<V> R, const long long ix,
-                            const long long iy, const long long iz, const long long ox, const long long oy,
-                            const long long oz, const int dim, const int acc) {
-  const long long tot = ox * oy * oz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long I = t % ox, J = (t / ox) % oy, K = t / (ox * oy);
-    bool obd = (I == 0) | (I == ox - 1) | (J == 0) | (J == oy - 1);
-    if (dim == 3) obd |= (K == 0) | (K == oz - 1);
-    if (obd) {
-      if (!acc) out[t] = T(0);
-      continue;
-    }
-    T s = T(0);
-    const int kz0 = dim == 3 ? R.rowptr[2][K] : 0, kz1 = dim == 3 ? R.rowptr[2][K + 1] : 1;
-    for (int a = kz0; a < kz1; ++a) {
-      const long long k = dim == 3 ? R.col[2][a] : 0;
-      if (dim == 3 && (k == 0 || k == iz - 1)) continue;
-      const T wz = dim == 3 ? (T)R.val[2][a] : T(1);
-      for (int b = R.rowptr[1][J]; b < R.rowptr[1][J + 1]; ++b) {
-        const long long j = R.col[1][b];
-        if (j == 0 || j == iy - 1) continue;
-        const T w = wz * (T)R.val[1][b];
-        const T* row = in + (k * iy + j) * ix;
-        for (int c = R.rowptr[0][I]; c < R.rowptr[0][I + 1]; ++c) {
-          const long long i = R.col[0][c];
-          if (i == 0 || i == ix - 1) continue;
-          s = fma(w * (T)R.val[0][c], row[i], s);
-        }
-      }
-    }
-    if (acc) out[t] += s;
-    else out[t] = s;
-  }
-}
-
 __global__ void k_gj_copy(const double* __restrict__ A, long long n, long long k, double* __restrict__ rowk,
                           double* __restrict__ colk) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -630,28 +587,6 @@ cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, cons
                                                           M.col, M.val, mask_in, mask_out, accumulate);
   return counted(cudaGetLastError());
 }
-template <typename T>
-cudaError_t transfer3(const T* in, T* out, const long long in_dim[3], const long long out_dim[3], const Axis1D* M,
-                      int dim, int accumulate, cudaStream_t s) {
-  const long long tot = out_dim[0] * out_dim[1] * out_dim[2];
-  if (std::is_same<T, float>::value) {
-    Rows3<float> R{};
-    for (int a = 0; a < dim; ++a) { R.rowptr[a] = M[a].rowptr; R.col[a] = M[a].col; R.val[a] = M[a].val32; }
-    k_transfer3<T, float><<<grid_for(tot), kThreads, 0, s>>>(in, out, R, in_dim[0], in_dim[1], in_dim[2], out_dim[0],
-                                                             out_dim[1], out_dim[2], dim, accumulate);
-  } else {
-    Rows3<double> R{};
-    for (int a = 0; a < dim; ++a) { R.rowptr[a] = M[a].rowptr; R.col[a] = M[a].col; R.val[a] = M[a].val; }
-    k_transfer3<T, double><<<grid_for(tot), kThreads, 0, s>>>(in, out, R, in_dim[0], in_dim[1], in_dim[2],
-                                                              out_dim[0], out_dim[1], out_dim[2], dim, accumulate);
-  }
-  return counted(cudaGetLastError());
-}
-template cudaError_t transfer3<double>(const double*, double*, const long long*, const long long*, const Axis1D*, int,
-                                       int, cudaStream_t);
-template cudaError_t transfer3<float>(const float*, float*, const long long*, const long long*, const Axis1D*, int,
-                                      int, cudaStream_t);
-
 template cudaError_t axis_pass<double>(const double*, double*, const long long*, int, const Axis1D&, int, int,
                                        int, cudaStream_t);
 template cudaError_t axis_pass<float>(const float*, float*, const long long*, int, const Axis1D&, int, int, int,

@@ -31,7 +31,6 @@ constexpr int kRedBlocks = 1216;  // fixed partial count (8 x 152 SMs); fixed =>
 // Axis transfer: one 1D CSR matrix (rows = output indices along the axis).
 struct Axis1D {
   int n_out, n_in;
-  int nnz;           // entries (host copy of rowptr[n_out])
   int* rowptr;       // device, n_out + 1
   int* col;          // device, nnz
   double* val;       // device, nnz
@@ -95,14 +94,6 @@ cudaError_t node_coords(double* xyz, const Mesh& m, const double* gll, double wa
 template <typename T>
 cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, const Axis1D& M, int mask_in,
                       int mask_out, int accumulate, cudaStream_t s);
-// The whole tensor-product transfer out (=, or += if accumulate) (M[2] x M[1] x M[0]) in as one
-// launch: each output node sums over the product of its three 1D rows (M[2] unused in 2D),
-// input boundary nodes skipped, output boundary nodes zero (or left alone when accumulating).
-// Equal to the dim axis passes of axis_pass up to rounding; worth it where the product rows are
-// short and the levels small (the launches saved outweigh the extra terms).
-template <typename T>
-cudaError_t transfer3(const T* in, T* out, const long long in_dim[3], const long long out_dim[3], const Axis1D* M,
-                      int dim, int accumulate, cudaStream_t s);
 
 // Dense coarsest level: Gauss-Jordan inverse in place (SPD, no pivoting), and the solve
 // x[gmap[i]] = sum_j Ainv[i][j] b[gmap[j]].
