@@ -220,6 +220,8 @@ class Hierarchy:
         x = np.zeros_like(b)
         r0 = np.linalg.norm(b)
         hist = [r0]
+        if r0 == 0.0:                       # u = 0 solves it: no cycle
+            return x, 0, np.array(hist), True
         for it in range(1, maxit + 1):
             x = self.vcycle(b, None if it == 1 else x)
             r = b - self._apply(0, x)
@@ -234,6 +236,8 @@ class Hierarchy:
         r = b.copy()
         r0 = np.linalg.norm(r)
         hist = [r0]
+        if r0 == 0.0:
+            return u, 0, np.array(hist), True
         z = self.vcycle(r)
         p = z.copy()
         rho = z @ r
@@ -289,6 +293,8 @@ def solve_pcg_low_order(disc: Discretization, b, rtol=1e-8, maxit=1000):
     r = b.copy()
     r0 = np.linalg.norm(r)
     hist = [r0]
+    if r0 == 0.0:
+        return u, 0, np.array(hist), True
     z = lu.solve(r)
     p = z.copy()
     rho = z @ r

@@ -295,3 +295,31 @@ def test_low_order_pcg_counts_follow_table1(p):
     b = d.rhs(synth.nodal_field(7, d.N))
     _, it, _, ok = multigrid.solve_pcg_low_order(d, b)
     assert ok and abs(it - gold) <= 1, (p, it, gold)
+
+
+def test_solvers_return_zero_for_a_zero_right_hand_side():
+    """b = 0: every solver returns u = 0 after no iteration (the GPU solvers do the same)."""
+    prob = synth.problem(2, 4, 2, hier="h", n_hlevels=2, smoother="jacobi")
+    H = multigrid.Hierarchy(prob)
+    b = np.zeros(H.fine.A.shape[0])
+    for solve in (H.solve_mg, H.solve_pcg):
+        u, it, hist, ok = solve(b)
+        assert ok and it == 0 and not np.any(u)
+    u, it, _, ok = multigrid.solve_pcg_low_order(H.fine.disc, b)
+    assert ok and it == 0 and not np.any(u)
+
+
+def test_low_order_pcg_on_a_warped_variable_coefficient_3d_mesh():
+    """3D warped mesh, mu contrast 1e3: CG with the factored low-order preconditioner converges
+    to 1e-8, its true residual meets the tolerance, and it needs fewer iterations than CG with
+    the diagonal (Jacobi) preconditioner."""
+    d = fem.Discretization(3, 3, 3, warp_amp=0.1, mu_b=1e3)
+    b = d.rhs(synth.nodal_field(9, d.N))
+    u, it, _, ok = multigrid.solve_pcg_low_order(d, b)
+    A = d.stiffness()
+    assert ok and np.linalg.norm(b - A @ u) <= 1.0001e-8 * np.linalg.norm(b)
+    import scipy.sparse.linalg as spla
+    count = []
+    spla.cg(A, b, rtol=1e-8, maxiter=5000, M=spla.LinearOperator(A.shape, lambda r: r / A.diagonal()),
+            callback=lambda xk: count.append(1))
+    assert it < len(count)
