@@ -89,3 +89,29 @@ def test_workload_builders_for_the_paper_studies():
         assert lo["order"] == 1 and list(lo["nelem"]) == [e * prob["order"] for e in prob["nelem"]]
         assert lo["n_hlevels"] == levels, (prob["nelem"], prob["order"], lo["n_hlevels"])
         assert lo["node_xyz"].shape == (prob["dim"], N)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hmg.h is a C header: a C99 translation unit that uses every enum and the
+    descriptor compiles with -pedantic -Werror (no C++ types cross the boundary)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use_hmg.c"
+    src.write_text(
+        '#include "hmg.h"\n'
+        "int main(void) {\n"
+        "  hmg_desc d;\n"
+        "  hmg_problem* p = 0;\n"
+        "  (void)d; (void)p;\n"
+        "  return (int)HMG_OK + (int)HMG_HIER_P + (int)HMG_SMOOTH_BLOCKJACOBI + (int)HMG_MODE_PCG +\n"
+        "         (int)HMG_PREC_BF16 - 7;\n"
+        "}\n")
+    r = subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I",
+                        os.path.join(root, "include"), "-c", str(src), "-o", str(tmp_path / "use_hmg.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
