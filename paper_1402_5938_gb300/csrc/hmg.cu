@@ -755,15 +755,20 @@ hmg_status build_coarse(ProblemImpl& P, Level& l, cudaStream_t s) {
   TRY(P.alloc((void**)&l.gmap, nI * sizeof(long long)));
   TRY(cudaMemcpyAsync(l.gmap, gm.data(), nI * sizeof(long long), cudaMemcpyHostToDevice, s));
   TRY(launch_elem_dense(l.m, l.basis, l.G, l.Ainv, nI, s));
-  double *rowk = nullptr, *colk = nullptr;
-  TRY(dev_alloc((void**)&rowk, nI * sizeof(double), s));
-  if (dev_alloc((void**)&colk, nI * sizeof(double), s) != cudaSuccess) { dev_free(rowk, s); set_error("alloc"); return HMG_ENOMEM; }
-  cudaError_t e = gauss_jordan_inverse(l.Ainv, nI, rowk, colk, s);
-  dev_free(rowk, s);
-  dev_free(colk, s);
+  double* work = nullptr;
+  int* bad = nullptr;
+  TRY(dev_alloc((void**)&work, blocked_gj_work_doubles(nI) * sizeof(double), s));
+  if (dev_alloc((void**)&bad, sizeof(int), s) != cudaSuccess) { dev_free(work, s); set_error("alloc"); return HMG_ENOMEM; }
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = blocked_gauss_jordan_inverse(l.Ainv, nI, work, bad, s);
+  int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
+  dev_free(work, s);
+  dev_free(bad, s);
   TRY(e);
   TRY(e2);
+  if (hbad) { set_error("coarsest operator: a non-positive pivot (not positive definite)"); return HMG_EINVAL; }
   return HMG_OK;
 }
 
@@ -1284,7 +1289,8 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   const size_t nq0 = (size_t)(ms[0].nelem * np_of(ms[0]));
   if (D.node_xyz) { custom += (size_t)D.dim * N0 * 8; res += (size_t)D.dim * N0 * 8 + 512; }
   if (D.mu_fn) custom += (size_t)(D.dim + 1) * nq0 * 8;
-  const size_t temp = std::max(max_stage + 16 + custom + blk_temp, std::max(arnoldi, (size_t)nI * 16));
+  const size_t temp = std::max(max_stage + 16 + custom + blk_temp,
+                               std::max(arnoldi, blocked_gj_work_doubles(nI) * 8 + 1024));
   if (resident) *resident = res;
   if (peak) *peak = res + temp;
   return HMG_OK;

@@ -2,10 +2,13 @@
 // that every reduction sums its terms in the same order on every call (deterministic).
 #include <math.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "tma.cuh"
 #include "vector.cuh"
+#include "ops.cuh"
 
 namespace hmg {
 
@@ -379,30 +382,6 @@ __global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, long long 
   }
 }
 
-__global__ void k_gj_copy(const double* __restrict__ A, long long n, long long k, double* __restrict__ rowk,
-                          double* __restrict__ colk) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    rowk[i] = A[k * n + i];
-    colk[i] = A[i * n + k];
-  }
-}
-
-__global__ void k_gj_update(double* __restrict__ A, long long n, long long k, const double* __restrict__ rowk,
-                            const double* __restrict__ colk) {
-  const double piv = rowk[k];
-  const double ipiv = 1.0 / piv;
-  const long long tot = n * n;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const long long i = t / n, j = t - i * n;
-    double v;
-    if (i == k && j == k) v = ipiv;
-    else if (i == k) v = rowk[j] * ipiv;
-    else if (j == k) v = -colk[i] * ipiv;
-    else v = A[t] - colk[i] * rowk[j] * ipiv;
-    A[t] = v;
-  }
-}
-
 // one warp per output row
 template <typename T>
 __global__ void k_coarse_gemv(const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x,
@@ -592,15 +571,87 @@ template cudaError_t axis_pass<double>(const double*, double*, const long long*,
 template cudaError_t axis_pass<float>(const float*, float*, const long long*, int, const Axis1D&, int, int, int,
                                       cudaStream_t);
 
-cudaError_t gauss_jordan_inverse(double* A, long long n, double* rowk, double* colk, cudaStream_t s) {
-  const long long tot = n * n;
-  long long g = (tot + kThreads - 1) / kThreads;
-  if (g > 152LL * 16) g = 152LL * 16;
-  for (long long k = 0; k < n; ++k) {
-    k_gj_copy<<<grid_for(n), kThreads, 0, s>>>(A, n, k, rowk, colk);
-    k_gj_update<<<(unsigned)g, kThreads, 0, s>>>(A, n, k, rowk, colk);
+namespace {
+// C (ldc) = beta C + alpha A B for an M x N block of C, A: M x K (lda), B: K x N (ldb), K <= 32:
+// one 64 x 64 tile of C per thread block, the tile's A rows and B columns staged in shared
+// memory (zero outside the matrices), 4 x 4 outputs per thread; every global access is
+// bounds-checked against M, N and K.
+constexpr int kGemmK = 32;
+__global__ void __launch_bounds__(256)
+k_dgemm_k32(const int M, const int N, const int K, const double alpha, const double* __restrict__ A,
+            const long long lda, const double* __restrict__ B, const long long ldb, const double beta,
+            double* __restrict__ C, const long long ldc) {
+  __shared__ double As[64][kGemmK + 1];
+  __shared__ double Bs[kGemmK][64];
+  const long long i0 = (long long)blockIdx.y * 64, j0 = (long long)blockIdx.x * 64;
+  for (int idx = threadIdx.x; idx < 64 * K; idx += blockDim.x) {
+    const int r = idx / K, k = idx - r * K;
+    As[r][k] = (i0 + r < M) ? A[(i0 + r) * lda + k] : 0.0;
   }
-  return counted(cudaGetLastError(), 2 * n - 1);
+  for (int idx = threadIdx.x; idx < K * 64; idx += blockDim.x) {
+    const int k = idx >> 6, col = idx & 63;
+    Bs[k][col] = (j0 + col < N) ? B[k * ldb + j0 + col] : 0.0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  double acc[4][4] = {};
+  for (int k = 0; k < K; ++k) {
+    double a[4], b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a[q] = As[ty + 16 * q][k];
+      b[q] = Bs[k][tx + 16 * q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[q][w] = fma(a[q], b[w], acc[q][w]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const long long i = i0 + ty + 16 * q, j = j0 + tx + 16 * w;
+      if (i < M && j < N) {
+        double* o = C + i * ldc + j;
+        *o = (beta == 0.0 ? 0.0 : beta * *o) + alpha * acc[q][w];
+      }
+    }
+}
+
+cudaError_t dgemm_k32(int M, int N, int K, double alpha, const double* A, long long lda, const double* B,
+                      long long ldb, double beta, double* C, long long ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (K < 1 || K > kGemmK) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+  k_dgemm_k32<<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return counted(cudaGetLastError());
+}
+}  // namespace
+
+size_t blocked_gj_work_doubles(long long n) { return (size_t)(2 * kGemmK * n + kGemmK * kGemmK); }
+
+cudaError_t blocked_gauss_jordan_inverse(double* A, long long n, double* work, int* bad, cudaStream_t s) {
+  constexpr int NB = kGemmK;
+  double* R = work;                 // NB x n: the panel rows times the pivot block's inverse
+  double* Cb = R + (size_t)NB * n;  // n x NB: the panel columns
+  double* P = Cb + (size_t)n * NB;  // NB x NB: the pivot block, inverted in place
+  const size_t w = sizeof(double);
+  cudaError_t e = cudaSuccess;
+  for (long long k0 = 0; k0 < n && e == cudaSuccess; k0 += NB) {
+    const int b = (int)std::min<long long>(NB, n - k0);
+    e = cudaMemcpy2DAsync(P, b * w, A + k0 * n + k0, n * w, b * w, b, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = launch_block_invert(P, 1, b, bad, s);
+    if (e == cudaSuccess) e = dgemm_k32(b, (int)n, b, 1.0, P, b, A + k0 * n, n, 0.0, R, n, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(Cb, b * w, A + k0, n * w, b * w, n, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = dgemm_k32((int)n, (int)n, b, -1.0, Cb, b, R, n, 1.0, A, n, s);
+    if (e == cudaSuccess) e = dgemm_k32((int)n, b, b, -1.0, Cb, b, P, b, 0.0, A + k0, n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A + k0 * n, R, (size_t)b * n * w, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(A + k0 * n + k0, n * w, P, b * w, b * w, b, cudaMemcpyDeviceToDevice, s);
+  }
+  return e;
 }
 
 cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const long long* gmap, long long n,

@@ -97,7 +97,12 @@ cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, cons
 
 // Dense coarsest level: Gauss-Jordan inverse in place (SPD, no pivoting), and the solve
 // x[gmap[i]] = sum_j Ainv[i][j] b[gmap[j]].
-cudaError_t gauss_jordan_inverse(double* A, long long nI, double* rowk, double* colk, cudaStream_t s);
+// The inverse by 32-wide panels (block Gauss-Jordan: invert the pivot block, scale its rows,
+// rank-32 update of the rest by an FP64 GEMM, then the pivot columns and rows): n/32 panels of 7
+// operations instead of 2n launches. work: blocked_gj_work_doubles(n) doubles; *bad (device int)
+// is set when a pivot block has a non-positive pivot.
+size_t blocked_gj_work_doubles(long long n);
+cudaError_t blocked_gauss_jordan_inverse(double* A, long long n, double* work, int* bad, cudaStream_t s);
 cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const long long* gmap,
                          long long nI, cudaStream_t s);
 cudaError_t coarse_solve_f32(const double* Ainv, const float* b, float* x, const long long* gmap,
