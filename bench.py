@@ -1,15 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the matrix-free high-order multigrid solver (one JSON line on rank 0).
 
-Workload (one "step"): a full MG-preconditioned CG solve (Algorithm 1) to a 1e-8 relative
-residual of the 3D variable-coefficient problem on a 16^3 hex mesh of the unit cube warped
-by x_i += 0.1 prod_j sin(pi x_j), Q_4 (65^3 = 274,625 DOF incl. boundary nodes),
-mu = 1 + 1e3 sum_i cos^2(2 pi x_i), seeded f ~ U(-1,1) at the nodes, V(3,3) cycles with
-Chebyshev-Jacobi smoothing, FP64 throughout. The hierarchy (geometry, diagonal, Chebyshev
-bounds, coarsest inverse) is built once before timing and reported as setup_ms.
+Workload: the ~2M-DOF configuration of the order sweep at p = 4 -- a 32^3 hex mesh of the
+unit cube warped by x_i += 0.1 prod_j sin(pi x_j), Q_4 (129^3 = 2,146,689 DOF incl. boundary
+nodes), mu = 1 + 1e3 sum_i cos^2(2 pi x_i), seeded f ~ U(-1,1) at the nodes, p-multigrid
+(Q4 -> Q2 -> Q1, then two mesh halvings) V(3,3) Chebyshev-Jacobi as the PCG preconditioner,
+FP64 throughout. The hierarchy (geometry, diagonal, Chebyshev bounds, coarsest inverse) is
+built once before timing and reported as setup_ms.
 
-value = DOF solved per second (N / solve time), whole job over all ranks (replicas).
-The operator apply itself is timed separately for the roofline object.
+One step = one pass of the whole hot path: the finest-level operator apply y = A x timed on
+its own (CUDA events), then the PCG solve to a 1e-8 relative residual (gather/scatter, sum
+factorization, smoothers, transfers, coarsest solve, V-cycles inside Algorithm 1).
+value = GDOF/s of the order-p operator apply (N / apply time), whole job over all ranks
+(replicas); solve_ms = time to 1e-8 of the same step. e2e: the same apply through the host-
+buffer call hmg_apply_host (page-locked x in, y out, copies inside the timed region), and the
+solve through hmg_solve_host (nodal f in, u out). Further blocks: the same problem's FP32 /
+FP16 / BF16 V-cycles inside FP64 PCG, the order sweep at 129^3 nodes (p = 2, 8, 16), and the
+16^3 Q4 (274,625 DOF) single-solve configuration with its h- and p-hierarchies.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--hier p|h] [--impl reference]
 """
@@ -28,76 +35,83 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "GDOF/s of order-p operator apply; solve time to 1e-8; serve p50/p99 latency"
-WORKLOAD = "3D warped var-coef Q4 16^3 (65^3=274,625 DOF), mu=1+1e3*sum cos^2(2 pi x_i), PCG + V(3,3) Chebyshev(3) to 1e-8, FP64"
-# FP64 peak of one GB300: 152 SMs x 2.07 GHz x 4 FP64 flops/clock/SM (2 FMA lanes) = 1.259 TFLOP/s
-FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+WORKLOAD = ("3D warped var-coef Q4 32^3 (129^3=2,146,689 DOF), mu=1+1e3*sum cos^2(2 pi x_i), "
+            "p-MG PCG + V(3,3) Chebyshev(3) to 1e-8, FP64")
 L2_FLUSH_BYTES = 256 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_apply64<3,n> launch on this workload,
-# from the ncu capture summarized in profiles/apply64_fp64_q4_16cube.md (n = p + 1)
-APPLY_TRAFFIC = {5: 28.744704e6}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the headline's FP64 apply kernel, by
+# (kernel, elements): per launch, from the ncu capture named in "traffic_source"; None when the
+# kernel has changed since that capture
+APPLY_TRAFFIC = {}
+REF_ROWS_PER_STEP = 400
 
 
-def workload(hier):
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def workload(hier, nelem=32, order=4):
     import synth
-    return synth.warped_var3d(16, 4, hier=hier)
-
-
-def oracle_sample_problem(hier):
-    import synth
-    return synth.warped_var3d(8, 4, hier=hier)
+    return synth.warped_var3d(nelem, order, hier=hier)
 
 
 # ------------------------------------------------------------------ oracle arm (CPU)
 def run_reference(args):
-    """Time the FP64 CPU oracle (assembled sparse operators) on a bounded sample of the
-    same workload: 8^3 elements instead of 16^3, same order, coefficient, warp, cycle."""
+    """The FP64 CPU oracle on the same workload and metric: sampled rows of the order-p operator
+    apply y = A x by the oracle's weak form (Sec. 2.1, evaluated per row from the element
+    geometry and dense basis tables, no assembly: the assembled operator of 129^3 nodes does not
+    fit a bounded sample), REF_ROWS_PER_STEP rows per step, single-threaded."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     import numpy as np
 
     import synth
-    from oracle import multigrid
-    prob = oracle_sample_problem(args.hier)
+    from oracle import fem
+    prob = workload(args.hier)
     t0 = time.perf_counter()
-    H = multigrid.Hierarchy(prob)
-    d = H.fine.disc
-    b = d.rhs(synth.nodal_field(synth.SEED_WARPED_VAR3D, d.N))
+    d = fem.Discretization(3, prob["nelem"], prob["order"], warp_amp=prob["warp_amp"], mu_a=prob["mu_a"],
+                           mu_b=prob["mu_b"], mu_k=prob["mu_k"])
+    x = synth.uniform_pm1(7, d.N)
+    d.node_coords_cached()
     setup_s = time.perf_counter() - t0
-    times, its = [], []
+    rng = np.random.default_rng(12)
+    times = []
+    rows_per = args.ref_rows
     for k in range(args.warmup + args.steps):
+        rows = d.interior[rng.choice(d.n_interior, rows_per, replace=False)]
         t = time.perf_counter()
-        _, it, hist, ok = H.solve_pcg(b)
+        d.apply_rows(x, rows)
         dt = time.perf_counter() - t
         if k >= args.warmup:
             times.append(dt)
-            its.append(it)
     t_step = statistics.mean(times)
-    value = d.N / t_step / 1e9
-    threads = int(os.environ.get("OMP_NUM_THREADS", "0") or 0) or os.cpu_count()
+    value = rows_per / t_step / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "hier": args.hier},
-        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
-                         "sample": f"oracle PCG solve of the same warped var-coef Q4 problem on 8^3 elements "
-                                   f"({d.N} DOF) instead of 16^3; setup {setup_s:.1f}s excluded; "
-                                   f"{its[0]} iterations"},
+        "config": {"workload": WORKLOAD, "hier": args.hier, "dof": d.N},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": 1, "nproc": os.cpu_count(), "kind": "oracle",
+                         "sample": f"oracle order-4 apply (weak form per row) on {rows_per} random interior rows "
+                                   f"per step of the same {d.N}-DOF problem, single thread; setup "
+                                   f"{setup_s:.1f}s excluded"},
         "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def cpu_baseline(hier):
-    """Oracle timed in a child process on the host (single-threaded BLAS), one step."""
+def cpu_baseline(hier, steps=10):
+    """The oracle arm in a child process on the host (single thread), steps x REF_ROWS_PER_STEP rows."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                RANK="0", WORLD_SIZE="1")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "2", "--warmup", "1", "--hier", hier],
-                       capture_output=True, text=True, env=env, timeout=600)
+                        "--steps", str(steps), "--warmup", "1", "--hier", hier],
+                       capture_output=True, text=True, env=env, timeout=900)
     for ln in r.stdout.splitlines()[::-1]:
         if ln.startswith("{"):
             return json.loads(ln)["cpu_baseline"]
@@ -203,6 +217,83 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU arm
+_PEAK = {}
+
+
+def fp64_peak():
+    """Measured FP64 FMA rate of this GPU in TFLOP/s (hmg_measure_peak), once per process."""
+    if "fp64" not in _PEAK:
+        from paper_1402_5938_gb300 import measure_peak
+        _PEAK["fp64"] = measure_peak("fp64")
+    return _PEAK["fp64"]
+
+
+def flop_per_elem(dim, n):
+    """Algorithmic flops of one element's sum-factorized apply (a3-a5): 24n^4 + 15n^3 in 3D."""
+    return (24 * n ** 4 + 15 * n ** 3) if dim == 3 else (16 * n ** 3 + 6 * n ** 2)
+
+
+def events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def timed_solves(P, b, u, flush, stream, reps, warm=2, mode="pcg"):
+    """Median ms of `reps` L2-flushed solves (after `warm` untimed ones), last status and iterations."""
+    import torch
+    for _ in range(warm):
+        P.solve(mode, b, u, rtol=1e-8, maxit=500)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = events(2)
+        e0.record(stream)
+        st, it, _ = P.solve(mode, b, u, rtol=1e-8, maxit=500)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), st, it
+
+
+def timed_apply(fn, flush, stream, reps):
+    """Median ms of `reps` L2-flushed calls of fn (one operator apply each)."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = events(2)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def mixed_block(prob, P64, b, flush, stream, t64_ms, reps=5):
+    """The same problem solved with the FP32, FP16 and BF16 V-cycles inside FP64 PCG: solve time,
+    iterations, the true FP64 residual of the mixed solution, and the V-cycle operator's apply."""
+    import torch
+    out = {}
+    N = b.numel()
+    for prec in ("fp32", "fp16", "bf16"):
+        Pm = __import__("paper_1402_5938_gb300").Problem(dict(prob, smooth_prec=prec))
+        um = torch.zeros_like(b)
+        t, st, it = timed_solves(Pm, b, um, flush, stream, reps)
+        rm = torch.zeros_like(b)
+        P64.apply(0, um, rm)
+        x32 = b.float()
+        y32 = torch.zeros_like(x32)
+        ta = timed_apply(lambda: Pm.apply_f32(0, x32, y32), flush, stream, 10)
+        out[prec] = {"solve_ms": t, "iterations": it, "status": st,
+                     "fp64_rel_residual": float(torch.linalg.norm(b - rm) / torch.linalg.norm(b)),
+                     "speedup_vs_fp64": t64_ms / t, "fine_apply_ms": ta, "fine_apply_gdofs": N / (ta * 1e-3) / 1e9,
+                     "fine_apply_variant": Pm.level_variants(0)[1]}
+        Pm.close()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -221,19 +312,23 @@ def run_gpu(args):
     import synth
     from paper_1402_5938_gb300 import Problem, launch_count
 
+    peak64 = fp64_peak()
     prob = workload(args.hier)
     if args.host_loop:  # same kernels launched one by one (for launch lists; graph nodes are not listed)
         prob = dict(prob, solve_graph=0)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     P = Problem(prob)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
     N = P.ndof(0)
-    f_host = torch.from_numpy(synth.nodal_field(synth.SEED_WARPED_VAR3D, N)).pin_memory()
+    f_host = torch.from_numpy(synth.nodal_field(synth.SEED_PSWEEP3D, N)).pin_memory()
     f = f_host.to(dev)
     b = torch.zeros(N, dtype=torch.float64, device=dev)
     u = torch.zeros_like(b)
     P.rhs(f, b)
+    x = torch.from_numpy(synth.uniform_pm1(7, N)).to(dev)
+    y = torch.zeros_like(x)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -244,143 +339,105 @@ def run_gpu(args):
 
     its = []
     for _ in range(args.warmup):
+        P.apply(0, x, y)
         st, it, hist = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
         its.append(it)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [events(3) for _ in range(args.steps)]
     a0 = P.fine_applies()
     barrier()
     l0 = launch_count()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
-            flush.zero_()                                   # L2 flush between timed solves
+            flush.zero_()                                   # L2 flush between timed steps
             ev[k][0].record(stream)
-            st, it, hist = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+            P.apply(0, x, y)                                # the order-p operator apply
             ev[k][1].record(stream)
+            st, it, hist = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
+            ev[k][2].record(stream)
             its.append(it)
         barrier()
     launches = launch_count() - l0
-    applies = (P.fine_applies() - a0) / args.steps
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    t_step, value = aggregate_ranks(sum(step_ms) / len(step_ms), N, world, dist, dev)
+    applies = (P.fine_applies() - a0) / args.steps - 1
+    apply_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1, _ in ev)
+    solve_ms = statistics.mean(e1.elapsed_time(e2) for _, e1, e2 in ev)
+    step_ms = statistics.mean(e0.elapsed_time(e2) for e0, _, e2 in ev)
+    t_apply, value = aggregate_ranks(apply_ms, N, world, dist, dev)
+    t_step, _ = aggregate_ranks(step_ms, N, world, dist, dev)
     rel_res = float(hist[-1] / hist[0])
 
-    # ---- end to end through the public API: pinned host f -> rhs -> solve -> host u
+    # ---- end to end through the host-buffer C ABI calls: page-locked x in, y out (apply) and
+    # nodal f in, u out (rhs + solve), every copy inside the timed region
+    x_host = x.cpu().pin_memory()
+    y_host = torch.empty(N, dtype=torch.float64).pin_memory()
     u_host = torch.empty(N, dtype=torch.float64).pin_memory()
-    e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    P.apply_host(0, x_host, y_host)
+    P.solve_host("pcg", f_host, u_host, rtol=1e-8, maxit=500)
     barrier()
-    e2e_ev[0].record(stream)
-    for k in range(args.steps):
-        f.copy_(f_host, non_blocking=True)
-        P.rhs(f, b)
-        P.solve("pcg", b, u, rtol=1e-8, maxit=500)
-        u_host.copy_(u, non_blocking=True)
-    e2e_ev[1].record(stream)
+    ta = time.perf_counter()
+    for _ in range(args.steps):
+        P.apply_host(0, x_host, y_host)
+    e2e_apply_ms = (time.perf_counter() - ta) * 1e3 / args.steps
+    ts = time.perf_counter()
+    for _ in range(args.steps):
+        st_h, it_h, _ = P.solve_host("pcg", f_host, u_host, rtol=1e-8, maxit=500)
+    e2e_solve_ms = (time.perf_counter() - ts) * 1e3 / args.steps
     barrier()
-    _, e2e_value = aggregate_ranks(e2e_ev[0].elapsed_time(e2e_ev[1]) / args.steps, N, world, dist, dev)
+    _, e2e_value = aggregate_ranks(e2e_apply_ms, N, world, dist, dev)
+    e2e_err = float((y_host.to(dev) - y).abs().max() / y.abs().max())
+    u_err = float((u_host.to(dev) - u).abs().max() / u.abs().max())
 
-    # ---- the same problem with the mixed-precision V-cycles inside FP64 PCG (context; the
-    # headline value above is plain FP64): median of 5 L2-flushed solves, true FP64 residual
-    mixed = {}
-    for prec in (() if args.host_loop else ("fp32", "fp16", "bf16")):  # not in launch-list runs
-        Pm = Problem(dict(prob, smooth_prec=prec))
-        um = torch.zeros_like(b)
-        for _ in range(2):
-            Pm.solve("pcg", b, um, rtol=1e-8, maxit=500)
-        ts = []
-        for _ in range(5):
-            flush.zero_()
-            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            m0.record(stream)
-            stm, itm, _ = Pm.solve("pcg", b, um, rtol=1e-8, maxit=500)
-            m1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(m0.elapsed_time(m1))
-        rm = torch.zeros_like(b)
-        P.apply(0, um, rm)
-        t_m = statistics.median(ts)
-        mixed[prec] = {"solve_ms": t_m, "iterations": itm, "status": stm,
-                       "fp64_rel_residual": float(torch.linalg.norm(b - rm) / torch.linalg.norm(b)),
-                       "speedup_vs_fp64": t_step / t_m}
-        Pm.close()
-
-    # ---- the same problem with the other hierarchy of the configuration (h-multigrid on three
-    # meshes vs p-multigrid), FP64, median of 5 L2-flushed solves (context for the headline)
-    other = {}
-    if not args.host_loop:
-        oh = "h" if args.hier == "p" else "p"
-        Po = Problem(dict(workload(oh)))
-        uo = torch.zeros_like(b)
-        for _ in range(2):
-            Po.solve("pcg", b, uo, rtol=1e-8, maxit=500)
-        ts = []
-        for _ in range(5):
-            flush.zero_()
-            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            m0.record(stream)
-            sto, ito, _ = Po.solve("pcg", b, uo, rtol=1e-8, maxit=500)
-            m1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(m0.elapsed_time(m1))
-        other = {"hier": oh, "solve_ms": statistics.median(ts), "iterations": ito, "status": sto,
-                 "levels": Po.nlevels()}
-        Po.close()
-
-    # ---- the dominant kernel: the FP64 order-p apply on the finest level, timed alone
-    x = torch.from_numpy(synth.uniform_pm1(7, N)).to(dev)
-    y = torch.zeros_like(x)
-    for _ in range(3):
-        P.apply(0, x, y)
-    reps = 50
-    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    ea.record(stream)
-    for _ in range(reps):
-        flush.zero_()
-        P.apply(0, x, y)
-    eb.record(stream)
-    barrier()
-    ef, eg = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ef.record(stream)
-    for _ in range(reps):
-        flush.zero_()
-    eg.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = (ea.elapsed_time(eb) - ef.elapsed_time(eg)) / reps
-    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    roof_ms = solve_roofline_ms(P, its[-1], hbm, FP64_PEAK_TFLOPS)
+    # ---- roofline of the dominant kernel: the FP64 order-p apply (FP64 pipe)
     (E3, p, _) = P.level_info(0)
     n = p + 1
     E = E3[0] * E3[1] * E3[2]
-    flops = E * (24 * n ** 4 + 15 * n ** 3)
+    v64 = P.level_variants(0)[0]
+    flops = E * flop_per_elem(3, n)
     achieved_tf = flops / (apply_ms * 1e-3) / 1e12
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    roof_ms = solve_roofline_ms(P, its[-1], hbm, peak64)
+    kern = f"k_apply64<3,{n},{v64}>"
+    traffic = APPLY_TRAFFIC.get((kern, E))
+
+    # ---- context blocks (not part of the timed steps)
+    mixed = {} if args.host_loop or args.quick else mixed_block(prob, P, b, flush, stream, solve_ms)
+    sweep = [] if args.host_loop or args.quick else sweep_block(flush, stream, peak64, orders=((64, 2), (16, 8), (8, 16)))
+    c2 = {} if args.host_loop or args.quick else c2_block(flush, stream)
 
     if rank == 0:
-        cpu = cpu_baseline(args.hier)
+        cpu = cpu_baseline(args.hier) if not args.quick else None
         line = {
             "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "hier": args.hier, "global_batch": world, "dof": N,
-                       "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed solves",
+                       "parallelism": f"replicas{world}",
+                       "l2": "flushed (256 MB write) before every timed step; the apply's 196.6 MB of FP64 "
+                             "geometric factors also exceed L2",
+                       "step": "hmg_apply on the finest level, then hmg_solve (PCG + p-MG) to 1e-8",
                        "solve_loop": "host" if args.host_loop else "graph"},
-            "solve_ms": t_step, "setup_ms": setup_ms, "iterations": its[-1], "final_rel_residual": rel_res,
-            "mixed_precision": mixed, "other_hierarchy": other,
+            "apply_ms": t_apply, "solve_ms": solve_ms, "setup_ms": setup_ms, "iterations": its[-1],
+            "final_rel_residual": rel_res,
             "fine_applies_per_solve": applies,
             # per PCG iteration: A p, then a V(3,3) whose pre-smoother starts from zero (2 applies),
             # the restricted residual (1) and the post-smoother (3)
-            "fine_applies_model": 7 * its[-1], "apply_gdofs": N / (apply_ms * 1e-3) / 1e9,
-            "apply_ms": apply_ms,
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": APPLY_TRAFFIC.get(n),
-                         "kernel": f"k_apply64<3,{n}>",
-                         "note": "FP64 pipe; peak = 152 SM x 2.07 GHz x 4 flop/clk (nominal); "
-                                 "algorithmic flops 24n^4+15n^3 per element"},
-            "solve_roofline": {"roofline_ms": roof_ms, "measured_ms": t_step, "frac": roof_ms / t_step,
+            "fine_applies_model": 7 * its[-1],
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": achieved_tf / peak64, "traffic": traffic, "kernel": kern,
+                         "units_per_launch": E, "flop_per_unit": flop_per_elem(3, n),
+                         "traffic_source": "ncu capture of this kernel on this workload (profiles/)" if traffic else None,
+                         "note": "FP64 pipe; peak = measured FP64 FMA rate of this GPU (hmg_measure_peak, "
+                                 "burst); algorithmic flops 24n^4+15n^3 per element; apply time = hmg_apply "
+                                 "(zeroing y + the apply kernel) with CUDA events in the timed steps"},
+            "solve_roofline": {"roofline_ms": roof_ms, "measured_ms": solve_ms, "frac": roof_ms / solve_ms,
                                "model": "every apply at max(flops/FP64 peak, bytes/HBM) + vector passes and "
                                         "coarsest GEMV at HBM (HBM peak from MEASURED_PEAKS.json)"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+            "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
+                    "call": "hmg_apply_host (page-locked x -> y)", "ms": e2e_apply_ms, "max_rel_diff_vs_device": e2e_err},
+            "e2e_solve": {"ms": e2e_solve_ms, "dof_per_s": N / (e2e_solve_ms * 1e-3), "status": st_h,
+                          "iterations": it_h, "call": "hmg_solve_host (page-locked nodal f -> u)",
+                          "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "max_rel_diff_vs_device": u_err},
+            "mixed_precision": mixed, "sweep_129cube": sweep, "single_solve_16cube_q4": c2,
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
@@ -391,83 +448,82 @@ def run_gpu(args):
     return 0
 
 
+def c2_block(flush, stream):
+    """The 16^3 Q4 warped var-coef problem (65^3 = 274,625 DOF, seed 2) with both of its
+    hierarchies, FP64 PCG to 1e-8 (median of 10 L2-flushed solves) and its fine apply."""
+    import torch
+
+    import synth
+    from paper_1402_5938_gb300 import Problem
+    out = {"workload": "3D warped var-coef Q4 16^3 (65^3=274,625 DOF), PCG + V(3,3) Chebyshev(3), FP64"}
+    for hier in ("p", "h"):
+        P = Problem(workload(hier, 16, 4))
+        N = P.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device="cuda")
+        P.rhs(torch.from_numpy(synth.nodal_field(synth.SEED_WARPED_VAR3D, N)).cuda(), b)
+        u = torch.zeros_like(b)
+        t, st, it = timed_solves(P, b, u, flush, stream, 10)
+        y = torch.zeros_like(b)
+        ta = timed_apply(lambda: P.apply(0, b, y), flush, stream, 20)
+        out[hier] = {"solve_ms": t, "iterations": it, "status": st, "levels": P.nlevels(), "apply_ms": ta,
+                     "apply_variant": P.level_variants(0)[0],
+                     "apply_frac_of_fp64_peak": 4096 * flop_per_elem(3, 5) / (ta * 1e-3) / 1e12 / fp64_peak()}
+        if hier == "p":
+            out["mixed_precision"] = mixed_block(workload(hier, 16, 4), P, b, flush, stream, t)
+        P.close()
+    return out
+
+
+def sweep_block(flush, stream, peak64, orders):
+    """Order sweep at 129^3 nodes, same warp and coefficient (seed 3): per order the FP64 apply
+    (fraction of the FP64 peak), FP64 PCG + p-MG to 1e-8, and the FP32 / FP16 / BF16 V-cycles."""
+    import torch
+
+    import synth
+    from paper_1402_5938_gb300 import Problem
+    out = []
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    for E, p in orders:
+        prob = synth.warped_var3d(E, p, hier="p")
+        P64 = Problem(prob)
+        N = P64.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device="cuda")
+        P64.rhs(torch.from_numpy(synth.nodal_field(synth.SEED_PSWEEP3D, N)).cuda(), b)
+        y = torch.zeros_like(b)
+        t64 = timed_apply(lambda: P64.apply(0, b, y), flush, stream, 10)
+        u64 = torch.zeros_like(b)
+        s64, st, it64 = timed_solves(P64, b, u64, flush, stream, 3)
+        n = p + 1
+        v64, _ = P64.level_variants(0)
+        row = {"mesh": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_variant": v64,
+               "pcg_fp64_ms": s64, "pcg_fp64_iters": it64, "pcg_fp64_status": st}
+        if v64 == 4:   # stored dense element matrices: 2 n^6 flops, 8 n^6 bytes per element
+            ex_flops, ex_bytes = E ** 3 * 2 * n ** 6, E ** 3 * 8 * n ** 6 + 16 * N
+            row.update({"apply_fp64_kernel": "dense element matrices",
+                        "apply_fp64_frac_of_fp64_peak": ex_flops / (t64 * 1e-3) / 1e12 / peak64,
+                        "apply_fp64_frac_of_hbm": ex_bytes / (t64 * 1e-3) / 1e9 / hbm})
+        else:
+            row.update({"apply_fp64_kernel": "sum factorization",
+                        "apply_fp64_frac_of_fp64_peak": E ** 3 * flop_per_elem(3, n) / (t64 * 1e-3) / 1e12 / peak64})
+        for prec, m in mixed_block(prob, P64, b, flush, stream, s64, reps=3).items():
+            row[prec] = m
+        out.append(row)
+        P64.close()
+    return out
+
+
 def run_sweep(args):
     """Order sweep at ~2M DOF (129^3 nodes; (64^3,2), (32^3,4), (16^3,8), (8^3,16)), same warp and
     coefficient: per order the FP64 apply time and the V-cycle operator's time in FP32, FP16 and
-    BF16 (tensor cores, orders <= 7), and FP64 vs mixed-precision PCG + p-MG time to 1e-8,
-    iterations, the mixed solution's FP64 residual and relative difference from the FP64 one.
-    One JSON line per order (not the benchmark line)."""
+    BF16, and FP64 vs mixed-precision PCG + p-MG time to 1e-8, iterations, the mixed solution's
+    FP64 residual. One JSON line per order (not the benchmark line)."""
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
-    import synth
-    from paper_1402_5938_gb300 import Problem
-    dev = torch.device("cuda", 0)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def timed(fn, reps):
-        ts = []
-        for _ in range(reps):
-            flush.zero_()
-            a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            out = fn()
-            b_.record()
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b_))
-        return statistics.median(ts), out
-
-    hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    for E, p in [(64, 2), (32, 4), (16, 8), (8, 16)]:
-        prob = synth.warped_var3d(E, p, hier="p")
-        P64 = Problem(prob)
-        N = P64.ndof(0)
-        f = torch.from_numpy(synth.nodal_field(synth.SEED_PSWEEP3D, N)).to(dev)
-        b = torch.zeros(N, dtype=torch.float64, device=dev)
-        P64.rhs(f, b)
-        y = torch.zeros_like(b)
-        t64, _ = timed(lambda: P64.apply(0, b, y), 10)
-        u64 = torch.zeros_like(b)
-        s64, (_, it64, h64) = timed(lambda: P64.solve("pcg", b, u64, rtol=1e-8, maxit=500), 3)
-        n = p + 1
-        flops = E ** 3 * (24 * n ** 4 + 15 * n ** 3)
-        v64, _ = P64.level_variants(0)
-        line = {"sweep": f"{E}^3 Q{p}", "dof": N, "apply_fp64_ms": t64, "apply_fp64_variant": v64,
-                "apply_fp64_tflops_algorithmic": flops / t64 / 1e9,
-                "pcg_fp64_ms": s64, "pcg_fp64_iters": it64, "setup_bytes_fp64": P64.device_bytes()}
-        if v64 == 4:
-            # stored dense element matrices: 2 n^6 flops and 8 n^6 bytes per element executed
-            # (fewer flops than the sum-factorized count above), so the roofline is its own
-            ex_flops, ex_bytes = E ** 3 * 2 * n ** 6, E ** 3 * 8 * n ** 6 + 16 * N
-            line.update({"apply_fp64_kernel": "dense element matrices",
-                         "apply_fp64_frac_of_fp64_peak": ex_flops / t64 / 1e9 / FP64_PEAK_TFLOPS,
-                         "apply_fp64_frac_of_hbm": ex_bytes / t64 / 1e6 / hbm_peak})
-        else:
-            line.update({"apply_fp64_kernel": "sum factorization",
-                         "apply_fp64_frac_of_fp64_peak": flops / t64 / 1e9 / FP64_PEAK_TFLOPS})
-        # V-cycle precisions: FP32, and FP16 / BF16 tensor-core applies (orders <= 7) with flexible PCG
-        for prec, gbytes in (("fp32", 4), ("fp16", 2), ("bf16", 2)):
-            Pm = Problem(dict(prob, smooth_prec=prec))
-            x32, y32 = torch.zeros(N, dtype=torch.float32, device=dev), torch.zeros(N, dtype=torch.float32, device=dev)
-            x32.copy_(b)
-            tm, _ = timed(lambda: Pm.apply_f32(0, x32, y32), 10)
-            um = torch.zeros_like(b)
-            sm, (stm, itm, hm) = timed(lambda: Pm.solve("pcg", b, um, rtol=1e-8, maxit=500), 3)
-            P64.apply(0, um, y)
-            res = float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
-            diff = float(torch.linalg.norm(um - u64) / torch.linalg.norm(u64))
-            fine_bytes = gbytes if (prec == "fp32" or p <= 7) else 4
-            line.update({
-                f"apply_{prec}_ms": tm, f"apply_{prec}_gdofs": N / tm / 1e6,
-                f"apply_{prec}_hbm_gbs": (E ** 3 * 6 * fine_bytes * n ** 3 + 8 * N) / tm / 1e6,
-                f"pcg_{prec}_ms": sm, f"pcg_{prec}_iters": itm, f"pcg_{prec}_status": stm,
-                f"{prec}_speedup_vs_fp64": s64 / sm, f"{prec}_final_rel_residual_fp64": res,
-                f"{prec}_vs_fp64_solution_rel_diff": diff, f"setup_bytes_{prec}": Pm.device_bytes()})
-            Pm.close()
-        print(json.dumps(line), flush=True)
-        P64.close()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for row in sweep_block(flush, torch.cuda.current_stream(), fp64_peak(), ((64, 2), (32, 4), (16, 8), (8, 16))):
+        print(json.dumps(dict(row, sweep=row["mesh"])), flush=True)
     return 0
 
 
@@ -796,7 +852,7 @@ def run_block_jacobi(args):
                 # the GEMV does 2 flops per 8-byte entry, above GB300's FP64 ridge (~0.19 flop/B):
                 # its roof is the FP64 pipe unless the bytes take longer
                 t_hbm = byts / (hbm * 1e9)
-                t_fp64 = flops / (FP64_PEAK_TFLOPS * 1e12)
+                t_fp64 = flops / (fp64_peak() * 1e12)
                 x = torch.zeros_like(b)
                 ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 ts = []
@@ -815,7 +871,7 @@ def run_block_jacobi(args):
                                      "frac": max(t_hbm, t_fp64) / (step_ms * 1e-3),
                                      "achieved_gbs": byts / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm,
                                      "achieved_tflops": flops / (step_ms * 1e-3) / 1e12,
-                                     "peak_tflops": FP64_PEAK_TFLOPS,
+                                     "peak_tflops": fp64_peak(),
                                      "kernels": "k_jacobi_first + k_block_smooth (zero guess, 1 step)"}
             P.close()
         print(json.dumps(out), flush=True)
@@ -962,6 +1018,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--quick", action="store_true", help="headline only (no context blocks, no CPU baseline)")
+    ap.add_argument("--ref-rows", type=int, default=REF_ROWS_PER_STEP,
+                    help="--impl reference: oracle rows of the apply per step")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--hier", choices=["h", "p"], default="p")
     ap.add_argument("--host-loop", action="store_true",

@@ -197,15 +197,23 @@ hmg_status hmg_restrict(hmg_problem* prob, int level, const double* rf_dev, doub
  * by its sizes: fine level nelem_fine[dim] elements of order_fine; the coarse level halves
  * the elements per axis (halve_mesh != 0, counts must be even) and/or has order_coarse <=
  * order_fine. rf_dev / rc_dev: caller-owned FP64 node vectors of the fine / coarse level
- * (lexicographic, x fastest, boundary entries ignored / written as zero).
+ * (lexicographic, x fastest, boundary entries ignored / written as zero); rf_dev must hold at
+ * least prod_a (nelem_fine[a] * order_fine + 1) doubles and rc_dev at least
+ * prod_a (Ec[a] * order_coarse + 1), Ec[a] = nelem_fine[a] / 2 when halving, else nelem_fine[a]
+ * (a < dim). The C ABI cannot check device buffer sizes: shorter buffers are read and written
+ * out of bounds.
  * Limits (fixed device storage held by every device that loads the library, ~18.5 MiB):
  * at most 4097 fine nodes per axis, and the two intermediate passes together at most
  * 2^21 doubles (16 MiB) -- e.g. a 129^3-node fine level; larger sizes return HMG_EINVAL.
- * The first call on a device looks up the device addresses of that storage; make it
- * before any stream capture. Every call reuses the same storage (stencils and
- * intermediates), so calls that overlap on the GPU (different streams, or without
- * ordering between them) race; calls on one stream are ordered. The stencils are copied
- * from pageable host memory, which synchronizes `stream` before the copy starts. */
+ * That storage is reserved when the CUDA module of the library is loaded on a device; with
+ * lazy module loading (the CUDA default) that may happen during this entry point's first
+ * call on the device, which also looks up the storage's device addresses. A caller that may
+ * not allocate at all makes one warm-up call (or sets CUDA_MODULE_LOADING=EAGER) before it
+ * enters its allocation-free region. Every call copies the 1D stencils from pageable host
+ * memory, which synchronizes `stream` before each copy starts; no call can therefore be
+ * recorded into a CUDA graph by stream capture. Every call reuses the same storage (stencils
+ * and intermediates), so calls that overlap on the GPU (different streams, or without
+ * ordering between them) race; calls on one stream are ordered. */
 hmg_status hmg_restrict_noalloc(int dim, const int nelem_fine[3], int order_fine, int order_coarse,
                                 int halve_mesh, const double* rf_dev, double* rc_dev, void* stream);
 
@@ -224,6 +232,20 @@ hmg_status hmg_vcycle(hmg_problem* prob, const double* r_dev, double* z_dev, voi
  * maxit is reached, HMG_ENAN on a non-finite residual. Synchronizes `stream`. */
 hmg_status hmg_solve(hmg_problem* prob, int mode, const double* b_dev, double* u_dev, double rtol,
                      int maxit, int* iters, double* res_hist, void* stream);
+
+/* Host-buffer forms of hmg_apply and of hmg_rhs + hmg_solve, for callers whose data lives in host
+ * memory: the call copies its input into library-owned device staging (two finest-level FP64
+ * vectors, allocated from the stream-ordered pool on the first host-buffer call of a handle and
+ * held until hmg_destroy), runs the device path on `stream`, copies the result back and
+ * synchronizes `stream`. Page-locked host buffers give full copy bandwidth; pageable ones work.
+ * hmg_apply_host: y_host = A_k x_host on level k (hmg_ndof(prob, k) doubles each; Sec. 2.1, 2.3).
+ * hmg_solve_host: f_host is the nodal right-hand side f (hmg_ndof(prob, 0) doubles); the load
+ * vector b = M f (Sec. 2.1) is formed on the device and A u = b solved as by hmg_solve (Sec. 4.3,
+ * Algorithm 1; same mode, rtol, maxit, iters, res_hist and statuses); u_host receives u, also
+ * when the status is HMG_ENOCONV or HMG_ENAN. */
+hmg_status hmg_apply_host(hmg_problem* prob, int level, const double* x_host, double* y_host, void* stream);
+hmg_status hmg_solve_host(hmg_problem* prob, int mode, const double* f_host, double* u_host, double rtol,
+                          int maxit, int* iters, double* res_hist, void* stream);
 
 /* PCG on prob's finest operator A_p (Algorithm 1's loop, from u = 0, to ||r|| <= rtol ||b||)
  * preconditioned by the low-order operator on the same nodes (Sec. 3.1.3; Sec. 4.2's
@@ -285,6 +307,13 @@ hmg_status hmg_server_destroy(hmg_server* srv);
 
 const char* hmg_status_string(hmg_status s);
 const char* hmg_last_error(void);
+
+/* Measured arithmetic peak of the current device in TFLOP/s, the denominator of the operator's
+ * FP64 roofline (no counterpart in the paper): what = 0 FP64 fused multiply-add on the CUDA cores,
+ * 1 FP32 fused multiply-add, 2 FP64 tensor-core MMA (m8n8k4). Independent FMA (MMA) chains in
+ * every thread of 8 blocks of 256 threads per SM, best of three timed launches (CUDA events,
+ * legacy default stream, synchronized) after a warm-up launch; tens of milliseconds per call. */
+hmg_status hmg_measure_peak(int what, double* tflops);
 
 /* Failure-detection self test: one device thread waits, with at most `polls` polls, on an
  * mbarrier that nothing completes (no copy in flight) -- the bounded wait every TMA-staged kernel

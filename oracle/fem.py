@@ -248,6 +248,29 @@ class Discretization:
         """A_ii = a(phi_i, phi_i) for selected global nodes (the weak form with u_h = phi_i)."""
         return self._weak_rows(rows, None)
 
+    def mass_rows(self, f_full, rows):
+        """(M f)_i = (f_h, phi_i) for selected global nodes i (Sec. 2.1's load vector f_k), f_h the
+        nodal interpolant of f over all N nodes: sum over the elements e containing node i of
+        sum_qp W |det J| f_h(x_qp) phi_i(x_qp), with f_h and phi_i from the dense basis table
+        (no assembly). Boundary rows return zero, as the interior load vector has none."""
+        f_full = np.asarray(f_full, dtype=np.float64)
+        out = np.zeros(len(rows))
+        Phi, dPhi, W = tables = self.basis_tables()
+        cache = {}
+        for r_i, g in enumerate(rows):
+            if self.boundary[g]:
+                continue
+            for e in self._elements_of_node(g):
+                e = int(e)
+                if e not in cache:
+                    _, _, detJ = self.element_geometry([e], tables)
+                    gl = self.element_nodes([e])[0]
+                    cache[e] = (W * np.abs(detJ[0]), gl, Phi @ f_full[gl])
+                c, gl, fq = cache[e]
+                a = int(np.flatnonzero(gl == g)[0])
+                out[r_i] += np.sum(c * fq * Phi[:, a])
+        return out
+
     def _elements_of_node(self, g):
         p, d = self.p, self.dim
         I = [self.node_axis_index[ax][g] for ax in range(d)]

@@ -156,7 +156,7 @@ long long packed_block_doubles(long long nelem, int MI) { return nelem * ((MI + 
 cudaError_t launch_block_pack(const double* Kb, double* Kp, long long nelem, int MI, cudaStream_t s) {
   if (MI <= 0 || nelem <= 0) return cudaSuccess;
   long long g = (packed_block_doubles(nelem, MI) + 255) / 256;
-  if (g > 152LL * 32) g = 152LL * 32;
+  if (g > (long long)device_sm_count() * 32) g = (long long)device_sm_count() * 32;
   k_block_pack<<<(unsigned)g, 256, 0, s>>>(Kb, Kp, nelem, MI);
   return counted(cudaGetLastError());
 }
@@ -178,7 +178,7 @@ cudaError_t launch_block_smooth(const Mesh& m, const double* Kp, const double* s
 cudaError_t launch_mask_elem_interior(double* dinv, const Mesh& m, cudaStream_t s) {
   if (m.p < 2) return cudaSuccess;
   long long g = (m.N + 255) / 256;
-  if (g > 152LL * 16) g = 152LL * 16;
+  if (g > (long long)device_sm_count() * 16) g = (long long)device_sm_count() * 16;
   k_mask_elem_interior<<<(unsigned)g, 256, 0, s>>>(dinv, m);
   return counted(cudaGetLastError());
 }

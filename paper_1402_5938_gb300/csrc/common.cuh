@@ -64,6 +64,9 @@ double hessenberg_max_real_eig(const double* H, int m);
 
 void set_error(const std::string& msg);
 
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sm_count();
+
 // Number of kernels this library has launched (all threads); read by hmg_launch_count().
 long long add_launches(long long n);
 cudaError_t ensure_smem_ptr(const void* kernel, size_t bytes);

@@ -38,6 +38,18 @@ std::atomic<long long> g_launches{0};
 }
 long long add_launches(long long n) { return g_launches.fetch_add(n) + n; }
 
+int device_sm_count() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = cached[dev].load();
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+    cached[dev].store(n);
+  }
+  return n;
+}
+
 namespace {
 std::mutex g_smem_mu;
 std::set<std::pair<const void*, int>> g_smem_done;
@@ -119,6 +131,7 @@ struct ProblemImpl {
   void* t1 = nullptr;         // transfer intermediates
   void* t2 = nullptr;
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *ph = nullptr;
+  double *hx = nullptr, *hy = nullptr;  // finest-level staging of the host-buffer entry points
   std::vector<void*> dev_allocs;
   size_t bytes = 0;
   long long fine_applies = 0;
@@ -1568,6 +1581,47 @@ hmg_status hmg_solve_low_order(hmg_problem* p, hmg_problem* low, const double* b
     hmg_status de = device_error(p->impl, (cudaStream_t)stream);
     if (de != HMG_OK) return de;
   }
+  return st;
+}
+
+// Two finest-level FP64 vectors for hmg_apply_host / hmg_solve_host, allocated from the stream-ordered
+// pool on the first such call and held until hmg_destroy.
+static hmg_status host_staging(ProblemImpl& P, cudaStream_t s) {
+  if (P.hx) return HMG_OK;
+  const size_t nb = (size_t)P.L[0].m.N * sizeof(double);
+  TRY(dev_alloc((void**)&P.hx, nb, s));
+  P.dev_allocs.push_back(P.hx);
+  TRY(dev_alloc((void**)&P.hy, nb, s));
+  P.dev_allocs.push_back(P.hy);
+  return HMG_OK;
+}
+
+hmg_status hmg_apply_host(hmg_problem* p, int level, const double* x_host, double* y_host, void* stream) {
+  if (!level_ok(p, level) || !x_host || !y_host) { set_error("null argument"); return HMG_EINVAL; }
+  ProblemImpl& P = p->impl;
+  cudaStream_t s = (cudaStream_t)stream;
+  CHECK(host_staging(P, s));
+  const size_t nb = (size_t)P.L[level].m.N * sizeof(double);
+  TRY(cudaMemcpyAsync(P.hx, x_host, nb, cudaMemcpyHostToDevice, s));
+  TRY(cudaMemsetAsync(P.hy, 0, nb, s));
+  CHECK(apply_level(P, level, P.hx, P.hy, 1.0, s));
+  TRY(cudaMemcpyAsync(y_host, P.hy, nb, cudaMemcpyDeviceToHost, s));
+  return device_error(P, s);  // synchronizes s
+}
+
+hmg_status hmg_solve_host(hmg_problem* p, int mode, const double* f_host, double* u_host, double rtol, int maxit,
+                          int* iters, double* res_hist, void* stream) {
+  if (!level_ok(p, 0) || !f_host || !u_host) { set_error("null argument"); return HMG_EINVAL; }
+  ProblemImpl& P = p->impl;
+  cudaStream_t s = (cudaStream_t)stream;
+  CHECK(host_staging(P, s));
+  const size_t nb = (size_t)P.L[0].m.N * sizeof(double);
+  TRY(cudaMemcpyAsync(P.hx, f_host, nb, cudaMemcpyHostToDevice, s));
+  CHECK(hmg_rhs(p, P.hx, P.hy, stream));                 // b = M f into hy
+  const hmg_status st = hmg_solve(p, mode, P.hy, P.hx, rtol, maxit, iters, res_hist, stream);
+  if (st != HMG_OK && st != HMG_ENOCONV && st != HMG_ENAN) return st;
+  TRY(cudaMemcpyAsync(u_host, P.hx, nb, cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
   return st;
 }
 

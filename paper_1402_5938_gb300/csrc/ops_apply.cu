@@ -11,19 +11,6 @@ namespace hmg {
 
 namespace {
 
-int sm_count() {
-  static int cached[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 152;
-  if (!cached[dev]) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    cached[dev] = n;
-  }
-  return cached[dev];
-}
-
 // resident blocks per SM of (kernel, dynamic shared memory), queried once
 int blocks_per_sm(const void* kernel, int threads, size_t smem) {
   static std::mutex mu;
@@ -56,7 +43,7 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
         const long long ngroups = (m.nelem + W::EW - 1) / W::EW;
         if (ngroups == 0) return cudaSuccess;
         const long long grid = std::min<long long>((ngroups + wpb - 1) / wpb,
-                                                   (long long)sm_count() * blocks_per_sm((const void*)kw, 32 * wpb, smem));
+                                                   (long long)device_sm_count() * blocks_per_sm((const void*)kw, 32 * wpb, smem));
         kw<<<(unsigned)grid, 32 * wpb, smem, s>>>(x, y, G, m, make_tab<N, float>(b), alpha, ngroups);
         return counted(cudaGetLastError());
       }
@@ -68,7 +55,7 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
     // variant 0: ~64 KB of shared memory per block; 1: half the tile; 2: double the tile
     const size_t target = variant == 1 ? 32 * 1024 : (variant == 2 ? 128 * 1024 : 64 * 1024);
     int epb = (int)std::max<size_t>(1, target / per);
-    const long long want = std::max(1LL, m.nelem / (2LL * sm_count()));
+    const long long want = std::max(1LL, m.nelem / (2LL * device_sm_count()));
     if (epb > want) epb = (int)want;
     if (epb > 64) epb = 64;
     const size_t smem = C::smem(epb);
@@ -83,7 +70,7 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
     const int lines = epb * NL;
     const int threads = lines >= 160 ? std::min(512, (lines + 31) / 32 * 32) : 256;
     const long long grid =
-        std::min<long long>(ntiles, (long long)sm_count() * blocks_per_sm((const void*)kern, threads, smem));
+        std::min<long long>(ntiles, (long long)device_sm_count() * blocks_per_sm((const void*)kern, threads, smem));
     kern<<<(unsigned)grid, threads, smem, s>>>(x, y, G, m, make_tab<N, float>(b), alpha, epb, ntiles, err);
     return counted(cudaGetLastError());
   });

@@ -13,19 +13,6 @@ namespace hmg {
 
 namespace {
 
-int sm_count16() {
-  static int cached[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 152;
-  if (!cached[dev]) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    cached[dev] = n;
-  }
-  return cached[dev];
-}
-
 int resident16(const void* kernel, int threads, size_t smem) {
   static std::mutex mu;
   static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
@@ -62,7 +49,7 @@ cudaError_t apply16_launch(const Mesh& m, const Basis1D& b, const float* x, floa
   if (ngroups == 0) return cudaSuccess;
   const long long blocks = (ngroups + wpb - 1) / wpb;
   const long long grid =
-      std::min<long long>(blocks, (long long)sm_count16() * resident16((const void*)kern, 32 * wpb, smem));
+      std::min<long long>(blocks, (long long)device_sm_count() * resident16((const void*)kern, 32 * wpb, smem));
   kern<<<(unsigned)grid, 32 * wpb, smem, s>>>(x, y, static_cast<const T*>(G16), gsc, m, make_tab16(b), alpha,
                                               ngroups, err);
   return counted(cudaGetLastError());

@@ -49,7 +49,7 @@ cudaError_t apply_dense64_dim(const Mesh& m, const Basis1D& b, const double* x, 
       constexpr int EPB = 256 / Sh<DIM, N>::NP;
       const long long groups = (m.nelem + EPB - 1) / EPB;
       if (groups == 0) return cudaSuccess;
-      const unsigned grid = (unsigned)std::min<long long>(groups, 152LL * 8);
+      const unsigned grid = (unsigned)std::min<long long>(groups, (long long)device_sm_count() * 8);
       k_apply_dense64<DIM, N><<<grid, 256, 0, s>>>(x, y, Ke, m, alpha);
       return counted(cudaGetLastError());
     }

@@ -32,7 +32,7 @@ cudaError_t geom_point_dim(const Mesh& m, const Basis1D& b, double mu_a, double 
     constexpr int N = decltype(nc)::value;
     constexpr int NP = Sh<DIM, N>::NP;
     const long long tot = m.nelem * NP;
-    const unsigned g2 = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 64);
+    const unsigned g2 = (unsigned)std::min<long long>((tot + 255) / 256, (long long)device_sm_count() * 64);
     k_geom_point<DIM, N><<<g2, 256, 0, s>>>(Js, G, wdetJ, m, mu_a, mu_b, mu_k, mu_arr, make_geotab<N>(b), bad);
     return counted(cudaGetLastError());
   });
@@ -43,7 +43,7 @@ cudaError_t extract_xq_dim(const Mesh& m, const Basis1D& b, const double* Js, do
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
     const long long tot = m.nelem * Sh<DIM, N>::NP;
-    const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, 152LL * 64);
+    const unsigned g = (unsigned)std::min<long long>((tot + 255) / 256, (long long)device_sm_count() * 64);
     k_extract_xq<DIM, N><<<g, 256, 0, s>>>(Js, xq, m);
     return counted(cudaGetLastError());
   });
@@ -125,7 +125,7 @@ cudaError_t launch_level_coords(const Mesh& m0, const Basis1D& b0, const double*
   MapNodes nodes{};
   for (int i = 0; i < b0.n; ++i) nodes.r0[i] = b0.r[i];
   for (int i = 0; i < bk.n; ++i) nodes.rk[i] = bk.r[i];
-  const unsigned g = (unsigned)std::min<long long>((mk.N + 255) / 256, 152LL * 64);
+  const unsigned g = (unsigned)std::min<long long>((mk.N + 255) / 256, (long long)device_sm_count() * 64);
   if (mk.N == 0) return cudaSuccess;
   if (m0.dim == 3)
     k_level_coords<3><<<g, 256, 0, s>>>(X0, m0, mk, nodes, Xk);

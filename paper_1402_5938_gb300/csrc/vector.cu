@@ -18,7 +18,7 @@ constexpr int kThreads = 256;
 
 inline unsigned grid_for(long long n) {
   long long g = (n + kThreads - 1) / kThreads;
-  if (g > 152LL * 16) g = 152LL * 16;
+  if (g > (long long)device_sm_count() * 16) g = (long long)device_sm_count() * 16;
   if (g < 1) g = 1;
   return (unsigned)g;
 }
@@ -657,14 +657,14 @@ cudaError_t blocked_gauss_jordan_inverse(double* A, long long n, double* work, i
 cudaError_t coarse_solve(const double* Ainv, const double* b, double* x, const long long* gmap, long long n,
                          cudaStream_t s) {
   long long g = (n + 7) / 8;
-  if (g > 152LL * 16) g = 152LL * 16;
+  if (g > (long long)device_sm_count() * 16) g = (long long)device_sm_count() * 16;
   k_coarse_gemv<double><<<(unsigned)g, kThreads, 0, s>>>(Ainv, b, x, gmap, n);
   return counted(cudaGetLastError());
 }
 cudaError_t coarse_solve_f32(const double* Ainv, const float* b, float* x, const long long* gmap, long long n,
                              cudaStream_t s) {
   long long g = (n + 7) / 8;
-  if (g > 152LL * 16) g = 152LL * 16;
+  if (g > (long long)device_sm_count() * 16) g = (long long)device_sm_count() * 16;
   k_coarse_gemv<float><<<(unsigned)g, kThreads, 0, s>>>(Ainv, b, x, gmap, n);
   return counted(cudaGetLastError());
 }

@@ -72,6 +72,10 @@ _SIGS = {
     "hmg_solve": (_I, [_P, _I, _V, _V, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _V]),
     "hmg_solve_low_order": (_I, [_P, _P, _V, _V, _D, _I, _D, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong),
                                  ctypes.POINTER(_D), _V]),
+    "hmg_apply_host": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _V]),
+    "hmg_solve_host": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_I),
+                            ctypes.POINTER(_D), _V]),
+    "hmg_measure_peak": (_I, [_I, ctypes.POINTER(_D)]),
     "hmg_restrict_noalloc": (_I, [_I, ctypes.POINTER(ctypes.c_int), _I, _I, _I, _V, _V, _V]),
     "hmg_solve_batched": (_I, [ctypes.POINTER(_P), _I, _I, ctypes.POINTER(_V), ctypes.POINTER(_V), _D, _I,
                                ctypes.POINTER(_I), ctypes.POINTER(ctypes.POINTER(_D)), ctypes.POINTER(_I), _V]),
@@ -131,6 +135,29 @@ def _ptr(t, n=None, dtype=None):
     if n is not None and t.numel() < n:
         raise ValueError(f"tensor has {t.numel()} entries, the level needs {n}")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, n):
+    """Pointer to n contiguous float64 host values (numpy array or CPU tensor)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("expected a contiguous float64 numpy array")
+        if a.size < n:
+            raise ValueError(f"array has {a.size} entries, the level needs {n}")
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    import torch
+    if not (isinstance(a, torch.Tensor) and not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+        raise TypeError("expected a contiguous float64 host array or CPU tensor")
+    if a.numel() < n:
+        raise ValueError(f"tensor has {a.numel()} entries, the level needs {n}")
+    return ctypes.cast(ctypes.c_void_p(a.data_ptr()), ctypes.POINTER(ctypes.c_double))
+
+
+def measure_peak(what):
+    """hmg_measure_peak: measured TFLOP/s of 'fp64' FMA, 'fp32' FMA or 'fp64_mma' on the current device."""
+    v = ctypes.c_double()
+    _check(lib().hmg_measure_peak({"fp64": 0, "fp32": 1, "fp64_mma": 2}[what], ctypes.byref(v)))
+    return v.value
 
 
 def make_desc(prob: dict) -> Desc:
@@ -276,6 +303,23 @@ class Problem:
         return st, it.value, np.array(hist[: it.value + 1])
 
 
+    def apply_host(self, level, x_host, y_host, stream=None):
+        """hmg_apply_host: y_host = A_k x_host with host buffers (numpy float64 arrays or CPU
+        tensors, contiguous, hmg_ndof(level) entries; page-locked tensors copy fastest)."""
+        n = self.ndof(level)
+        _check(lib().hmg_apply_host(self.h, level, _host_ptr(x_host, n), _host_ptr(y_host, n), _stream(stream)))
+
+    def solve_host(self, mode, f_host, u_host, rtol=1e-8, maxit=1000, stream=None):
+        """hmg_solve_host: nodal f on the host -> u on the host. Returns (status, iterations, history)."""
+        n = self.ndof(0)
+        it = ctypes.c_int()
+        hist = (ctypes.c_double * (maxit + 1))()
+        st = lib().hmg_solve_host(self.h, MODE[mode], _host_ptr(f_host, n), _host_ptr(u_host, n), float(rtol),
+                                  int(maxit), ctypes.byref(it), hist, _stream(stream))
+        if st not in (HMG_OK, HMG_ENOCONV, HMG_ENAN):
+            _check(st)
+        return st, it.value, np.array(hist[: it.value + 1])
+
     def solve_low_order(self, low, b, u, rtol=1e-8, maxit=1000, inner_rtol=1e-12, stream=None):
         """hmg_solve_low_order: PCG preconditioned by the low-order problem `low` (a Problem of
         order 1 on this problem's nodes). Returns (status, iterations, inner iterations, history)."""
@@ -307,12 +351,25 @@ def solve_batched(problems, mode, bs, us, rtol=1e-8, maxit=1000, stream=None):
     return list(sts), list(its), [np.array(h[: its[i] + 1]) for i, h in enumerate(hists)]
 
 
+def noalloc_lengths(dim, nelem_fine, order_fine, order_coarse, halve_mesh):
+    """(fine, coarse) node counts of hmg_restrict_noalloc's level pair: prod_a (E_a p_f + 1) and
+    prod_a (E_a' p_c + 1) over the first dim axes, E_a' = E_a / 2 when the mesh is halved."""
+    nf = nc = 1
+    for a in range(int(dim)):
+        e = int(nelem_fine[a])
+        nf *= e * int(order_fine) + 1
+        nc *= (e // 2 if halve_mesh else e) * int(order_coarse) + 1
+    return nf, nc
+
+
 def restrict_noalloc(dim, nelem_fine, order_fine, order_coarse, halve_mesh, rf, rc, stream=None):
     """hmg_restrict_noalloc: r_c = P^T r_f for a structured mesh given by its sizes, using
-    only the library's fixed device storage (no handle, no allocation)."""
+    only the library's fixed device storage (no handle, no allocation). rf and rc must hold
+    the fine and coarse levels' node counts (noalloc_lengths); shorter tensors raise ValueError."""
     E = list(nelem_fine) + [1] * (3 - len(nelem_fine))
+    nf, nc = noalloc_lengths(dim, E, order_fine, order_coarse, halve_mesh)
     _check(lib().hmg_restrict_noalloc(int(dim), (ctypes.c_int * 3)(*E), int(order_fine), int(order_coarse),
-                                      int(bool(halve_mesh)), _ptr(rf), _ptr(rc), _stream(stream)))
+                                      int(bool(halve_mesh)), _ptr(rf, nf), _ptr(rc, nc), _stream(stream)))
 
 
 def launch_count():

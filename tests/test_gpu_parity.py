@@ -102,6 +102,8 @@ def test_apply_diag_rhs_coords_match_oracle(hmg, case):
         assert np.abs(y[rows] - ref).max() < 1e-12 * np.abs(ref).max()
         dref = d.diag_rows(rows)
         assert _rel(1.0 / dinv[rows], dref) < 1e-12
+        bref = d.mass_rows(f, rows)
+        assert np.abs(b[rows] - bref).max() < 1e-12 * np.abs(bref).max()
     P.close()
 
 

@@ -1,0 +1,177 @@
+"""Every block-shape variant of the operator apply against the FP64 oracle, pinned through the
+autotuner's decision cache (HMG_AUTOTUNE_CACHE) in a fresh process so that the variant runs on
+every level of the hierarchy, tiny levels included.
+
+FP64 sum factorization, variants 0-3 (3 stages the geometric factors by TMA): every level's
+operator within 1e-12 relative of the oracle's assembled A (Sec. 2.1, Sec. 2.3's matrix-free
+apply), PCG iteration counts within +-1 of the oracle's (Algorithm 1); at the 16^3 Q4 size of
+the single-solve workload, variants 2 and 3 on sampled rows of the oracle's weak form at element
+vertices, edges, faces and interiors. FP32 variants 0-3 (3 = warp groups): within 2e-5 of the
+oracle (the FP32 rounding bound of the operator's chain of contractions), and the FP64 PCG with
+the FP32 V-cycle within +-1 iteration of the oracle."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SCRIPT = r"""
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np, torch
+import synth
+from oracle import multigrid
+from paper_1402_5938_gb300 import Problem
+cases = {cases!r}
+prec = {prec!r}
+for ci, prob in enumerate(cases):
+    P = Problem(dict(prob, smooth_prec=prec))
+    H = multigrid.Hierarchy(prob)
+    worst = 0.0
+    variants = []
+    for k in range(P.nlevels() - 1):
+        d = H.levels[k].disc
+        x = synth.uniform_pm1(70 + k, d.N)
+        x[d.boundary] = 0.0
+        if prec == "fp64":
+            y = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+            P.apply(k, torch.from_numpy(x).cuda(), y)
+        else:
+            x = x.astype(np.float32).astype(np.float64)
+            y = torch.zeros(d.N, dtype=torch.float32, device="cuda")
+            P.apply_f32(k, torch.from_numpy(x).float().cuda(), y)
+        want = H.levels[k].A @ x[d.interior]
+        got = y.double().cpu().numpy()
+        assert np.all(got[d.boundary] == 0.0)
+        worst = max(worst, float(np.abs(got[d.interior] - want).max() / np.abs(want).max()))
+        variants.append(P.level_variants(k)[0 if prec == "fp64" else 1])
+    d = H.fine.disc
+    f = synth.nodal_field(71, d.N)
+    b = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+    P.rhs(torch.from_numpy(f).cuda(), b)
+    u = torch.zeros_like(b)
+    st, it, _ = P.solve("pcg", b, u, rtol=1e-8, maxit=200)
+    _, it_ref, _, ok = H.solve_pcg(d.rhs(f))
+    print("RESULT", ci, worst, st, it, it_ref, ok, ",".join(map(str, variants)))
+    P.close()
+"""
+
+# 2D and 3D, orders 2/4/8/16 on their hierarchies; the 3D 8^3 Q4 fine level (64,000 Gauss
+# points) and the 2D 24^2 Q4 one are above the autotuner's size threshold
+CASES = [
+    dict(dim=3, nelem=(8, 8, 8), order=4, hier="p", n_hlevels=2),
+    dict(dim=3, nelem=(3, 2, 2), order=2, hier="h", n_hlevels=1),
+    dict(dim=3, nelem=(2, 2, 2), order=8, hier="p", n_hlevels=1),
+    dict(dim=2, nelem=(24, 24), order=4, hier="p", n_hlevels=2),
+    dict(dim=2, nelem=(3, 2), order=16, hier="p", n_hlevels=1),
+    dict(dim=2, nelem=(5, 4), order=8, hier="h", n_hlevels=2),
+]
+
+
+def _problems():
+    import synth
+    return [synth.problem(c["dim"], c["nelem"], c["order"], warp_amp=0.1, mu_b=1e3, hier=c["hier"],
+                          n_hlevels=c["n_hlevels"]) for c in CASES]
+
+
+def _pin_file(path, probs, kind, variant):
+    """Cache lines 'device dim order elements kind variant' for every level of every problem;
+    FP64 levels of mixed problems keep variant 0."""
+    from oracle import multigrid
+    lines = set()
+    for prob in probs:
+        for E, p in multigrid.level_shapes(prob):
+            ne = int(np.prod(E))
+            lines.add(f"0 {prob['dim']} {p} {ne} 0 {variant if kind == 0 else 0}")
+            if kind:
+                lines.add(f"0 {prob['dim']} {p} {ne} {kind} {variant}")
+    path.write_text("\n".join(sorted(lines)) + "\n")
+
+
+def _run(tmp_path, prec, kind, variant):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    probs = _problems()
+    cache = tmp_path / "tune.txt"
+    _pin_file(cache, probs, kind, variant)
+    env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", SCRIPT.format(root=ROOT, cases=probs, prec=prec)], env=env,
+                         cwd=ROOT, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-3000:]
+    rows = [ln.split() for ln in out.stdout.splitlines() if ln.startswith("RESULT")]
+    assert len(rows) == len(probs)
+    return rows
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_fp64_variant_matches_oracle_on_every_level(tmp_path, variant):
+    for r in _run(tmp_path, "fp64", 0, variant):
+        ci, worst, st, it, it_ref, ok, used = int(r[1]), float(r[2]), int(r[3]), int(r[4]), int(r[5]), r[6], r[7]
+        assert set(used.split(",")) == {str(variant)}, (ci, used)
+        assert worst <= 1e-12, (ci, worst)
+        assert st == 0 and ok == "True" and abs(it - it_ref) <= 1, (ci, it, it_ref)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_fp32_variant_matches_oracle_on_every_level(tmp_path, variant):
+    for r in _run(tmp_path, "fp32", 1, variant):
+        ci, worst, st, it, it_ref, ok, used = int(r[1]), float(r[2]), int(r[3]), int(r[4]), int(r[5]), r[6], r[7]
+        assert set(used.split(",")) == {str(variant)}, (ci, used)
+        assert worst <= 2e-5, (ci, worst)
+        assert st == 0 and ok == "True" and abs(it - it_ref) <= 1, (ci, it, it_ref)
+
+
+ROWS_SCRIPT = r"""
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np, torch
+import synth
+from oracle import fem
+from paper_1402_5938_gb300 import Problem
+prob = synth.warped_var3d(16, 4, hier="p")
+P = Problem(prob)
+d = fem.Discretization(3, 16, 4, warp_amp=prob["warp_amp"], mu_a=prob["mu_a"], mu_b=prob["mu_b"], mu_k=prob["mu_k"])
+x = synth.uniform_pm1(72, d.N)
+y = torch.zeros(d.N, dtype=torch.float64, device="cuda")
+P.apply(0, torch.from_numpy(x).cuda(), y)
+y = y.cpu().numpy()
+# rows at element vertices, on element edges, on element faces and inside elements (node index
+# along an axis: multiple of p = element boundary), near the domain boundary and in the middle
+rng = np.random.default_rng(73)
+idx = d.node_axis_index
+on = [(idx[a] % 4 == 0) for a in range(3)]
+nb = on[0].astype(int) + on[1] + on[2]
+rows = []
+for want in (3, 2, 1, 0):
+    cand = np.flatnonzero((nb == want) & ~d.boundary)
+    rows += list(rng.choice(cand, 8, replace=False))
+rows += [int(np.ravel_multi_index((1, 1, 1), d.Nn[::-1])), int(np.ravel_multi_index((32, 32, 32), d.Nn[::-1]))]
+rows = np.array(rows)
+ref = d.apply_rows(x, rows)
+print("RESULT", float(np.abs(y[rows] - ref).max() / np.abs(ref).max()), P.level_variants(0)[0])
+"""
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_fp64_variant_at_16cube_q4_sampled_rows(tmp_path, variant):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    cache = tmp_path / "tune.txt"
+    cache.write_text(f"0 3 4 4096 0 {variant}\n")
+    env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", ROWS_SCRIPT.format(root=ROOT)], env=env, cwd=ROOT,
+                         capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-3000:]
+    r = [ln.split() for ln in out.stdout.splitlines() if ln.startswith("RESULT")][0]
+    assert int(r[2]) == variant
+    assert float(r[1]) <= 1e-12, r

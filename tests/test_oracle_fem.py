@@ -142,6 +142,58 @@ def test_apply_rows_equals_assembled_rows():
     assert np.allclose(d.apply_rows(x, rows), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("dim,E,p", [(2, (3, 2), 5), (3, (2, 2, 1), 3), (3, (1, 1, 1), 11)])
+def test_diag_rows_equals_assembled_diagonal(dim, E, p):
+    # the weak form with u_h = phi_i (the GPU diagonal's reference where A cannot be assembled)
+    # against the diagonal of the assembled element matrices; p = 11 in 3D is one of the sizes
+    # the GPU tests check only by sampled rows
+    d = fem.Discretization(dim, E, p, warp_amp=0.1, mu_a=1.0, mu_b=1e3)
+    rng = np.random.default_rng(4)
+    rows = d.interior[rng.choice(d.n_interior, min(10, d.n_interior), replace=False)]
+    ref = d.assemble().diagonal()[rows]
+    got = d.diag_rows(rows)
+    assert np.all(ref > 0)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.all(d.diag_rows(np.flatnonzero(d.boundary)[:3]) == 0.0)
+
+
+@pytest.mark.parametrize("dim,E,p", [(2, (3, 2), 5), (3, (2, 1, 2), 4), (3, (1, 1, 1), 11)])
+def test_mass_rows_equals_assembled_mass(dim, E, p):
+    d = fem.Discretization(dim, E, p, warp_amp=0.1, mu_a=1.0, mu_b=1e3)
+    rng = np.random.default_rng(5)
+    f = rng.uniform(-1, 1, d.N)                      # all N nodal values, boundary included
+    rows = d.interior[rng.choice(d.n_interior, min(10, d.n_interior), replace=False)]
+    ref = (d.assemble(mass=True) @ f)[rows]
+    assert np.abs(d.mass_rows(f, rows) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dim,E,p", [(2, (4, 3), 3), (3, (2, 3, 2), 2), (3, (2, 1, 1), 6)])
+def test_mass_rows_of_one_are_gll_weights(dim, E, p):
+    # On the affine unit square/cube, (M 1)_i = int phi_i; the Lagrange basis on the p+1 GLL
+    # nodes of an interval integrates to the GLL quadrature weights (that rule is exact to degree
+    # 2p-1 >= p), so int phi_i is the product over axes of the assembled 1D GLL weights of node
+    # i's index: closed forms independent of the oracle's quadrature and element tables.
+    from oracle import basis
+    d = fem.Discretization(dim, E, p)
+    r = basis.gll_nodes(p)
+    # 1D GLL weights on [0,1] from their definition w_j = 2 / (p (p+1) P_p(x_j)^2) on [-1,1]
+    x = 2 * r - 1
+    Pp = np.polynomial.legendre.legval(x, [0] * p + [1])
+    w = 1.0 / (p * (p + 1) * Pp ** 2)                # halved for [0,1]
+    assert np.isclose(w.sum(), 1.0)
+    wax = []
+    for ax in range(dim):
+        v = np.zeros(d.Nn[ax])
+        for e in range(d.E[ax]):
+            v[e * p:e * p + p + 1] += w / d.E[ax]
+        wax.append(v)
+    rows = d.interior[:: max(1, d.n_interior // 15)]
+    ref = np.ones(len(rows))
+    for ax in range(dim):
+        ref *= wax[ax][d.node_axis_index[ax][rows]]
+    assert np.abs(d.mass_rows(np.ones(d.N), rows) - ref).max() <= 1e-14
+
+
 # ---- user-given geometry (node_xyz) and coefficient (mu_fn) -------------------------------
 
 def _poly_map(X):

@@ -2,12 +2,14 @@
 memory, and so cannot create a problem handle (its setup allocates the hierarchy). It keeps
 its stencils and intermediate arrays in fixed device storage of the library; its output
 must equal that of the handle-based hmg_restrict on the same level pair, on two calls in a
-row (the second call reuses the storage the first one left behind). This file is
-collected last so that a run that stops at the first failure has run everything else."""
+row (the second call reuses the storage the first one left behind), and the oracle's
+restriction P^T of Sec. 2.2 Eq. (Pstencil) directly. This file is collected last so that a
+run that stops at the first failure has run everything else."""
 import numpy as np
 import pytest
 
 import synth
+from oracle import fem, transfer
 
 torch = pytest.importorskip("torch")
 
@@ -56,11 +58,49 @@ def test_restrict_noalloc_matches_restrict_on_two_calls(hmg, prob, halve):
     P.close()
 
 
+# (dim, fine elements, fine order, coarse order, halve): one h- and one p-transfer per dimension
+ORACLE_CASES = [(2, (6, 4), 2, 2, True), (2, (3, 5), 6, 3, False), (3, (4, 2, 2), 3, 3, True),
+                (3, (2, 3, 2), 4, 2, False)]
+
+
+@pytest.mark.parametrize("case", ORACLE_CASES, ids=lambda c: str(c))
+def test_restrict_noalloc_matches_oracle_transpose(hmg, case):
+    dim, E, pf, pc, halve = case
+    fine = fem.Discretization(dim, E, pf, warp_amp=0.1)
+    coarse = fem.Discretization(dim, tuple(e // 2 for e in E) if halve else E, pc, warp_amp=0.1)
+    Pm = transfer.prolongation(fine, coarse)
+    rf = synth.uniform_pm1(43, fine.N)
+    want = Pm.T @ rf[fine.interior]
+    for call in range(2):
+        rc = torch.full((coarse.N,), float("nan"), dtype=torch.float64, device=DEV)
+        hmg.restrict_noalloc(dim, E, pf, pc, halve, torch.from_numpy(rf).to(DEV), rc)
+        torch.cuda.synchronize()
+        out = rc.cpu().numpy()
+        assert np.all(out[coarse.boundary] == 0.0), f"call {call}"
+        assert np.abs(out[coarse.interior] - want).max() <= 1e-13 * np.abs(want).max(), f"call {call}"
+
+
+def test_restrict_noalloc_rejects_short_buffers(hmg):
+    nf, nc = hmg.noalloc_lengths(3, (4, 2, 2), 3, 3, True)
+    rf = torch.zeros(nf, dtype=torch.float64, device=DEV)
+    with pytest.raises(ValueError):
+        hmg.restrict_noalloc(3, (4, 2, 2), 3, 3, True, rf, torch.zeros(nc - 1, dtype=torch.float64, device=DEV))
+    with pytest.raises(ValueError):
+        hmg.restrict_noalloc(3, (4, 2, 2), 3, 3, True, rf[:-1], torch.zeros(nc, dtype=torch.float64, device=DEV))
+
+
+def _buffers(hmg, *args):
+    nf, nc = hmg.noalloc_lengths(*args)
+    return (torch.zeros(nf, dtype=torch.float64, device=DEV), torch.zeros(nc, dtype=torch.float64, device=DEV))
+
+
 def test_restrict_noalloc_rejects_sizes_beyond_its_storage(hmg):
-    x = torch.zeros(8, dtype=torch.float64, device=DEV)
+    args = (3, (2048, 2, 2), 4, 4, True)                                  # 8193 nodes on one axis
     with pytest.raises(hmg.HmgError, match="fine nodes along an axis"):
-        hmg.restrict_noalloc(3, (2048, 2, 2), 4, 4, True, x, x)        # 8193 nodes on one axis
+        hmg.restrict_noalloc(*args, *_buffers(hmg, *args))
+    args = (3, (64, 64, 64), 4, 4, True)                                  # 257^3 fine nodes
     with pytest.raises(hmg.HmgError, match="fixed scratch"):
-        hmg.restrict_noalloc(3, (64, 64, 64), 4, 4, True, x, x)        # 257^3 fine nodes
+        hmg.restrict_noalloc(*args, *_buffers(hmg, *args))
+    args = (3, (3, 2, 2), 2, 2, True)                                     # odd count cannot halve
     with pytest.raises(hmg.HmgError):
-        hmg.restrict_noalloc(3, (3, 2, 2), 2, 2, True, x, x)           # odd count cannot halve
+        hmg.restrict_noalloc(*args, *_buffers(hmg, *args))
