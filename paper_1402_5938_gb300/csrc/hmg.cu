@@ -103,7 +103,7 @@ struct Level {
   double* wdetJ = nullptr;
   double* dinv = nullptr;
   float* G32 = nullptr;
-  void* G16 = nullptr;    // 16-bit factors of the FP16/BF16 V-cycle operator (orders <= 7)
+  void* G16 = nullptr;    // 16-bit factors of the FP16/BF16 V-cycle operator
   double* Ke = nullptr;   // element matrices of a low-order FP64 level (dense-apply variant)
   double* Kb = nullptr;   // block Jacobi: inverses of the element-interior blocks [E][MI][MI]
   double* dinv_s = nullptr;  // block Jacobi: D^-1 on shared nodes, 0 at element-interior nodes
@@ -708,10 +708,12 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     TRY(cudaEventCreate(&e0));
     TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bv = 0;
+    int bv = (prec != 0 && l.G16 && l.m.p > kMaxOrder16) ? kFirstPencilVariant : 0;
     cudaError_t err = cudaSuccess;
     const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : (l.G16 ? kApply16Variants : kApply32Variants);
-    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
+    // 16-bit levels above the tensor-core kernel's orders have only the pencil variants
+    const int v0 = (prec != 0 && l.G16 && l.m.p > kMaxOrder16) ? kFirstPencilVariant : 0;
+    for (int v = v0; v < nvar && err == cudaSuccess; ++v) {
       auto run = [&]() {
         if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v, l.Ke);
         if (l.G16)
@@ -725,6 +727,9 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
       if (err == cudaSuccess) err = cudaEventSynchronize(e1);
       float ms = 0.f;
       if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err == cudaSuccess && Phase::timing())
+        fprintf(stderr, "hmg autotune: dim %d p %d elements %lld %s variant %d: %.4f ms per apply\n", l.m.dim,
+                l.m.p, l.m.nelem, kind == 0 ? "fp64" : (kind == HMG_PREC_FP32 ? "fp32" : "16-bit"), v, ms / 3);
       if (err == cudaSuccess && ms < best) {
         best = ms;
         bv = v;
@@ -944,7 +949,7 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         if (hb) { set_error("block Jacobi: an element-interior block is not positive definite"); return HMG_EINVAL; }
       }
       if (mixed) {
-        if (lowp && l.m.p <= kMaxOrder16) {
+        if (lowp) {
           TRY(P.alloc((void**)&l.G16, gsz * nc_of(D.dim) * 2 + 256));  // TMA tail padding
           if (D.smooth_prec == HMG_PREC_FP16) TRY(P.alloc((void**)&l.gsc, l.m.nelem * sizeof(float)));
         } else {
@@ -1264,7 +1269,7 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
       blk_temp = std::max(blk_temp, (size_t)m.nelem * mi * mi * 8 + 512);
     }
     if (mixed) {
-      if (lowp && m.p <= kMaxOrder16) {
+      if (lowp) {
         add(gsz * nc_of(D.dim) * 2 + 256);
         if (D.smooth_prec == HMG_PREC_FP16) add((size_t)m.nelem * 4);
       } else {

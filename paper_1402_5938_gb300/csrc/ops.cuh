@@ -13,7 +13,10 @@ namespace hmg {
 // groups without block barriers); setup
 // picks it per level by timing (autotuning).
 constexpr int kApply64Variants = 4;
-constexpr int kApply32Variants = 4;  // 0-2 block tiles, 3 warp groups (orders <= 8; else as 0)
+// FP32: 0-2 block tiles, 3 warp groups (orders <= 8; else as 0), 4 pencil form (pencil.cuh), 5 pencil
+// form with the factors held in registers from the start (small orders; else as 4), 6 plane form
+// (3D orders <= 4; else as 5)
+constexpr int kApply32Variants = 7;
 constexpr int kMaxNWarp32 = 9;
 // FP64 variant kApply64Dense: stored element matrices Ke (launch_elem_mats) instead of sum
 // factorization, for orders with N <= kMaxNDense; other variants ignore Ke.
@@ -28,12 +31,15 @@ cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, d
 cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
                              const float* G, float alpha, int* err, cudaStream_t s, int variant = 0);
 
-// y += alpha * A x with 16-bit geometric factors and tensor-core contractions (FP32 vectors),
-// for orders p <= 7; prec is HMG_PREC_FP16 (gsc: per-element factor scales) or HMG_PREC_BF16
-// (gsc unused). G16 needs >= 16 bytes of tail padding. variant 0..2 selects the warps per block,
-// 3 half-size element groups (more warps on small meshes).
-constexpr int kApply16Variants = 4;
+// y += alpha * A x with 16-bit geometric factors (FP32 vectors); prec is HMG_PREC_FP16 (gsc: per-
+// element factor scales) or HMG_PREC_BF16 (gsc unused). G16 needs >= 16 bytes of tail padding.
+// Variants 0..3, orders p <= kMaxOrder16: 16-bit operands on the tensor cores (mma.sync) with FP32
+// accumulation, 0..2 selecting the warps per block, 3 half-size element groups; variants 4, 5 (all
+// orders, and the only ones above kMaxOrder16): the pencil form with FP32 arithmetic on the 16-bit
+// factors (5: factors in registers from the start); 6: the plane form (3D orders <= 4; else as 5).
+constexpr int kApply16Variants = 7;
 constexpr int kMaxOrder16 = 7;
+constexpr int kFirstPencilVariant = 4;
 cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
                               const float* gsc, float alpha, int prec, int* err, cudaStream_t s, int variant = 0);
 // G16 = G / gsc[e] in 16-bit (FP16: gsc[e] a power of two, largest |G16| in [0.5, 1); BF16: no scale),

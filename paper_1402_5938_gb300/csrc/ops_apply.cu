@@ -6,6 +6,7 @@
 
 #include "dispatch.cuh"
 #include "ops.cuh"
+#include "pencil.cuh"
 
 namespace hmg {
 
@@ -32,6 +33,11 @@ cudaError_t apply32_dim(const Mesh& m, const Basis1D& b, const float* x, float* 
                         int* err, int variant, cudaStream_t s) {
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
+    if constexpr (DIM == 3 && N <= kMaxNPlane) {
+      if (variant == 6) return launch_plane<N, float>(m, b, x, y, G, nullptr, alpha, s);
+    }
+    if (variant >= 4)
+      return launch_pencil<DIM, N, float>(m, b, x, y, G, nullptr, alpha, variant != 4, s);
     if constexpr (N <= kMaxNWarp32) {
       if (variant == 3) {  // warp-group form
         using W = Apply32wCfg<DIM, N>;

@@ -8,6 +8,7 @@
 #include "dispatch.cuh"
 #include "element16.cuh"
 #include "ops.cuh"
+#include "pencil.cuh"
 
 namespace hmg {
 
@@ -58,9 +59,15 @@ cudaError_t apply16_launch(const Mesh& m, const Basis1D& b, const float* x, floa
 template <int DIM, typename T>
 cudaError_t apply16_dim(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
                         const float* gsc, float alpha, int* err, int variant, cudaStream_t s) {
-  if (b.n > kMaxN16) return cudaErrorInvalidValue;
   return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
     constexpr int N = decltype(nc)::value;
+    // variants 4, 5: the pencil form with 16-bit factors and FP32 arithmetic (every order; 5 keeps
+    // the factors in registers from the start); orders above the tensor-core kernel's take 4
+    if constexpr (DIM == 3 && N <= kMaxNPlane) {
+      if (variant == 6) return launch_plane<N, T>(m, b, x, y, static_cast<const T*>(G16), gsc, alpha, s);
+    }
+    if (variant >= 4 || N > kMaxN16)
+      return launch_pencil<DIM, N, T>(m, b, x, y, static_cast<const T*>(G16), gsc, alpha, variant >= 5, s);
     if constexpr (N > kMaxN16) {
       return cudaErrorInvalidValue;
     } else {
