@@ -82,11 +82,10 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC
  *   smooth_prec        : HMG_PREC_FP64, or HMG_PREC_FP32 for the V-cycle's smoother, residual and
  *                        transfer work below the FP64 fine residual / PCG / coarsest solve.
  *                        HMG_PREC_FP16 / HMG_PREC_BF16: the same FP32 V-cycle whose operator
- *                        applies on levels of order p <= 7 store the geometric factors in 16 bits
- *                        (FP16 with a power-of-two scale per element) and run the 1D contractions
- *                        on the tensor cores with 16-bit operands and FP32 accumulation (levels of
- *                        higher order keep the FP32 apply); PCG then uses the flexible
- *                        (Polak-Ribiere) beta, since such a preconditioner is only nearly linear.
+ *                        applies store the geometric factors in 16 bits (FP16 with a power-of-two
+ *                        scale per element; BF16 unscaled), read in FP32 arithmetic on every
+ *                        level; PCG then uses the flexible (Polak-Ribiere) beta, since such a
+ *                        preconditioner is only nearly linear.
  *   node_xyz, mu_fn    : optional user geometry and coefficient (Sec. 2: a general domain Omega
  *                        and mu(x) >= mu_0 > 0); NULL keeps the warp map and the cos^2 formula.
  *                        The solve server takes built-in geometry and coefficients only.
@@ -156,8 +155,8 @@ hmg_status hmg_level_info(const hmg_problem* prob, int level, int* nelem3, int* 
 size_t hmg_device_bytes(const hmg_problem* prob);
 /* Apply block shapes the setup's autotuner chose on a level (no counterpart in the paper):
  * FP64 operator (0-2 block shapes, 3 with TMA-staged factors, 4 stored dense element matrices
- * for orders 1-2) and the mixed V-cycle's operator (FP32: 0-2 tile sizes; FP16/BF16: 0-2 warps
- * per block, 3 half-size element groups). */
+ * for orders 1-2) and the mixed V-cycle's operator (when a thread loads its factors: 0 one phase
+ * before the pointwise product, 1 before the first phase, 2 at their use). */
 hmg_status hmg_level_variants(const hmg_problem* prob, int level, int* v_fp64, int* v_vcycle);
 
 /* Physical node coordinates of a level, written as xyz_dev[c * N + node], c < dim (the warp map,
@@ -173,9 +172,9 @@ hmg_status hmg_rhs(hmg_problem* prob, const double* f_nodal_dev, double* b_dev, 
 hmg_status hmg_apply(hmg_problem* prob, int level, const double* x_dev, double* y_dev, void* stream);
 
 /* FP32-vector variant of hmg_apply: the operator the mixed-precision V-cycle applies on level k
- * (smooth_prec = HMG_PREC_FP32: FP32 factors and arithmetic; HMG_PREC_FP16 / HMG_PREC_BF16:
- * 16-bit factors and tensor-core contractions with FP32 accumulation where the level's order is
- * <= 7, else FP32). Needs a smooth_prec other than HMG_PREC_FP64 at setup. */
+ * (FP32 vectors and arithmetic; geometric factors in FP32 for smooth_prec = HMG_PREC_FP32, in
+ * 16 bits for HMG_PREC_FP16 / HMG_PREC_BF16). Needs a smooth_prec other than HMG_PREC_FP64 at
+ * setup. */
 hmg_status hmg_apply_f32(hmg_problem* prob, int level, const float* x_dev, float* y_dev, void* stream);
 
 /* D^-1 of level k (inverse diagonal of A_k; 0 on boundary nodes), Sec. 3.2.1. */

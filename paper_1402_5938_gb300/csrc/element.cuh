@@ -123,281 +123,10 @@ __device__ __forceinline__ void contract(const T* src, T* dst, const T* M, int d
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// FP32 apply, y += alpha * A x, for the mixed-precision V-cycle. Here the geometric factors
-// (24 q^d bytes per element) dominate the traffic and the arithmetic is cheap, so the
-// kernel streams them: persistent blocks walk over tiles of `epb` elements, and one thread
-// per block loads each tile's contiguous G slab into shared memory with a bulk TMA copy
-// (cp.async.bulk + mbarrier), NBUF = 2 buffers deep so the next tile's factors arrive
-// while the current tile is gathered and contracted. Contractions are line-based with
-// the line in registers and table entries as uniform parameter-space operands.
-// A bulk copy must start on 16 bytes: the slab is fetched from the 16-byte boundary below
-// it (G is allocated with tail padding) and read at that offset in shared memory.
-// Waits are bounded: on timeout the block records kErrTmaTimeout in *err, waits (bounded)
-// for its other copy in flight and returns.
-// ---------------------------------------------------------------------------------------
+// Error code a kernel writes to its error flag when a bounded wait on a TMA copy gives up, and
+// the poll limit of those waits.
 constexpr int kErrTmaTimeout = 1;
 constexpr uint32_t kWaitPolls = 1u << 22;
-
-template <int DIM, int N, int NBUF>
-struct Apply32Cfg {
-  static constexpr int NP = Sh<DIM, N>::NP, NC = Sh<DIM, N>::NC;
-  __host__ __device__ static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
-  // bytes of one G buffer: the slab plus up to 16 bytes of alignment slack
-  __host__ __device__ static size_t gslot(int epb) { return al16((size_t)epb * NC * NP * 4 + 16); }
-  // shared-memory layout; every region starts on 16 bytes:
-  // [0,128): mbarriers + flag | G buffers | U | V (DIM tiles) | element bases (8 B) | face bits (4 B)
-  __host__ __device__ static size_t off_g() { return 128; }
-  __host__ __device__ static size_t off_u(int epb) { return off_g() + NBUF * gslot(epb); }
-  __host__ __device__ static size_t off_v(int epb) { return off_u(epb) + al16((size_t)epb * NP * 4); }
-  __host__ __device__ static size_t off_base(int epb) { return off_v(epb) + al16((size_t)DIM * epb * NP * 4); }
-  __host__ __device__ static size_t off_flag(int epb) { return off_base(epb) + al16((size_t)epb * 8); }
-  __host__ __device__ static size_t smem(int epb) { return off_flag(epb) + al16((size_t)epb * 4); }
-};
-
-template <int DIM, int N, int NBUF>
-__global__ void __launch_bounds__(512)
-k_apply32(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ G, const Mesh m,
-          const __grid_constant__ Tab<N, float> tab, const float alpha, const int epb, const long long ntiles,
-          int* __restrict__ err) {
-  using C = Apply32Cfg<DIM, N, NBUF>;
-  constexpr int NP = C::NP, NC = C::NC;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  int* sflag = reinterpret_cast<int*>(smem_raw + 64);
-  const size_t gslot = C::gslot(epb);
-  unsigned char* gbuf = smem_raw + C::off_g();
-  float* U = reinterpret_cast<float*>(smem_raw + C::off_u(epb));
-  float* V = reinterpret_cast<float*>(smem_raw + C::off_v(epb));
-  long long* ebase = reinterpret_cast<long long*>(smem_raw + C::off_base(epb));
-  int* eflag = reinterpret_cast<int*>(smem_raw + C::off_flag(epb));
-  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
-
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < NBUF; ++b) mbar_init(&bar[b], 1);
-    mbar_init_fence();
-  }
-  __syncthreads();
-
-  // byte offset of tile t's slab above the 16-byte boundary it is fetched from
-  auto slab = [&](long long t, const char** src, uint32_t* bytes) -> int {
-    const long long e0 = t * epb;
-    const long long ne = min((long long)epb, m.nelem - e0);
-    const char* p = reinterpret_cast<const char*>(G + e0 * NC * NP);
-    const int off = (int)(reinterpret_cast<uintptr_t>(p) & 15);
-    *src = p - off;
-    *bytes = (uint32_t)((ne * NC * NP * 4 + off + 15) & ~15LL);
-    return off;
-  };
-  auto issue = [&](long long t, int b) {
-    const char* src;
-    uint32_t bytes;
-    slab(t, &src, &bytes);
-    fence_proxy_async_smem();
-    bulk_g2s(gbuf + b * gslot, src, bytes, &bar[b]);
-  };
-
-  uint32_t phase[NBUF > 1 ? NBUF : 1] = {};
-  long long t = blockIdx.x;
-  if (threadIdx.x == 0 && t < ntiles) issue(t, 0);
-  for (int k = 0; t < ntiles; t += gridDim.x, ++k) {
-    const int b = NBUF > 1 ? (k & 1) : 0;
-    const long long tn = t + gridDim.x;
-    if (NBUF > 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, b ^ 1);
-    const long long e0 = t * epb;
-    const int ne = (int)min((long long)epb, m.nelem - e0);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) elem_base(m, e0 + e, &ebase[e], &eflag[e]);
-    __syncthreads();
-    for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
-      const int e = i / NP, a = i - e * NP;
-      bool bd;
-      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
-      U[i] = bd ? 0.0f : x[g];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      contract<DIM, N, float, false, false>(U, U, tab.B, d, ne);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) contract<DIM, N, float, false, false>(U, V + d * epb * NP, tab.D, d, ne);
-    // this tile's factors: thread 0 polls with a limit, then everyone observes the phase
-    if (threadIdx.x == 0) *sflag = mbar_wait(&bar[b], phase[b], kWaitPolls) ? 0 : 1;
-    __syncthreads();
-    if (*sflag) {
-      if (threadIdx.x == 0) {
-        atomicExch(err, kErrTmaTimeout);
-        if (NBUF > 1 && tn < ntiles) mbar_wait(&bar[b ^ 1], phase[b ^ 1], kWaitPolls);
-      }
-      return;
-    }
-    mbar_wait(&bar[b], phase[b], kWaitPolls);
-    phase[b] ^= 1;
-    const char* src;
-    uint32_t bytes;
-    const int off = slab(t, &src, &bytes);
-    const float* Gt = reinterpret_cast<const float*>(gbuf + b * gslot + off);
-    for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
-      const int e = i / NP, q = i - e * NP;
-      const float* g = Gt + e * NC * NP + q;
-      if (DIM == 3) {
-        const float u0 = V[i], u1 = V[epb * NP + i], u2 = V[2 * epb * NP + i];
-        const float g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
-        V[i] = g00 * u0 + g01 * u1 + g02 * u2;
-        V[epb * NP + i] = g01 * u0 + g11 * u1 + g12 * u2;
-        V[2 * epb * NP + i] = g02 * u0 + g12 * u1 + g22 * u2;
-      } else {
-        const float u0 = V[i], u1 = V[epb * NP + i];
-        const float g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
-        V[i] = g00 * u0 + g01 * u1;
-        V[epb * NP + i] = g01 * u0 + g11 * u1;
-      }
-    }
-    __syncthreads();
-    if (NBUF == 1 && threadIdx.x == 0 && tn < ntiles) issue(tn, 0);  // the single buffer is free
-    contract<DIM, N, float, true, false>(V, U, tab.D, 0, ne);
-    __syncthreads();
-    contract<DIM, N, float, true, true>(V + epb * NP, U, tab.D, 1, ne);
-    __syncthreads();
-    if (DIM == 3) {
-      contract<DIM, N, float, true, true>(V + 2 * epb * NP, U, tab.D, 2, ne);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      contract<DIM, N, float, true, false>(U, U, tab.B, d, ne);
-      __syncthreads();
-    }
-    for (int i = threadIdx.x; i < ne * NP; i += blockDim.x) {
-      const int e = i / NP, a = i - e * NP;
-      bool bd;
-      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
-      if (!bd) atomicAdd(y + g, alpha * U[i]);
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// FP32 apply, warp-group form (orders p <= 8): each warp owns a group of EW elements (about 128
-// lines per direction) and runs the same sum-factorized phases as k_apply32 on its own
-// shared-memory tiles, one line per lane at a time with the line in registers and the 1D table
-// entries as uniform kernel-parameter operands, separated by __syncwarp only (no block-wide
-// barriers); the geometric factors are read straight from global memory, consecutive lanes on
-// consecutive points of an element (coalesced).
-// ---------------------------------------------------------------------------------------
-template <int DIM, int N>
-struct Apply32wCfg {
-  static constexpr int NP = Sh<DIM, N>::NP, NL = Sh<DIM, N>::NL, NC = Sh<DIM, N>::NC;
-  static constexpr int EW0 = (128 + NL / 2) / NL;
-  static constexpr int EW = EW0 < 1 ? 1 : EW0;  // elements per warp group
-  static constexpr int TILE = EW * NP;            // floats per tile
-  // per warp: U, DIM gradient tiles, then (16-byte aligned) element bases (8 B) and face bits (4 B)
-  static constexpr size_t OFF_BASE = ((size_t)(1 + DIM) * TILE * 4 + 15) / 16 * 16;
-  static constexpr size_t WARP_BYTES = (OFF_BASE + (size_t)EW * 12 + 15) / 16 * 16;
-};
-
-// dst (=, or += if ACC) the table contraction of src along `dir` for the ne elements of a warp
-// group, lane by lane (src may equal dst: a lane reads its whole line before writing it)
-template <int DIM, int N, bool TRN, bool ACC>
-__device__ __forceinline__ void contract_w(const float* src, float* dst, const float* M, int dir, int ne, int lane) {
-  constexpr int NP = Sh<DIM, N>::NP, NL = Sh<DIM, N>::NL;
-  const int total = ne * NL;
-  for (int t = lane; t < total; t += 32) {
-    const int e = t / NL, l = t - e * NL;
-    int base, stride;
-    line_of<DIM, N>(dir, l, base, stride);
-    base += e * NP;
-    float in[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q) in[q] = src[base + q * stride];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float s = (TRN ? M[i] : M[i * N]) * in[0];
-#pragma unroll
-      for (int q = 1; q < N; ++q) s = fmaf(TRN ? M[q * N + i] : M[i * N + q], in[q], s);
-      if (ACC) dst[base + i * stride] += s;
-      else dst[base + i * stride] = s;
-    }
-  }
-}
-
-template <int DIM, int N>
-__global__ void __launch_bounds__(128)
-k_apply32w(const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ G, const Mesh m,
-           const __grid_constant__ Tab<N, float> tab, const float alpha, const long long ngroups) {
-  using C = Apply32wCfg<DIM, N>;
-  constexpr int NP = C::NP, NC = C::NC, EW = C::EW, TILE = C::TILE;
-  extern __shared__ __align__(128) unsigned char smem_w[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* ws = smem_w + warp * C::WARP_BYTES;
-  float* U = reinterpret_cast<float*>(ws);
-  float* V = U + TILE;  // DIM tiles
-  long long* ebase = reinterpret_cast<long long*>(ws + C::OFF_BASE);
-  int* eflag = reinterpret_cast<int*>(ebase + EW);
-  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
-  const long long gstride = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long grp = (long long)blockIdx.x * (blockDim.x >> 5) + warp; grp < ngroups; grp += gstride) {
-    const long long e0 = grp * EW;
-    const int ne = (int)min((long long)EW, m.nelem - e0);
-    for (int e = lane; e < ne; e += 32) elem_base(m, e0 + e, &ebase[e], &eflag[e]);  // EW may exceed 32
-    __syncwarp();
-    for (int i = lane; i < ne * NP; i += 32) {
-      const int e = i / NP, a = i - e * NP;
-      bool bd;
-      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
-      U[i] = bd ? 0.0f : x[g];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      contract_w<DIM, N, false, false>(U, U, tab.B, d, ne, lane);
-      __syncwarp();
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) contract_w<DIM, N, false, false>(U, V + d * TILE, tab.D, d, ne, lane);
-    __syncwarp();
-    const float* Gg = G + e0 * NC * NP;
-    for (int i = lane; i < ne * NP; i += 32) {
-      const int e = i / NP, q = i - e * NP;
-      const float* g = Gg + (long long)e * NC * NP + q;
-      if (DIM == 3) {
-        const float u0 = V[i], u1 = V[TILE + i], u2 = V[2 * TILE + i];
-        const float g00 = g[0], g01 = g[NP], g02 = g[2 * NP], g11 = g[3 * NP], g12 = g[4 * NP], g22 = g[5 * NP];
-        V[i] = g00 * u0 + g01 * u1 + g02 * u2;
-        V[TILE + i] = g01 * u0 + g11 * u1 + g12 * u2;
-        V[2 * TILE + i] = g02 * u0 + g12 * u1 + g22 * u2;
-      } else {
-        const float u0 = V[i], u1 = V[TILE + i];
-        const float g00 = g[0], g01 = g[NP], g11 = g[2 * NP];
-        V[i] = g00 * u0 + g01 * u1;
-        V[TILE + i] = g01 * u0 + g11 * u1;
-      }
-    }
-    __syncwarp();
-    contract_w<DIM, N, true, false>(V, U, tab.D, 0, ne, lane);
-    __syncwarp();
-    contract_w<DIM, N, true, true>(V + TILE, U, tab.D, 1, ne, lane);
-    __syncwarp();
-    if (DIM == 3) {
-      contract_w<DIM, N, true, true>(V + 2 * TILE, U, tab.D, 2, ne, lane);
-      __syncwarp();
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      contract_w<DIM, N, true, false>(U, U, tab.B, d, ne, lane);
-      __syncwarp();
-    }
-    for (int i = lane; i < ne * NP; i += 32) {
-      const int e = i / NP, a = i - e * NP;
-      bool bd;
-      const long long g = local_node<DIM, N>(a, ebase[e], eflag[e], nx, nxy, bd);
-      if (!bd) atomicAdd(y + g, alpha * U[i]);
-    }
-    __syncwarp();
-  }
-}
 
 // ---------------------------------------------------------------------------------------
 // FP64 apply, y += alpha * A x. On GB300 a warp-wide DFMA occupies the SM's FP64 pipe

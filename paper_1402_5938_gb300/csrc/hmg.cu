@@ -102,8 +102,7 @@ struct Level {
   double* G = nullptr;    // [E][NC][NP] geometric factors mu w detJ J^-1 J^-T
   double* wdetJ = nullptr;
   double* dinv = nullptr;
-  float* G32 = nullptr;
-  void* G16 = nullptr;    // 16-bit factors of the FP16/BF16 V-cycle operator
+  void* Glow = nullptr;   // factors of the mixed V-cycle's operator (FP32, FP16 or BF16, grouped layout)
   double* Ke = nullptr;   // element matrices of a low-order FP64 level (dense-apply variant)
   double* Kb = nullptr;   // block Jacobi: inverses of the element-interior blocks [E][MI][MI]
   double* dinv_s = nullptr;  // block Jacobi: D^-1 on shared nodes, 0 at element-interior nodes
@@ -386,10 +385,7 @@ hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  if (l.G16)
-    TRY(launch_apply_lowp(l.m, l.basis, x, y, l.G16, l.gsc, alpha, P.desc.smooth_prec, P.err, s, l.v32));
-  else
-    TRY(launch_apply_f32(l.m, l.basis, x, y, l.G32, alpha, P.err, s, l.v32));
+  TRY(launch_apply_low(l.m, l.basis, x, y, l.Glow, l.gsc, alpha, P.desc.smooth_prec, s, l.v32));
   return HMG_OK;
 }
 
@@ -691,9 +687,9 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   }();
   int dev = 0;
   TRY(cudaGetDevice(&dev));
-  const bool mixed = l.G32 != nullptr || l.G16 != nullptr;
+  const bool mixed = l.Glow != nullptr;
   for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
-    const int kind = prec == 0 ? 0 : (l.G16 ? P.desc.smooth_prec : HMG_PREC_FP32);
+    const int kind = prec == 0 ? 0 : P.desc.smooth_prec;
     const auto key = std::make_tuple(dev, l.m.dim, l.m.p, l.m.nelem, kind);
     {
       std::lock_guard<std::mutex> lk(mu);
@@ -708,17 +704,13 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     TRY(cudaEventCreate(&e0));
     TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bv = (prec != 0 && l.G16 && l.m.p > kMaxOrder16) ? kFirstPencilVariant : 0;
+    int bv = 0;
     cudaError_t err = cudaSuccess;
-    const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : (l.G16 ? kApply16Variants : kApply32Variants);
-    // 16-bit levels above the tensor-core kernel's orders have only the pencil variants
-    const int v0 = (prec != 0 && l.G16 && l.m.p > kMaxOrder16) ? kFirstPencilVariant : 0;
-    for (int v = v0; v < nvar && err == cudaSuccess; ++v) {
+    const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : kApplyLowVariants;
+    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
       auto run = [&]() {
         if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v, l.Ke);
-        if (l.G16)
-          return launch_apply_lowp(l.m, l.basis, l.x32, l.r32, l.G16, l.gsc, 1.0f, P.desc.smooth_prec, P.err, s, v);
-        return launch_apply_f32(l.m, l.basis, l.x32, l.r32, l.G32, 1.0f, P.err, s, v);
+        return launch_apply_low(l.m, l.basis, l.x32, l.r32, l.Glow, l.gsc, 1.0f, P.desc.smooth_prec, s, v);
       };
       if ((err = run()) != cudaSuccess) break;  // warm-up (also opts the kernel into its smem)
       if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
@@ -728,7 +720,7 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
       float ms = 0.f;
       if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
       if (err == cudaSuccess && Phase::timing())
-        fprintf(stderr, "hmg autotune: dim %d p %d elements %lld %s variant %d: %.4f ms per apply\n", l.m.dim,
+        fprintf(stderr, "hmg autotune timing: dim %d p %d elements %lld %s variant %d: %.4f ms per apply\n", l.m.dim,
                 l.m.p, l.m.nelem, kind == 0 ? "fp64" : (kind == HMG_PREC_FP32 ? "fp32" : "16-bit"), v, ms / 3);
       if (err == cudaSuccess && ms < best) {
         best = ms;
@@ -859,7 +851,6 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       CHECK(talloc((void**)&mu_d, (size_t)nq0 * sizeof(double)));
     }
     const bool mixed = D.smooth_prec != HMG_PREC_FP64;
-    const bool lowp = D.smooth_prec == HMG_PREC_FP16 || D.smooth_prec == HMG_PREC_BF16;
     for (size_t k = 0; k < P.L.size(); ++k) {
       Phase ph("setup: level geometry, diagonal", s);
       Level& l = P.L[k];
@@ -949,21 +940,14 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         if (hb) { set_error("block Jacobi: an element-interior block is not positive definite"); return HMG_EINVAL; }
       }
       if (mixed) {
-        if (lowp) {
-          TRY(P.alloc((void**)&l.G16, gsz * nc_of(D.dim) * 2 + 256));  // TMA tail padding
-          if (D.smooth_prec == HMG_PREC_FP16) TRY(P.alloc((void**)&l.gsc, l.m.nelem * sizeof(float)));
-        } else {
-          TRY(P.alloc((void**)&l.G32, gsz * nc_of(D.dim) * sizeof(float) + 256));  // TMA tail padding
-        }
+        TRY(P.alloc((void**)&l.Glow, low_factor_bytes(l.m, D.smooth_prec) + 256));  // prefetch rounding
+        if (D.smooth_prec == HMG_PREC_FP16) TRY(P.alloc((void**)&l.gsc, l.m.nelem * sizeof(float)));
         TRY(P.alloc((void**)&l.dinv32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.b32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.x32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.r32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.d32, n * sizeof(float)));
-        if (l.G16)
-          TRY(launch_pack_g16(l.G, l.G16, l.gsc, l.m.nelem, nc_of(D.dim), (int)np_of(l.m), D.dim, D.smooth_prec, s));
-        else
-          TRY(to_f32(l.G32, l.G, gsz * nc_of(D.dim), s));
+        TRY(launch_pack_low(l.G, l.Glow, l.gsc, l.m, D.smooth_prec, s));
         TRY(to_f32(l.dinv32, l.dinv, n, s));
       }
       CHECK(tune_level(P, l, s));
@@ -1250,7 +1234,6 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
   std::vector<std::pair<std::vector<int>, int>> shapes;
   CHECK(level_shapes(D, shapes));
   const bool mixed = D.smooth_prec != HMG_PREC_FP64;
-  const bool lowp = D.smooth_prec == HMG_PREC_FP16 || D.smooth_prec == HMG_PREC_BF16;
   std::vector<Mesh> ms;
   for (auto& sh : shapes) ms.push_back(make_mesh(D.dim, sh.first.data(), sh.second));
   size_t res = 0, allocs = 0, max_stage = 0, max_tbuf = 0, arnoldi = 0, blk_temp = 0;
@@ -1269,12 +1252,8 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
       blk_temp = std::max(blk_temp, (size_t)m.nelem * mi * mi * 8 + 512);
     }
     if (mixed) {
-      if (lowp) {
-        add(gsz * nc_of(D.dim) * 2 + 256);
-        if (D.smooth_prec == HMG_PREC_FP16) add((size_t)m.nelem * 4);
-      } else {
-        add(gsz * nc_of(D.dim) * 4 + 256);
-      }
+      add(low_factor_bytes(m, D.smooth_prec) + 256);
+      if (D.smooth_prec == HMG_PREC_FP16) add((size_t)m.nelem * 4);
       for (int v = 0; v < 5; ++v) add(n * 4);
     }
     max_stage = std::max(max_stage, gsz * D.dim * (D.dim + 1) * 8);
@@ -1449,7 +1428,7 @@ hmg_status hmg_apply(hmg_problem* p, int level, const double* x, double* y, void
 
 hmg_status hmg_apply_f32(hmg_problem* p, int level, const float* x, float* y, void* stream) {
   if (!level_ok(p, level) || !x || !y) { set_error("null argument"); return HMG_EINVAL; }
-  if (!p->impl.L[level].G32 && !p->impl.L[level].G16) {
+  if (!p->impl.L[level].Glow) {
     set_error("the V-cycle operator in FP32 vectors exists only for a smooth_prec other than HMG_PREC_FP64");
     return HMG_EINVAL;
   }

@@ -6,18 +6,11 @@
 
 namespace hmg {
 
-// y += alpha * A x (FP64 or FP32 data; G in the same precision). Both kernels stage G with
-// bulk TMA copies (FP64: when the slab fits in shared memory) and need G allocated with >= 16
-// bytes of tail padding; a timed-out wait sets *err (device int) to a nonzero code.
-// `variant` selects the block shape (FP64: 0..3, 3 = TMA-staged G; FP32: 0..2 tile sizes, 3 warp
-// groups without block barriers); setup
-// picks it per level by timing (autotuning).
+// y += alpha * A x in FP64 (G [E][NC][NP] in FP64). Variant 3 stages G with bulk TMA copies (when
+// the slab fits in shared memory) and needs G allocated with >= 16 bytes of tail padding; a
+// timed-out wait sets *err (device int) to a nonzero code. `variant` selects the block shape
+// (0..3, 3 = TMA-staged G); setup picks it per level by timing (autotuning).
 constexpr int kApply64Variants = 4;
-// FP32: 0-2 block tiles, 3 warp groups (orders <= 8; else as 0), 4 pencil form (pencil.cuh), 5 pencil
-// form with the factors held in registers from the start (small orders; else as 4), 6 plane form
-// (3D orders <= 4; else as 5)
-constexpr int kApply32Variants = 7;
-constexpr int kMaxNWarp32 = 9;
 // FP64 variant kApply64Dense: stored element matrices Ke (launch_elem_mats) instead of sum
 // factorization, for orders with N <= kMaxNDense; other variants ignore Ke.
 constexpr int kApply64Dense = 4;
@@ -28,24 +21,19 @@ cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, d
 // Ke[(e * NP + b) * NP + a] = K_e[a][b], the element stiffness matrices (all nodes; the apply
 // masks the boundary), by sum-factorized unit columns.
 cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, double* Ke, cudaStream_t s);
-cudaError_t launch_apply_f32(const Mesh& m, const Basis1D& b, const float* x, float* y,
-                             const float* G, float alpha, int* err, cudaStream_t s, int variant = 0);
-
-// y += alpha * A x with 16-bit geometric factors (FP32 vectors); prec is HMG_PREC_FP16 (gsc: per-
-// element factor scales) or HMG_PREC_BF16 (gsc unused). G16 needs >= 16 bytes of tail padding.
-// Variants 0..3, orders p <= kMaxOrder16: 16-bit operands on the tensor cores (mma.sync) with FP32
-// accumulation, 0..2 selecting the warps per block, 3 half-size element groups; variants 4, 5 (all
-// orders, and the only ones above kMaxOrder16): the pencil form with FP32 arithmetic on the 16-bit
-// factors (5: factors in registers from the start); 6: the plane form (3D orders <= 4; else as 5).
-constexpr int kApply16Variants = 7;
-constexpr int kMaxOrder16 = 7;
-constexpr int kFirstPencilVariant = 4;
-cudaError_t launch_apply_lowp(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* G16,
-                              const float* gsc, float alpha, int prec, int* err, cudaStream_t s, int variant = 0);
-// G16 = G / gsc[e] in 16-bit (FP16: gsc[e] a power of two, largest |G16| in [0.5, 1); BF16: no scale),
-// in the layout launch_apply_lowp reads (3D: point-major [e][q][6]; 2D: [e][3][q]).
-cudaError_t launch_pack_g16(const double* G, void* G16, float* gsc, long long nelem, int nc, int np, int dim,
-                            int prec, cudaStream_t s);
+// The operator of the mixed V-cycle, y += alpha * A x with FP32 vectors and arithmetic (the pencil
+// form of pencil.cuh) and geometric factors Glow in precision prec: HMG_PREC_FP32, or 16 bits
+// (HMG_PREC_FP16 with the per-element power-of-two scales gsc, HMG_PREC_BF16 unscaled), in the
+// grouped layout launch_pack_low writes (low_factor_bytes bytes; allocate >= 16 bytes more for
+// the L2 prefetch's rounding). variant 0 loads a thread's factors one phase before the pointwise
+// product, 1 before the first phase (small orders; as 0 otherwise), 2 at their use; setup picks
+// one per level by timing.
+constexpr int kApplyLowVariants = 3;
+size_t low_factor_bytes(const Mesh& m, int prec);
+cudaError_t launch_apply_low(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* Glow,
+                             const float* gsc, float alpha, int prec, cudaStream_t s, int variant = 0);
+// Glow (zero-filled beforehand) from G [E][NC][NP] in FP64; FP16 also writes gsc[e].
+cudaError_t launch_pack_low(const double* G, void* Glow, float* gsc, const Mesh& m, int prec, cudaStream_t s);
 
 // Geometry, stage 1: Gauss-point coordinates and Jacobians into the stage buffer
 // J [E][dim*(dim+1)][NP], from the warp map (coords = nullptr) or given node coordinates

@@ -1,10 +1,10 @@
 // Reduced-precision operator apply of the mixed V-cycle, "pencil" form: y += alpha * A x with
-// FP32 vectors and arithmetic and geometric factors stored in FP32, FP16 (power-of-two scale per
+// FP32 vectors and arithmetic, the geometric factors stored in FP32, FP16 (power-of-two scale per
 // element) or BF16 (paper Sec. 2.3 matrix-free apply, sum factorization).
 //
-// This operator is bound by memory traffic (the factors: 24 or 12 bytes per Gauss point), so
-// the kernel is shaped to issue as few instructions per flop as possible and to keep enough
-// loads in flight, not for tensor cores: one thread owns one 1D line of an element in every
+// This operator is bound by memory traffic (the factors: 24 or 12 bytes per Gauss point), so the
+// kernel is shaped to issue few instructions per flop and to keep every memory path busy with
+// whole transactions, not for tensor cores: one thread owns one 1D line of an element in every
 // direction (N^{d-1} threads per element, EPB elements per block, one tile per block), so every
 // index is fixed per thread before the first phase and the unrolled contractions see compile-
 // time offsets from a per-thread base, the 1D tables as uniform kernel-parameter operands and the
@@ -15,10 +15,15 @@
 //   y-lines add D_y^T v_y; x-lines add D_x^T v_x and apply B_x^T; y-lines B_y^T; z-lines B_z^T and
 //   scatter-add to y. Eight block barriers per tile.
 //   2D: the same with x/y lines and four barriers.
-// Tiles use a j-pitch of N rounded up to an odd number so that the x-line accesses of a warp hit
-// distinct shared-memory banks. GPRE loads a thread's factors into registers before the first
-// phase (small orders); otherwise they are read when needed, after a bulk L2 prefetch of the
-// block's factor slab at the start.
+// Lanes run over the block's elements first (element = thread mod EPB, line = thread / EPB), and
+// the tile pitches (PJ, PK, element stride EP) are chosen per order so that the lanes of a warp
+// address distinct shared-memory banks in all line orientations. The factors are stored grouped
+// by block, element innermost ([group][component][point][element]), so that a warp's factor load
+// is one contiguous run; consecutive elements of a group are consecutive in x, so the gather and
+// the scatter of a warp also touch runs of consecutive nodes. A thread's factors are loaded into
+// registers one phase before the pointwise product (after a bulk L2 prefetch of the block's factor
+// slab at the start), before the first phase (small orders), or at their use: three variants
+// that trade load latency against registers, chosen per level by timing.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -31,16 +36,62 @@
 
 namespace hmg {
 
+// Elements per block and tile pitches of the pencil form, per dimension and order: the smallest
+// shared-memory tiles whose warp accesses are free of bank conflicts (or nearly so) with about
+// 100-500 threads per block.
+struct PencilShape {
+  int epb, pj, pk, ep;
+};
+__host__ __device__ constexpr PencilShape pencil_shape(int dim, int n) {
+  if (dim == 3) {
+    switch (n) {
+      case 2: return {32, 2, 4, 9};
+      case 3: return {32, 3, 9, 27};
+      case 4: return {8, 5, 20, 84};
+      case 5: return {16, 5, 25, 126};
+      case 6: return {8, 7, 42, 252};
+      case 7: return {8, 7, 51, 364};
+      case 8: return {4, 9, 72, 584};
+      case 9: return {4, 9, 81, 744};
+      case 10: return {4, 13, 130, 1304};
+      case 11: return {4, 11, 123, 1368};
+      case 12: return {2, 13, 156, 1872};
+      case 13: return {3, 13, 173, 2251};
+      case 14: return {2, 17, 238, 3344};
+      case 15: return {2, 17, 255, 3856};
+      case 16: return {2, 17, 272, 4368};
+      default: return {1, 17, 289, 4913};
+    }
+  }
+  switch (n) {
+    case 2: return {64, 2, 0, 5};
+    case 3: return {32, 3, 0, 9};
+    case 4: return {32, 4, 0, 17};
+    case 5: return {32, 5, 0, 25};
+    case 6: return {16, 7, 0, 42};
+    case 7: return {32, 7, 0, 49};
+    case 8: return {16, 9, 0, 74};
+    case 9: return {32, 9, 0, 81};
+    case 10: return {16, 11, 0, 110};
+    case 11: return {32, 11, 0, 121};
+    case 12: return {8, 13, 0, 156};
+    case 13: return {32, 13, 0, 169};
+    case 14: return {16, 15, 0, 210};
+    case 15: return {32, 15, 0, 225};
+    case 16: return {8, 17, 0, 276};
+    default: return {16, 17, 0, 290};
+  }
+}
+
 template <int DIM, int N>
 struct PencilCfg {
+  static constexpr PencilShape SH = pencil_shape(DIM, N);
   static constexpr int NL = DIM == 3 ? N * N : N;           // lines per direction per element
   static constexpr int NP = DIM == 3 ? N * N * N : N * N;   // points per element
   static constexpr int NC = DIM == 3 ? 6 : 3;
-  static constexpr int PJ = (N % 2 == 0) ? N + 1 : N;       // j pitch (odd)
-  static constexpr int PK = N * PJ;                          // k pitch (3D)
-  static constexpr int EP = DIM == 3 ? N * PK : N * PJ;      // floats per element tile
-  static constexpr int EPB0 = 128 / NL;
-  static constexpr int EPB = (EPB0 >= 1 && EPB0 * NL >= 120) ? EPB0 : (256 / NL >= 1 ? 256 / NL : 1);
+  static constexpr int EPB = SH.epb, PJ = SH.pj, PK = SH.pk, EP = SH.ep;
+  static_assert(PJ >= N && (DIM == 2 || (PK >= N * PJ && EP >= N * PK)) && (DIM == 3 || EP >= N * PJ),
+                "tile pitches must not overlap");
   static constexpr int LINES = EPB * NL;
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr int NBUF = DIM == 3 ? 4 : 3;
@@ -49,104 +100,114 @@ struct PencilCfg {
   static constexpr bool PRE_OK = NC * N <= 42;
 };
 
-// The NC factors of point q of element e, as FP32. FP32: [e][NC][NP]; 16-bit: 3D point-major
-// [e][NP][6] (three 32-bit words), 2D [e][3][NP]; FP16 values times the element's scale.
-template <int DIM, int N, typename GT, typename T>
-__device__ __forceinline__ void load_g(const GT* __restrict__ G, long long e, int q, float sc, T* g) {
-  constexpr int NP = PencilCfg<DIM, N>::NP, NC = PencilCfg<DIM, N>::NC;
-  if constexpr (std::is_same<GT, float>::value || std::is_same<GT, double>::value) {
-    const GT* p = G + e * NC * NP + q;
+// Values of the grouped factor layout of one level (elements padded to whole groups of EPB).
+inline size_t pencil_factor_values(int dim, int n, long long nelem) {
+  const PencilShape s = pencil_shape(dim, n);
+  const long long groups = (nelem + s.epb - 1) / s.epb;
+  const long long np = dim == 3 ? (long long)n * n * n : (long long)n * n;
+  return (size_t)(groups * s.epb * (dim == 3 ? 6 : 3) * np);
+}
+
+// The NC factors of point q of element slot el of group g, as FP32. FP32: [g][NC][NP][EPB];
+// 16-bit, 3D: pairs of components as 32-bit words [g][3][NP][EPB]; 16-bit, 2D: [g][3][NP][EPB];
+// FP16 values times the element's scale.
+template <int DIM, int N, typename GT>
+__device__ __forceinline__ void load_g(const GT* __restrict__ G, long long g, int el, int q, float sc, float* v) {
+  using C = PencilCfg<DIM, N>;
+  constexpr int NP = C::NP, NC = C::NC, EPB = C::EPB;
+  if constexpr (std::is_same<GT, float>::value) {
+    const float* p = G + (g * NC * NP + q) * EPB + el;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) g[c] = __ldg(p + c * NP);
+    for (int c = 0; c < NC; ++c) v[c] = __ldg(p + (long long)c * NP * EPB);
   } else if constexpr (DIM == 3) {
-    const unsigned* p = reinterpret_cast<const unsigned*>(G + (e * NP + q) * 6);
+    const unsigned* p = reinterpret_cast<const unsigned*>(G) + (g * 3 * NP + q) * EPB + el;
 #pragma unroll
     for (int w = 0; w < 3; ++w) {
-      const unsigned v = __ldg(p + w);
+      const unsigned u = __ldg(p + (long long)w * NP * EPB);
       if constexpr (std::is_same<GT, __half>::value) {
-        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&v));
-        g[2 * w] = f.x * sc;
-        g[2 * w + 1] = f.y * sc;
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+        v[2 * w] = f.x * sc;
+        v[2 * w + 1] = f.y * sc;
       } else {
-        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v));
-        g[2 * w] = f.x;
-        g[2 * w + 1] = f.y;
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+        v[2 * w] = f.x;
+        v[2 * w + 1] = f.y;
       }
     }
   } else {
-    const GT* p = G + e * 3 * NP + q;
+    const GT* p = G + (g * 3 * NP + q) * EPB + el;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      if constexpr (std::is_same<GT, __half>::value) g[c] = __half2float(p[c * NP]) * sc;
-      else g[c] = __bfloat162float(p[c * NP]);
+      if constexpr (std::is_same<GT, __half>::value) v[c] = __half2float(p[(long long)c * NP * EPB]) * sc;
+      else v[c] = __bfloat162float(p[(long long)c * NP * EPB]);
     }
   }
 }
 
 // out[i] = sum_m M[i*N + m] in[m] (TRN: M[m*N + i]), M a parameter-space table
-template <int N, bool TRN, typename T>
-__device__ __forceinline__ void mat1d(const T* __restrict__ M, const T* in, T* out) {
+template <int N, bool TRN>
+__device__ __forceinline__ void mat1d(const float* __restrict__ M, const float* in, float* out) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T s = (TRN ? M[i] : M[i * N]) * in[0];
+    float s = (TRN ? M[i] : M[i * N]) * in[0];
 #pragma unroll
-    for (int m = 1; m < N; ++m) s = fma(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
+    for (int m = 1; m < N; ++m) s = fmaf(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
     out[i] = s;
   }
 }
 // out[i] = acc[i] + sum_m M[m*N + i] in[m]
-template <int N, typename T>
-__device__ __forceinline__ void mat1d_t_acc(const T* __restrict__ M, const T* in, const T* acc, T* out) {
+template <int N>
+__device__ __forceinline__ void mat1d_t_acc(const float* __restrict__ M, const float* in, const float* acc,
+                                            float* out) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    T s = acc[i];
+    float s = acc[i];
 #pragma unroll
-    for (int m = 0; m < N; ++m) s = fma(M[m * N + i], in[m], s);
+    for (int m = 0; m < N; ++m) s = fmaf(M[m * N + i], in[m], s);
     out[i] = s;
   }
 }
 
-// Byte range [lo, hi) rounded out to 16 bytes, prefetched into L2 by one bulk operation (the
-// buffer holds >= 16 bytes of tail padding, so the rounded end stays inside the allocation).
+// Byte range [p, p + bytes) rounded out to 16 bytes and prefetched into L2 by bulk operations
+// (the buffer holds >= 16 bytes of tail padding, so the rounded end stays inside the allocation).
 __device__ __forceinline__ void bulk_prefetch_l2(const void* p, size_t bytes) {
   const uintptr_t lo = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
   const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~(uintptr_t)15;
-  uintptr_t a = lo;
-  while (a < hi) {  // one operation moves less than 2^20 bytes; slabs here are far smaller
+  for (uintptr_t a = lo; a < hi;) {
     const uint32_t n = (uint32_t)((hi - a) < (1u << 19) ? (hi - a) : (1u << 19));
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"(n) : "memory");
     a += n;
   }
 }
 
-// One tile: the EPB elements e0, e0 + 1, ... of mesh m (those below m.nelem), y += alpha A x, in
-// value type T (float, or double for the batched FP64 operator) with factors of type GT; `smem`
-// holds PencilCfg::SMEM bytes per value byte of float (scaled by sizeof(T) / 4).
-template <int DIM, int N, typename T, typename GT, bool GPRE>
-__device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restrict__ y, const GT* __restrict__ G,
-                                            const float* __restrict__ gsc, const Mesh& m, const Tab<N, T>& tab,
-                                            const T alpha, const long long e0, T* sm_pencil) {
+// One tile: the group g of EPB elements e0 = g * EPB, ... of mesh m (those below m.nelem),
+// y += alpha A x; `sm` holds PencilCfg::SMEM bytes.
+template <int DIM, int N, typename GT, int GM>
+__device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* __restrict__ y,
+                                            const GT* __restrict__ G, const float* __restrict__ gsc, const Mesh& m,
+                                            const Tab<N, float>& tab, const float alpha, const long long g,
+                                            float* sm) {
   using C = PencilCfg<DIM, N>;
   constexpr int NL = C::NL, NP = C::NP, NC = C::NC, PJ = C::PJ, PK = C::PK, EP = C::EP, EPB = C::EPB;
-  constexpr int TS = EPB * EP;       // values per buffer
-  T* S = sm_pencil;                  // interpolation passes (forward and transposed)
-  T* U = S + TS;                     // u at the Gauss points, later the transposed-derivative sum W
-  T* GX = U + TS;                    // u_x, later v_x
-  T* GY = GX + TS;                   // u_y, later v_y (3D)
+  constexpr int TS = EPB * EP;       // floats per buffer
+  float* S = sm;                     // interpolation passes (forward and transposed)
+  float* U = S + TS;                 // u at the Gauss points, later the transposed-derivative sum W
+  float* GX = U + TS;                // u_x, later v_x
+  float* GY = GX + TS;               // u_y, later v_y (3D)
   const int t = threadIdx.x;
-  const int el = t / NL;
-  const int l = t - el * NL;
-  const long long e = e0 + el;
+  const int el = t % EPB;            // element slot of the group
+  const int l = t / EPB;             // line of the element
   // threads beyond the last line (the rest of the last warp) run every phase on element 0's tile
   // with their shared-memory stores switched off, so that all threads reach the same barriers
-  const bool act = t < C::LINES;
+  const bool act = l < NL;
+  const long long e0 = g * EPB;
+  const long long e = e0 + el;
   const bool valid = act && e < m.nelem;
-  const int a = l % N, b = DIM == 3 ? l / N : 0;   // line coordinates
+  const int a = act ? l % N : 0, b = (DIM == 3 && act) ? l / N : 0;   // line coordinates
   const int eb = act ? el * EP : 0;
   if (t == 0) {
-    const long long ne = (m.nelem - e0) < EPB ? (m.nelem - e0) : EPB;
-    const size_t gbytes = sizeof(GT) * (size_t)NC * NP;
-    bulk_prefetch_l2(reinterpret_cast<const char*>(G) + e0 * gbytes, ne * gbytes);
+    const size_t gbytes = sizeof(GT) * (size_t)NC * NP * EPB;
+    bulk_prefetch_l2(reinterpret_cast<const char*>(G) + g * gbytes, gbytes);
   }
   // element position, global node of the line's first node, and boundary masks
   long long nb = 0;
@@ -175,21 +236,23 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   const int ox = eb + a * PJ + (DIM == 3 ? b * PK : 0);
   const int oy = eb + a + (DIM == 3 ? b * PK : 0);
   const int oz = eb + a + b * PJ;
+  auto qidx = [&](int k) { return DIM == 3 ? a + b * N + k * N * N : a + k * N; };
 
-  T gpre[GPRE ? NC * N : 1];
+  constexpr bool GPRE = GM == 1;       // factors loaded before the first phase
+  constexpr bool GAHEAD = GM == 0;     // ... one phase before the pointwise product
+  float gpre[GPRE ? NC * N : 1];
   if constexpr (GPRE) {
     if (valid) {
 #pragma unroll
-      for (int k = 0; k < N; ++k)
-        load_g<DIM, N, GT, T>(G, e, DIM == 3 ? a + b * N + k * N * N : a + k * N, sc, gpre + k * NC);
+      for (int k = 0; k < N; ++k) load_g<DIM, N, GT>(G, g, el, qidx(k), sc, gpre + k * NC);
     }
   }
-  T v[N], w[N];
+  float v[N], w[N];
   // ---- gather along the thread's line (z in 3D, y in 2D) and interpolate along it
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const bool bd = bd_lat | ((k == 0) & f_lo) | ((k == N - 1) & f_hi);
-    v[k] = (valid && !bd) ? __ldg(x + nb + k * sline) : T(0);
+    v[k] = (valid && !bd) ? __ldg(x + nb + k * sline) : 0.0f;
   }
   mat1d<N, false>(tab.B, v, w);
   if (DIM == 3) {
@@ -221,7 +284,20 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
     if (act) GX[ox + k] = v[k];
   }
   __syncthreads();
-  T uz[N];
+  // the thread's factors: loaded here (unless GPRE loaded them at the start), one phase before
+  // the pointwise product needs them, so that their latency overlaps the derivative phase
+  float gl[GAHEAD ? NC * N : 1];
+  if constexpr (GAHEAD) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), sc, gl + k * NC);
+      else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) gl[k * NC + c] = 0.0f;
+      }
+    }
+  }
+  float uz[N];
   if (DIM == 3) {
     // y-lines: u_y; z-lines: u_z (kept in registers)
 #pragma unroll
@@ -243,35 +319,33 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   // ---- the thread's line (z in 3D, y in 2D): v = G grad u at its points, then D^T along it
   const int ol = DIM == 3 ? oz : oy;
   constexpr int SL = DIM == 3 ? PK : PJ;
-  T vl[N];
+  float vl[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    T g[NC];
-    if constexpr (GPRE) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c) g[c] = gpre[k * NC + c];
-    } else {
-      if (valid) load_g<DIM, N, GT, T>(G, e, DIM == 3 ? a + b * N + k * N * N : a + k * N, sc, g);
+    float gj[GM == 2 ? NC : 1];
+    if constexpr (GM == 2) {    // factors read at their use
+      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), sc, gj);
       else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) g[c] = T(0);
+        for (int c = 0; c < NC; ++c) gj[c] = 0.0f;
       }
     }
-    const T ux = GX[ol + k * SL];
+    const float* gv = GM == 2 ? gj : (GPRE ? gpre + k * NC : gl + k * NC);
+    const float ux = GX[ol + k * SL];
     if (DIM == 3) {
-      const T uy = GY[ol + k * SL];
-      if (act) GX[ol + k * SL] = g[0] * ux + g[1] * uy + g[2] * uz[k];
-      if (act) GY[ol + k * SL] = g[1] * ux + g[3] * uy + g[4] * uz[k];
-      vl[k] = g[2] * ux + g[4] * uy + g[5] * uz[k];
+      const float uy = GY[ol + k * SL];
+      if (act) GX[ol + k * SL] = gv[0] * ux + gv[1] * uy + gv[2] * uz[k];
+      if (act) GY[ol + k * SL] = gv[1] * ux + gv[3] * uy + gv[4] * uz[k];
+      vl[k] = gv[2] * ux + gv[4] * uy + gv[5] * uz[k];
     } else {
-      if (act) GX[ol + k * SL] = g[0] * ux + g[1] * uz[k];
-      vl[k] = g[1] * ux + g[2] * uz[k];
+      if (act) GX[ol + k * SL] = gv[0] * ux + gv[1] * uz[k];
+      vl[k] = gv[1] * ux + gv[2] * uz[k];
     }
   }
   mat1d<N, true>(tab.D, vl, w);
 #pragma unroll
   for (int k = 0; k < N; ++k)
-      if (act) U[ol + k * SL] = w[k];
+    if (act) U[ol + k * SL] = w[k];
   __syncthreads();
   if (DIM == 3) {
     // y-lines: W += D_y^T v_y
@@ -296,7 +370,7 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   mat1d<N, true>(tab.B, w, v);
 #pragma unroll
   for (int k = 0; k < N; ++k)
-      if (act) S[ox + k] = v[k];
+    if (act) S[ox + k] = v[k];
   __syncthreads();
   if (DIM == 3) {
     // y-lines: B_y^T
@@ -321,295 +395,81 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   }
 }
 
-template <int DIM, int N, typename GT, bool GPRE>
+template <int DIM, int N, typename GT, int GM>
 __global__ void __launch_bounds__(PencilCfg<DIM, N>::THREADS)
 k_apply_pencil(const float* __restrict__ x, float* __restrict__ y, const GT* __restrict__ G,
                const float* __restrict__ gsc, const Mesh m, const __grid_constant__ Tab<N, float> tab,
                const float alpha) {
   extern __shared__ __align__(16) float sm_pencil[];
-  pencil_tile<DIM, N, float, GT, GPRE>(x, y, G, gsc, m, tab, alpha, (long long)blockIdx.x * PencilCfg<DIM, N>::EPB,
-                                       sm_pencil);
+  pencil_tile<DIM, N, GT, GM>(x, y, G, gsc, m, tab, alpha, (long long)blockIdx.x, sm_pencil);
 }
 
-// ---------------------------------------------------------------------------------------
-// 3D "plane" form for small orders (N = p + 1 <= 5): a thread owns a whole 2D plane of an
-// element and applies the two 1D tables of that plane's directions in registers, so only the
-// changes of plane orientation go through shared memory (14 N^3 shared accesses per element
-// against 23 N^3 for the line form, four barriers). Threads alternate between yz-planes
-// (fixed x index: gather, z-interpolation, the pointwise factor product, the z and y transposed
-// derivatives, the last transposed interpolation and the scatter, all along consecutive nodes in
-// x across the lanes) and xy-planes (fixed z index: the x interpolation and derivative, the y
-// derivative, the x transposed derivative and the x and y transposed interpolations):
-//   yz(i):  x -> B_y, B_z                       -> S
-//   xy(kq): S -> B_x = u, D_x u, D_y u          -> U, GX, S
-//   yz(iq): U -> D_z u; G grad u; D_y^T v_y + D_z^T v_z -> U, v_x -> GX
-//   xy(k):  U, GX -> + D_x^T v_x, B_x^T, B_y^T  -> S
-//   yz(i):  S -> B_z^T, scatter-add
-// Element tiles use the pitches j -> N, k -> PK with PK = 1 (mod 32) and an element stride of
-// N PK = N (mod 32), so that the lanes of a warp, which run over (element, plane index),
-// address 32 consecutive banks in both orientations.
-// ---------------------------------------------------------------------------------------
-constexpr bool plane_banks_ok(int N, int PK, int EPB, int threads) {
-  const int EP = N * PK;
-  for (int w = 0; w * 32 < threads; ++w) {
-    for (int orient = 0; orient < 2; ++orient) {
-      unsigned used = 0u;
-      for (int lane = 0; lane < 32; ++lane) {
-        const int t = 32 * w + lane;
-        if (t >= EPB * N) continue;
-        const int el = t / N, r = t % N;
-        const int addr = el * EP + (orient == 0 ? r : r * PK);
-        const unsigned bit = 1u << (addr % 32);
-        if (used & bit) return false;
-        used |= bit;
-      }
-    }
-  }
-  return true;
-}
-constexpr int plane_pk(int N, int EPB, int threads) {
-  for (int pk = N * N; pk < N * N + 64; ++pk)
-    if (plane_banks_ok(N, pk, EPB, threads)) return pk;
-  return N * N;
-}
-
-template <int N>
-struct PlaneCfg {
-  static constexpr int NP = N * N * N, NC = 6;
-  static constexpr int EPB = 128 / N;
-  static constexpr int THREADS = (EPB * N + 31) / 32 * 32;
-  static constexpr int PJ = N;
-  static constexpr int PK = plane_pk(N, EPB, THREADS);
-  static constexpr int EP = N * PK;
-  static constexpr size_t SMEM = (size_t)3 * EPB * EP * sizeof(float);
-};
-
-template <int N, typename GT>
-__global__ void __launch_bounds__(PlaneCfg<N>::THREADS, 4)
-k_apply_plane(const float* __restrict__ x, float* __restrict__ y, const GT* __restrict__ G,
-              const float* __restrict__ gsc, const Mesh m, const __grid_constant__ Tab<N, float> tab,
-              const float alpha) {
-  using C = PlaneCfg<N>;
-  constexpr int NP = C::NP, NC = C::NC, PJ = C::PJ, PK = C::PK, EP = C::EP, EPB = C::EPB;
-  extern __shared__ __align__(16) float sm_plane[];
-  float* S = sm_plane;
-  float* U = S + EPB * EP;
-  float* GX = U + EPB * EP;
-  const int t = threadIdx.x;
-  const int el = t / N, r = t - (t / N) * N;   // element of the block, plane index
-  const bool act = t < EPB * N;
-  const long long e0 = (long long)blockIdx.x * EPB;
-  const long long e = e0 + el;
-  const bool valid = act && e < m.nelem;
-  const int eb = act ? el * EP : 0;
-  if (t == 0) {
-    const long long ne = (m.nelem - e0) < EPB ? (m.nelem - e0) : EPB;
-    const size_t gbytes = sizeof(GT) * (size_t)NC * NP;
-    bulk_prefetch_l2(reinterpret_cast<const char*>(G) + e0 * gbytes, ne * gbytes);
-  }
-  long long base = 0;
-  int fl = 0;
-  if (valid) {
-    const int ex = (int)(e % m.E[0]);
-    const long long rr = e / m.E[0];
-    const int ey = (int)(rr % m.E[1]);
-    const int ez = (int)(rr / m.E[1]);
-    base = ((long long)ez * m.p * m.Nn[1] + (long long)ey * m.p) * m.Nn[0] + (long long)ex * m.p;
-    fl = (ex == 0) | ((ex == m.E[0] - 1) << 1) | ((ey == 0) << 2) | ((ey == m.E[1] - 1) << 3) |
-         ((ez == 0) << 4) | ((ez == m.E[2] - 1) << 5);
-  }
-  const long long nx = m.Nn[0], nxy = m.Nn[0] * m.Nn[1];
-  // yz-plane of this thread: x index i = r; its nodes' boundary mask
-  const bool bd_x = ((r == 0) & (fl & 1)) | ((r == N - 1) & ((fl >> 1) & 1));
-  auto bd_of = [&](int j, int k) -> bool {
-    return bd_x | ((j == 0) & ((fl >> 2) & 1)) | ((j == N - 1) & ((fl >> 3) & 1)) | ((k == 0) & ((fl >> 4) & 1)) |
-           ((k == N - 1) & ((fl >> 5) & 1));
-  };
-  const float sc = (gsc != nullptr && valid) ? gsc[e] : 1.0f;
-  const int oyz = eb + r;             // yz-plane (i = r): + j * PJ + k * PK
-  const int oxy = eb + r * PK;        // xy-plane (k = r): + i + j * PJ
-
-  float A[N][N], Bv[N][N];
-  // ---- yz(i): gather, B_y, B_z -> S
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-      A[j][k] = (valid && !bd_of(j, k)) ? __ldg(x + base + r + j * nx + k * nxy) : 0.0f;
-#pragma unroll
-  for (int jq = 0; jq < N; ++jq)
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      float s = tab.B[jq * N] * A[0][k];
-#pragma unroll
-      for (int j = 1; j < N; ++j) s = fmaf(tab.B[jq * N + j], A[j][k], s);
-      Bv[jq][k] = s;
-    }
-#pragma unroll
-  for (int jq = 0; jq < N; ++jq)
-#pragma unroll
-    for (int kq = 0; kq < N; ++kq) {
-      float s = tab.B[kq * N] * Bv[jq][0];
-#pragma unroll
-      for (int k = 1; k < N; ++k) s = fmaf(tab.B[kq * N + k], Bv[jq][k], s);
-      if (act) S[oyz + jq * PJ + kq * PK] = s;
-    }
-  __syncthreads();
-  // ---- xy(kq): u = B_x, then D_x u -> GX, D_y u -> S (this plane's own region), u -> U
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int jq = 0; jq < N; ++jq) A[i][jq] = S[oxy + i + jq * PJ];
-#pragma unroll
-  for (int iq = 0; iq < N; ++iq)
-#pragma unroll
-    for (int jq = 0; jq < N; ++jq) {
-      float s = tab.B[iq * N] * A[0][jq];
-#pragma unroll
-      for (int i = 1; i < N; ++i) s = fmaf(tab.B[iq * N + i], A[i][jq], s);
-      Bv[iq][jq] = s;
-      if (act) U[oxy + iq + jq * PJ] = s;
-    }
-#pragma unroll
-  for (int iq = 0; iq < N; ++iq)
-#pragma unroll
-    for (int jq = 0; jq < N; ++jq) {
-      float sx = tab.D[iq * N] * Bv[0][jq], sy = tab.D[jq * N] * Bv[iq][0];
-#pragma unroll
-      for (int m2 = 1; m2 < N; ++m2) {
-        sx = fmaf(tab.D[iq * N + m2], Bv[m2][jq], sx);
-        sy = fmaf(tab.D[jq * N + m2], Bv[iq][m2], sy);
-      }
-      if (act) GX[oxy + iq + jq * PJ] = sx;
-      if (act) S[oxy + iq + jq * PJ] = sy;
-    }
-  __syncthreads();
-  // ---- yz(iq): u_z = D_z u; v = G grad u; W = D_y^T v_y + D_z^T v_z -> U; v_x -> GX
-#pragma unroll
-  for (int jq = 0; jq < N; ++jq)
-#pragma unroll
-    for (int kq = 0; kq < N; ++kq) A[jq][kq] = U[oyz + jq * PJ + kq * PK];
-  float VY[N][N];
-#pragma unroll
-  for (int jq = 0; jq < N; ++jq)
-#pragma unroll
-    for (int kq = 0; kq < N; ++kq) {
-      float uz = tab.D[kq * N] * A[jq][0];
-#pragma unroll
-      for (int k2 = 1; k2 < N; ++k2) uz = fmaf(tab.D[kq * N + k2], A[jq][k2], uz);
-      float g[NC];
-      if (valid) load_g<3, N, GT, float>(G, e, r + N * jq + N * N * kq, sc, g);
-      else {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) g[c] = 0.0f;
-      }
-      const int o = oyz + jq * PJ + kq * PK;
-      const float ux = GX[o], uy = S[o];
-      if (act) GX[o] = g[0] * ux + g[1] * uy + g[2] * uz;
-      VY[jq][kq] = g[1] * ux + g[3] * uy + g[4] * uz;
-      Bv[jq][kq] = g[2] * ux + g[4] * uy + g[5] * uz;   // v_z
-    }
-#pragma unroll
-  for (int jq = 0; jq < N; ++jq)
-#pragma unroll
-    for (int kq = 0; kq < N; ++kq) {
-      float s = 0.0f;
-#pragma unroll
-      for (int m2 = 0; m2 < N; ++m2) {
-        s = fmaf(tab.D[m2 * N + jq], VY[m2][kq], s);
-        s = fmaf(tab.D[m2 * N + kq], Bv[jq][m2], s);
-      }
-      if (act) U[oyz + jq * PJ + kq * PK] = s;
-    }
-  __syncthreads();
-  // ---- xy(k): W += D_x^T v_x; B_x^T; B_y^T -> S
-#pragma unroll
-  for (int iq = 0; iq < N; ++iq)
-#pragma unroll
-    for (int jq = 0; jq < N; ++jq) {
-      A[iq][jq] = U[oxy + iq + jq * PJ];
-      Bv[iq][jq] = GX[oxy + iq + jq * PJ];
-    }
-#pragma unroll
-  for (int iq = 0; iq < N; ++iq)
-#pragma unroll
-    for (int jq = 0; jq < N; ++jq) {
-      float s = A[iq][jq];
-#pragma unroll
-      for (int m2 = 0; m2 < N; ++m2) s = fmaf(tab.D[m2 * N + iq], Bv[m2][jq], s);
-      VY[iq][jq] = s;
-    }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int jq = 0; jq < N; ++jq) {
-      float s = tab.B[i] * VY[0][jq];
-#pragma unroll
-      for (int iq = 1; iq < N; ++iq) s = fmaf(tab.B[iq * N + i], VY[iq][jq], s);
-      A[i][jq] = s;
-    }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      float s = tab.B[j] * A[i][0];
-#pragma unroll
-      for (int jq = 1; jq < N; ++jq) s = fmaf(tab.B[jq * N + j], A[i][jq], s);
-      if (act) S[oxy + i + j * PJ] = s;
-    }
-  __syncthreads();
-  // ---- yz(i): B_z^T and scatter-add
-#pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int kq = 0; kq < N; ++kq) A[j][kq] = S[oyz + j * PJ + kq * PK];
-  if (valid) {
-#pragma unroll
-    for (int j = 0; j < N; ++j)
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        float s = tab.B[k] * A[j][0];
-#pragma unroll
-        for (int kq = 1; kq < N; ++kq) s = fmaf(tab.B[kq * N + k], A[j][kq], s);
-        if (!bd_of(j, k)) atomicAdd(y + base + r + j * nx + k * nxy, alpha * s);
-      }
-  }
-}
-
-// The plane form (3D, N <= kMaxNPlane) with factors of type GT.
-constexpr int kMaxNPlane = 5;
-template <int N, typename GT>
-cudaError_t launch_plane(const Mesh& m, const Basis1D& b, const float* x, float* y, const GT* G, const float* gsc,
-                         float alpha, cudaStream_t s) {
-  using C = PlaneCfg<N>;
+// The pencil-form apply with factors of type GT in the grouped layout: one group per block.
+// variant: 0 factors loaded one phase before the pointwise product, 1 before the first phase
+// (orders with few factors per line; else as 0), 2 at their use.
+template <int DIM, int N, typename GT, int GM>
+cudaError_t launch_pencil_gm(const Mesh& m, const Basis1D& b, const float* x, float* y, const GT* G,
+                             const float* gsc, float alpha, cudaStream_t s) {
+  using C = PencilCfg<DIM, N>;
   const long long blocks = (m.nelem + C::EPB - 1) / C::EPB;
   if (blocks == 0) return cudaSuccess;
-  auto kern = k_apply_plane<N, GT>;
+  auto kern = k_apply_pencil<DIM, N, GT, GM>;
   cudaError_t e = ensure_smem(kern, C::SMEM);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(x, y, G, gsc, m, make_tab<N, float>(b), alpha);
   return counted(cudaGetLastError());
 }
-
-// The pencil-form apply with factors of type GT: one tile of EPB elements per block.
 template <int DIM, int N, typename GT>
 cudaError_t launch_pencil(const Mesh& m, const Basis1D& b, const float* x, float* y, const GT* G, const float* gsc,
-                          float alpha, bool pre, cudaStream_t s) {
-  using C = PencilCfg<DIM, N>;
-  const long long blocks = (m.nelem + C::EPB - 1) / C::EPB;
-  if (blocks == 0) return cudaSuccess;
-  if (pre && C::PRE_OK) {
-    auto kern = k_apply_pencil<DIM, N, GT, C::PRE_OK>;
-    cudaError_t e = ensure_smem(kern, C::SMEM);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(x, y, G, gsc, m, make_tab<N, float>(b), alpha);
-  } else {
-    auto kern = k_apply_pencil<DIM, N, GT, false>;
-    cudaError_t e = ensure_smem(kern, C::SMEM);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(x, y, G, gsc, m, make_tab<N, float>(b), alpha);
+                          float alpha, int variant, cudaStream_t s) {
+  if (variant == 2) return launch_pencil_gm<DIM, N, GT, 2>(m, b, x, y, G, gsc, alpha, s);
+  if (variant == 1 && PencilCfg<DIM, N>::PRE_OK) return launch_pencil_gm<DIM, N, GT, 1>(m, b, x, y, G, gsc, alpha, s);
+  return launch_pencil_gm<DIM, N, GT, 0>(m, b, x, y, G, gsc, alpha, s);
+}
+
+// Grouped reduced-precision factors of one element per block from G[e][c][q] (FP64): FP32 as
+// they are; FP16 divided by gsc[e], the power of two that puts the element's largest |G| / gsc in
+// [0.5, 1); BF16 unscaled (gsc = nullptr). Layouts as load_g reads them; the buffer is zero-filled
+// beforehand, so the padding elements of the last group stay zero.
+template <typename GT>
+__global__ void k_pack_grouped(const double* __restrict__ G, GT* __restrict__ out, float* __restrict__ gsc,
+                               long long nelem, int dim, int np, int epb) {
+  const long long e = blockIdx.x;
+  if (e >= nelem) return;
+  const int nc = dim == 3 ? 6 : 3;
+  const int per_elem = nc * np;
+  const double* ge = G + e * per_elem;
+  double sc = 1.0;
+  if (gsc != nullptr) {
+    __shared__ double red[32];
+    double amax = 0.0;
+    for (int i = threadIdx.x; i < per_elem; i += blockDim.x) amax = fmax(amax, fabs(ge[i]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (threadIdx.x == 0) red[0] = v;
+    }
+    __syncthreads();
+    int ex = 0;
+    if (red[0] > 0.0) frexp(red[0], &ex);
+    sc = ldexp(1.0, ex);
+    if (threadIdx.x == 0) gsc[e] = (float)sc;
   }
-  return counted(cudaGetLastError());
+  const long long g = e / epb;
+  const int el = (int)(e - g * epb);
+  for (int i = threadIdx.x; i < per_elem; i += blockDim.x) {
+    const int c = i / np, q = i - c * np;
+    long long idx;
+    if (std::is_same<GT, float>::value || dim == 2) {
+      idx = ((g * nc + c) * np + q) * epb + el;
+    } else {  // 3D 16-bit: component pairs (2w, 2w + 1) in one 32-bit word
+      idx = (((g * 3 + c / 2) * np + q) * epb + el) * 2 + (c & 1);
+    }
+    out[idx] = (GT)(float)(ge[i] / sc);
+  }
 }
 
 }  // namespace hmg

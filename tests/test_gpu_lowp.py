@@ -1,15 +1,14 @@
-"""FP16 / BF16 V-cycle: the tensor-core operator against the FP64 oracle, and FP64 PCG /
-MG-refinement solves whose V-cycle applies it (FP64 fine residual, inner products and
+"""FP16 / BF16 V-cycle: the operator with 16-bit geometric factors against the FP64 oracle, and
+FP64 PCG / MG-refinement solves whose V-cycle applies it (FP64 fine residual, inner products and
 coarsest solve).
 
-Tolerance of the 16-bit apply, from its arithmetic: a term of y_i = sum_e K^T G K x passes
-through k roundings to the 16-bit format (unit roundoff u = 2^-11 for FP16, 2^-8 for BF16):
-x, the d-1 stored forward intermediates, G, v = G grad u, the d-1 stored transposed
-intermediates, and the 2d 1D-table entries of its factor chain, so k = 4d + 1 (13 in 3D, 9 in
-2D); the power-of-two scales are exact and the FP32 accumulation adds O(N 2^-24). To first
-order |y16_i - y_i| <= k u S_i with S = sum_e |K|^T |G| |K| |x| (absolute values of every
-factor), which the test evaluates with the oracle's basis tables and geometry; it allows
-(k + 1) u S_i."""
+Tolerance of the 16-bit apply, from its arithmetic: the factors G are the only values rounded to
+16 bits (unit roundoff u = 2^-11 for FP16, 2^-8 for BF16; the FP16 power-of-two scales are exact,
+and a factor in FP16's subnormal range after scaling is off by at most 2^-25 of its element's
+largest factor); x, the intermediates and the accumulation stay in FP32 (2^-24 per operation, a few
+dozen operations per term). To first order |y16_i - y_i| <= u S_i + c 2^-24 S_i with
+S = sum_e |K|^T |G| |K| |x| (absolute values of every factor), which the test evaluates with the
+oracle's basis tables and geometry; it allows 2 u S_i + 64 2^-24 S_i."""
 import numpy as np
 import pytest
 
@@ -82,9 +81,9 @@ def test_lowp_apply_within_rounding_bound(hmg, case, prec):
     xr[d.boundary] = 0.0
     ref = d.to_full(d.stiffness() @ xr[d.interior])
     S = abs_bound_scale(d, xr)
-    k = 4 * case["dim"] + 1
     err = np.abs(y - ref)[d.interior]
-    assert np.all(err <= (k + 1) * U16[prec] * S[d.interior] + 1e-30), float(np.max(err / S[d.interior]))
+    bound = (2 * U16[prec] + 64 * 2.0 ** -24) * S[d.interior] + 1e-30
+    assert np.all(err <= bound), float(np.max(err / S[d.interior]))
     # and it is a real 16-bit result, not an FP32 one in disguise: the error is well above FP32 rounding
     assert np.max(err / S[d.interior]) > 2.0 ** -20
     assert np.all(y[d.boundary] == 0.0)
@@ -92,8 +91,9 @@ def test_lowp_apply_within_rounding_bound(hmg, case, prec):
 
 
 def test_lowp_fp16_scaling_keeps_tiny_and_huge_inputs(hmg):
-    """FP16 scales x per element by a power of two: y(c x) = c y(x) for c = 2^-40 and 2^40 (the
-    scaled 16-bit operands are identical), where unscaled FP16 would flush to zero or overflow."""
+    """FP16 factors carry a power-of-two scale per element and the vectors stay FP32: y(c x) = c y(x)
+    for c = 2^-40 and 2^40 (scaling by a power of two is exact in every operation), where a 16-bit
+    vector operand would flush to zero or overflow."""
     prob = dict(synth.problem(3, (3, 2, 2), 4, warp_amp=0.1, mu_b=1e3, n_hlevels=1, smoother="jacobi"),
                 smooth_prec="fp16")
     P = hmg.Problem(prob)
@@ -106,7 +106,7 @@ def test_lowp_fp16_scaling_keeps_tiny_and_huge_inputs(hmg):
         ys.append(y.double().cpu().numpy() / c)
     assert np.all(np.isfinite(ys[1])) and np.all(np.isfinite(ys[2]))
     top = np.abs(ys[0]).max()
-    # identical 16-bit operands; only the FP32 atomic scatter order may differ between launches
+    # exact scaling; only the FP32 atomic scatter order may differ between launches
     assert np.abs(ys[1] - ys[0]).max() <= 1e-6 * top and np.abs(ys[2] - ys[0]).max() <= 1e-6 * top
     P.close()
 
@@ -116,7 +116,7 @@ SOLVES = [
     (synth.warped_var3d(8, 2, hier="h"), "pcg"),
     (synth.warped_var3d(4, 4, hier="p"), "mg"),
     (synth.problem(2, 16, 6, warp_amp=0.1, mu_b=1e3, hier="p"), "pcg"),
-    (synth.problem(3, 4, 8, warp_amp=0.1, mu_b=1e3, hier="p"), "pcg"),   # p = 8 fine level stays FP32
+    (synth.problem(3, 4, 8, warp_amp=0.1, mu_b=1e3, hier="p"), "pcg"),
 ]
 
 
@@ -124,14 +124,18 @@ SOLVES = [
 @pytest.mark.parametrize("prob,mode", SOLVES, ids=lambda c: str(c)[:60])
 def test_lowp_solve_reaches_fp64_accuracy(hmg, prob, mode, prec):
     """The 16-bit V-cycle inside FP64 PCG (flexible beta) or MG refinement reaches the FP64
-    tolerance: true FP64 residual <= 1e-8 relative, solution equal to the FP64 solve's to the
-    accuracy the residual bound gives, iteration count at most 1.5x + 2 the FP64 one."""
+    tolerance: true FP64 residual <= 1e-8 relative; iteration count within one of the FP64 solve's
+    (FP16) or at most two more (BF16); and, where the oracle's interior system is small enough to
+    factor, the solution within the bound the residual gives against the oracle's exact solution:
+    ||u - u*||_2 <= ||b - A u||_2 / lambda_min(A), A symmetric positive definite."""
+    import scipy.sparse.linalg as spla
+    from oracle import fem
     P64 = hmg.Problem(prob)
     Pl = hmg.Problem(dict(prob, smooth_prec=prec))
     N = P64.ndof(0)
-    f = _t(synth.nodal_field(31, N))
+    fn = synth.nodal_field(31, N)
     b = torch.zeros(N, dtype=torch.float64, device=DEV)
-    P64.rhs(f, b)
+    P64.rhs(_t(fn), b)
     u64 = torch.zeros_like(b)
     ul = torch.zeros_like(b)
     st64, it64, _ = P64.solve(mode, b, u64, rtol=1e-8, maxit=400)
@@ -141,10 +145,20 @@ def test_lowp_solve_reaches_fp64_accuracy(hmg, prob, mode, prec):
     P64.apply(0, ul, r)
     res = float(torch.linalg.norm(b - r) / torch.linalg.norm(b))
     assert res <= 1.05e-8
-    assert it <= 1.5 * it64 + 2
-    rel = float(torch.linalg.norm(ul - u64) / torch.linalg.norm(u64))
-    assert rel < 1e-5
-    print(f"{prec} {mode}: iterations {it} (FP64 {it64}), true residual {res:.2e}, |u - u64|/|u64| {rel:.1e}")
+    assert it64 - 1 <= it <= it64 + (1 if prec == "fp16" else 2), (it, it64)
+    d = fem.Discretization(prob["dim"], prob["nelem"], prob["order"], warp_amp=prob["warp_amp"],
+                           mu_a=prob["mu_a"], mu_b=prob["mu_b"], mu_k=prob["mu_k"])
+    if d.n_interior <= 12000:
+        A = d.stiffness().tocsc()
+        bi = d.rhs(fn)
+        ustar = spla.spsolve(A, bi)
+        lam_min = float(spla.eigsh(A, k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0])
+        ui = ul.cpu().numpy()[d.interior]
+        err = float(np.linalg.norm(ui - ustar))
+        bound = float(np.linalg.norm(bi - A @ ui)) / lam_min
+        assert err <= 1.0001 * bound + 1e-14 * np.linalg.norm(ustar), (err, bound)
+        print(f"{prec} {mode}: |u - u*| {err:.2e} <= {bound:.2e}")
+    print(f"{prec} {mode}: iterations {it} (FP64 {it64}), true residual {res:.2e}")
     P64.close()
     Pl.close()
 
@@ -170,10 +184,10 @@ def test_lowp_graph_and_batched_equal_host_loop(hmg, prec):
     Ph.close()
 
 
-def test_lowp_half_group_variant_within_rounding_bound(tmp_path):
-    """The half-size element-group shape (variant 3, picked by the autotuner on small meshes)
-    passes the same rounding-bound parity: pinned for every case through the decision cache,
-    in a fresh process."""
+def test_lowp_register_variant_within_rounding_bound(tmp_path):
+    """The apply with each thread's 16-bit factors loaded into registers first (variant 1, small
+    orders, picked by the autotuner where faster) passes the same rounding-bound parity: pinned for
+    every case through the decision cache, in a fresh process."""
     import os
     import subprocess
     import sys
@@ -184,7 +198,7 @@ def test_lowp_half_group_variant_within_rounding_bound(tmp_path):
     for case in CASES:
         ne = int(np.prod(case["nelem"]))
         for kind in (2, 3):                      # HMG_PREC_FP16, HMG_PREC_BF16
-            lines.append(f"0 {case['dim']} {case['order']} {ne} {kind} 3")
+            lines.append(f"0 {case['dim']} {case['order']} {ne} {kind} 1")
     cache.write_text("\n".join(lines) + "\n")
     env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

@@ -124,10 +124,10 @@ def test_mixed_vcycle_close_to_fp64_vcycle(hmg):
     P32.close()
 
 
-def test_fp32_warp_group_variant_matches_oracle(tmp_path):
-    """The warp-group FP32 apply (variant 3, orders <= 8, picked by the autotuner where faster)
-    passes the same parity as the block form: pinned for every case through the decision cache,
-    in a fresh process."""
+def test_fp32_register_variant_matches_oracle(tmp_path):
+    """The FP32 apply with each thread's factors loaded into registers first (variant 1, small
+    orders, picked by the autotuner where faster) passes the same parity as variant 0: pinned for
+    every case through the decision cache, in a fresh process."""
     import os
     import subprocess
     import sys
@@ -136,7 +136,7 @@ def test_fp32_warp_group_variant_matches_oracle(tmp_path):
     lines = []
     for case in CASES:
         ne = int(np.prod(case["nelem"]))
-        lines.append(f"0 {case['dim']} {case['order']} {ne} 1 3")   # kind 1 = HMG_PREC_FP32
+        lines.append(f"0 {case['dim']} {case['order']} {ne} 1 1")   # kind 1 = HMG_PREC_FP32
     cache = tmp_path / "tune32.txt"
     cache.write_text("\n".join(lines) + "\n")
     env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))

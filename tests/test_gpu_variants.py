@@ -6,10 +6,11 @@ FP64 sum factorization, variants 0-3 (3 stages the geometric factors by TMA): ev
 operator within 1e-12 relative of the oracle's assembled A (Sec. 2.1, Sec. 2.3's matrix-free
 apply), PCG iteration counts within +-1 of the oracle's (Algorithm 1); at the 16^3 Q4 size of
 the single-solve workload, variants 2 and 3 on sampled rows of the oracle's weak form at element
-vertices, edges, faces and interiors. FP32 variants 0-6 (3 = warp groups, 4-5 = pencil form, 6 = plane form):
-within 2e-5 of the oracle (the FP32 rounding bound of the operator's chain of contractions), and
-the FP64 PCG with the FP32 V-cycle within +-1 iteration of the oracle. FP16 / BF16 variants 0-6:
-every output within the first-order rounding bound of the 16-bit operator."""
+vertices, edges, faces and interiors. The V-cycle operator (pencil form) with FP32 factors, variants
+0-2 (when a thread loads its factors): within 2e-5 of the oracle (the FP32 rounding bound of
+the operator's chain of contractions), and the FP64 PCG with the FP32 V-cycle within +-1 iteration of
+the oracle. With FP16 / BF16 factors, variants 0-2: every output within the rounding bound of the
+16-bit factors."""
 import os
 import subprocess
 import sys
@@ -88,9 +89,8 @@ def _problems():
 def oracle_ref(tmp_path_factory):
     """Oracle results of every case, computed once: per level a seeded x (boundary entries 0; in
     FP32-representable values), A x by the assembled oracle operator, and for the 16-bit
-    operators the bound (k + 1) u S_i with S = sum_e |K|^T |G| |K| |x| and k = 4d + 1 roundings
-    (the bound of tests/test_gpu_lowp.py); the load vector's nodal f and the oracle's PCG
-    iteration count."""
+    operators the bound (2 u + 64 2^-24) S_i with S = sum_e |K|^T |G| |K| |x| (the bound of
+    tests/test_gpu_lowp.py); the load vector's nodal f and the oracle's PCG iteration count."""
     import synth
     from oracle import multigrid
     from test_gpu_lowp import abs_bound_scale
@@ -106,7 +106,7 @@ def oracle_ref(tmp_path_factory):
             out[f"want_{ci}_{k}"] = H.levels[k].A @ x[d.interior]
             S = abs_bound_scale(d, x)[d.interior]
             for prec, u in U16.items():
-                out[f"bound_{prec}_{ci}_{k}"] = (4 * d.dim + 2) * u * S + 1e-30
+                out[f"bound_{prec}_{ci}_{k}"] = (2 * u + 64 * 2.0 ** -24) * S + 1e-30
         f = synth.nodal_field(71, H.fine.disc.N)
         out[f"f_{ci}"] = f
         _, it_ref, _, ok = H.solve_pcg(H.fine.disc.rhs(f))
@@ -160,7 +160,7 @@ def test_fp64_variant_matches_oracle_on_every_level(tmp_path, oracle_ref, varian
         assert r["st"] == 0 and r["rel"] <= 1e-8 and abs(r["it"] - r["it_ref"]) <= 1, r
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_fp32_variant_matches_oracle_on_every_level(tmp_path, oracle_ref, variant):
     for r in _run(tmp_path, oracle_ref, "fp32", 1, variant):
         assert r["used"] == {str(variant)}, r
@@ -168,12 +168,11 @@ def test_fp32_variant_matches_oracle_on_every_level(tmp_path, oracle_ref, varian
         assert r["st"] == 0 and r["rel"] <= 1e-8 and abs(r["it"] - r["it_ref"]) <= 1, r
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_16bit_variant_within_rounding_bound_on_every_level(tmp_path, oracle_ref, prec, variant):
-    """Variants 0-3 run the tensor-core kernel on orders <= 7 (the pencil form above), 4-5 the
-    pencil form with 16-bit factors everywhere, 6 the plane form (3D orders <= 4, else the pencil form). The FP64 PCG with this V-cycle (flexible beta)
-    converges to 1e-8 within one iteration of the oracle's FP64 count (FP16) or two (BF16)."""
+    """The FP64 PCG with this V-cycle (flexible beta) converges to 1e-8 within one iteration of the
+    oracle's FP64 count (FP16) or two (BF16)."""
     for r in _run(tmp_path, oracle_ref, prec, {"fp16": 2, "bf16": 3}[prec], variant):
         assert r["used"] == {str(variant)}, r
         assert r["worst"] <= 1.0, r
