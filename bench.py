@@ -527,18 +527,16 @@ def run_sweep(args):
     return 0
 
 
-def run_batched(args):
-    """Batched workload: 512 independent 3D solves (E in 2..12, p in {2,4,6,8}, contrast 10^k,
-    k in 0..4) with an FP32 V-cycle inside FP64 PCG, all through one hmg_solve_batched call, against
-    the same 512 problems solved one at a time with the plain FP64 solver. One JSON line."""
+def batched_block(n=512, reps=3):
+    """The batched workload: n independent 3D solves (E in 2..12, p in {2,4,6,8}, contrast 10^k,
+    k in 0..4) with an FP32 V-cycle inside FP64 PCG, solved by one batch plan (one graph launch per
+    batch, one kernel per operation and group), against the same problems solved one at a time with
+    the plain FP64 solver. Wall time around each batch solve (synchronized)."""
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     import synth
-    from paper_1402_5938_gb300 import Problem, solve_batched
+    from paper_1402_5938_gb300 import BatchPlan, Problem, launch_count
     dev = torch.device("cuda", 0)
-    n = args.batch
     t0 = time.perf_counter()
     mixed, fp64, bs, dofs = [], [], [], []
     for i in range(n):
@@ -554,41 +552,58 @@ def run_batched(args):
         dofs.append(N)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plan = BatchPlan(mixed, "pcg", maxit_cap=500)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    groups, kpi = plan.info()
     us = [torch.zeros_like(b) for b in bs]
-    solve_batched(mixed, "pcg", bs, us, rtol=1e-8, maxit=500)          # builds the graphs
-    reps, tb = 3, []
+    plan.solve(bs, us, rtol=1e-8, maxit=500)                              # warm-up
+    tb, l0 = [], launch_count()
     for _ in range(reps):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        sts, its, _ = solve_batched(mixed, "pcg", bs, us, rtol=1e-8, maxit=500)
+        sts, its, _ = plan.solve(bs, us, rtol=1e-8, maxit=500)
         tb.append(time.perf_counter() - t)
+    kernels_per_batch = (launch_count() - l0) / reps
     u6 = [torch.zeros_like(b) for b in bs]
     for P, b, u in zip(fp64, bs, u6):                                   # build graphs
         P.solve("pcg", b, u, rtol=1e-8, maxit=500)
     torch.cuda.synchronize()
+    l0 = launch_count()
     t = time.perf_counter()
     its6 = []
     for P, b, u in zip(fp64, bs, u6):
         st, it, _ = P.solve("pcg", b, u, rtol=1e-8, maxit=500)
         its6.append(it)
     t_seq = time.perf_counter() - t
+    kernels_seq = launch_count() - l0
     diff = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(us, u6))
-    r = torch.zeros_like(bs[0])
     worst = 0.0
     for P, b, u in zip(fp64, bs, us):
         rr = torch.zeros_like(b)
         P.apply(0, u, rr)
         worst = max(worst, float(torch.linalg.norm(b - rr) / torch.linalg.norm(b)))
     tbm = statistics.median(tb)
-    print(json.dumps({
-        "batched": f"{n} solves", "total_dof": sum(dofs), "setup_s_both_sets": setup_s,
-        "batched_mixed_s": tbm, "batched_solves_per_s": n / tbm, "batched_gdof_per_s": sum(dofs) / tbm / 1e9,
-        "fp64_one_at_a_time_s": t_seq, "fp64_solves_per_s": n / t_seq, "speedup_vs_fp64_sequential": t_seq / tbm,
-        "all_converged": all(s_ == 0 for s_ in sts), "iters_mixed_mean": statistics.mean(its),
-        "iters_fp64_mean": statistics.mean(its6), "max_rel_diff_mixed_vs_fp64": diff,
-        "worst_fp64_residual_of_mixed": worst}), flush=True)
+    plan.close()
     for P in mixed + fp64:
         P.close()
+    return {
+        "batched": f"{n} solves", "total_dof": sum(dofs), "setup_s_both_sets": setup_s, "plan_build_s": plan_s,
+        "groups": groups, "kernels_per_loop_iteration": kpi, "kernels_per_batch": kernels_per_batch,
+        "batched_mixed_s": tbm, "batched_solves_per_s": n / tbm, "batched_gdof_per_s": sum(dofs) / tbm / 1e9,
+        "fp64_one_at_a_time_s": t_seq, "fp64_solves_per_s": n / t_seq, "fp64_one_at_a_time_kernels": kernels_seq,
+        "speedup_vs_fp64_sequential": t_seq / tbm,
+        "all_converged": all(s_ == 0 for s_ in sts), "iters_mixed_mean": statistics.mean(its),
+        "iters_fp64_mean": statistics.mean(its6), "max_rel_diff_mixed_vs_fp64": diff,
+        "worst_fp64_residual_of_mixed": worst}
+
+
+def run_batched(args):
+    """The batched workload as its own JSON line (see batched_block)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    print(json.dumps(batched_block(args.batch)), flush=True)
     return 0
 
 

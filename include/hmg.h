@@ -260,15 +260,37 @@ hmg_status hmg_solve_low_order(hmg_problem* prob, hmg_problem* low, const double
                                double rtol, int maxit, double inner_rtol, int* iters, long long* inner_iters,
                                double* res_hist, void* stream);
 
-/* n independent solves (different meshes, orders and coefficients allowed) as one call: every
- * problem's solve is the same device-side graph as hmg_solve's, launched concurrently on a pool
- * of streams forked from and joined back to `stream`, which is synchronized on return.
+/* n independent solves (different meshes, orders and coefficients allowed) as one call: a batch
+ * plan (hmg_batch_create, below) built for the call, solved once and destroyed; batches with an
+ * element-block Jacobi problem instead launch every problem's own per-iteration graphs in lockstep
+ * on a pool of streams forked from and joined back to `stream`, which is synchronized on return.
  * b[i], u[i]: problem i's vectors; iters[i], res_hist[i] (host, >= maxit+1 doubles) and
  * status[i] may be NULL. Returns HMG_OK if every solve converged, else the first failing
  * status. A handle may appear only once per call. (Batched form of Sec. 4.3 / Algorithm 1.) */
 hmg_status hmg_solve_batched(hmg_problem* const* probs, int n, int mode, const double* const* b_dev,
                              double* const* u_dev, double rtol, int maxit, int* iters, double* const* res_hist,
                              int* status, void* stream);
+
+/* A batch plan: n independent problems (different meshes, orders, coefficients) solved together
+ * by one CUDA graph launch per solve (batched form of Sec. 4.3 / Algorithm 1). Problems whose
+ * hierarchies share their structure (dimension, levels, order per level, smoother, nu_pre / nu_post,
+ * smooth_prec) form a group; every operator apply, smoothing step, transfer, coarsest solve and PCG
+ * vector step of a group is one kernel launch over all its members, the groups run as parallel
+ * branches, and a device-side loop iterates until every member has converged, reached maxit or gone
+ * non-finite -- each member stopping at the iteration it would stop at alone.
+ * hmg_batch_create: builds the plan (device tables, super-vectors, the instantiated graph) for
+ *   mode HMG_MODE_MG or HMG_MODE_PCG and iteration caps up to maxit_cap. The problems must outlive
+ *   the plan and may appear once each; element-block Jacobi problems are refused (HMG_EINVAL).
+ * hmg_batch_solve: b_dev[i] -> u_dev[i] for problem i (as hmg_solve, from u = 0, to
+ *   ||r|| <= rtol ||b||); iters, res_hist[i] (>= maxit+1 doubles), status may be NULL. Returns
+ *   HMG_OK if every solve converged, else the first failing status. Synchronizes `stream`.
+ * hmg_batch_info: number of groups and kernels launched per loop iteration. */
+typedef struct hmg_batch hmg_batch;
+hmg_status hmg_batch_create(hmg_problem* const* probs, int n, int mode, int maxit_cap, hmg_batch** out);
+hmg_status hmg_batch_solve(hmg_batch* plan, const double* const* b_dev, double* const* u_dev, double rtol, int maxit,
+                           int* iters, double* const* res_hist, int* status, void* stream);
+hmg_status hmg_batch_info(const hmg_batch* plan, int* groups, long long* kernels_per_iteration);
+hmg_status hmg_batch_destroy(hmg_batch* plan);
 
 /* Number of finest-level operator applies issued since setup (cost-model accounting,
  * Sec. 4.2/4.3: 7 per V(3,3) cycle). */

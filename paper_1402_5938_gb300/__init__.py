@@ -5,4 +5,4 @@ The numerical work lives in the CUDA library ``libhmg.so`` (sources in ``csrc/``
 """
 from .hmg import (Desc, HmgError, Problem, host_basis, host_hessenberg_max_real_eig, launch_count, lib,  # noqa: F401
                   make_desc, noalloc_lengths, restrict_noalloc, solve_batched)
-from .hmg import Server, desc_ndof, estimate_bytes, measure_peak  # noqa: F401
+from .hmg import BatchPlan, Server, desc_ndof, estimate_bytes, measure_peak  # noqa: F401

@@ -84,7 +84,9 @@ void pinned_free(void* p, size_t bytes);
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);
 
-struct ProblemImpl;  // defined in hmg.cu
+struct ProblemImpl;  // defined in problem.cuh
+// Whether a problem can join a grouped batch plan (batch.cu).
+bool batch_supported(const hmg_problem* p);
 
 }  // namespace hmg
 

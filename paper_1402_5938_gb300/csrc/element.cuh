@@ -199,17 +199,18 @@ inline int alpha_mode(double alpha) {
   return alpha == 1.0 ? kAlphaOne : (alpha == -1.0 ? kAlphaMinusOne : kAlphaOther);
 }
 
+// The work of one thread block of the FP64 apply: elements e0g, ..., e0g + NEG - 1 (those below
+// m.nelem); smem_raw is the block's dynamic shared memory (Apply64Cfg::smem bytes).
 template <int DIM, int N, int V>
-__global__ void __launch_bounds__(Apply64Cfg<DIM, N, V>::GT)
-k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ G, const Mesh m,
-          const __grid_constant__ Tab<N, double> tab, const double alpha, const int amode, int* __restrict__ err) {
+__device__ __forceinline__ void apply64_tile(const double* __restrict__ x, double* __restrict__ y,
+                                             const double* __restrict__ G, const Mesh& m, const Tab<N, double>& tab,
+                                             const double alpha, const int amode, int* __restrict__ err,
+                                             const long long e0g, unsigned char* smem_raw) {
   using C = Apply64Cfg<DIM, N, V>;
   constexpr int NP = C::NP, NEG = C::NEG, W = C::W, NC = Sh<DIM, N>::NC;
   constexpr int S1 = N, S2 = N * N;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   int* sflag = reinterpret_cast<int*>(smem_raw + 8);
-  const long long e0g = (long long)blockIdx.x * NEG;
   const int neg = (int)min((long long)NEG, m.nelem - e0g);
   int goff = 0;  // byte offset of the staged slab above its 16-byte boundary
   unsigned char* gstage = smem_raw + C::base_bytes;
@@ -344,6 +345,15 @@ k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __
       atomicAdd(y + g, amode == kAlphaOne ? v : (amode == kAlphaMinusOne ? -v : alpha * v));
     }
   }
+}
+
+template <int DIM, int N, int V>
+__global__ void __launch_bounds__(Apply64Cfg<DIM, N, V>::GT)
+k_apply64(const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ G, const Mesh m,
+          const __grid_constant__ Tab<N, double> tab, const double alpha, const int amode, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  apply64_tile<DIM, N, V>(x, y, G, m, tab, alpha, amode, err, (long long)blockIdx.x * Apply64Cfg<DIM, N, V>::NEG,
+                          smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------

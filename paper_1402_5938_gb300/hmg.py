@@ -91,6 +91,11 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)]),
     "hmg_server_destroy": (_I, [_P]),
     "hmg_selftest_bounded_wait": (_I, [ctypes.c_uint, ctypes.POINTER(_I)]),
+    "hmg_batch_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, ctypes.POINTER(_P)]),
+    "hmg_batch_solve": (_I, [_P, ctypes.POINTER(_V), ctypes.POINTER(_V), _D, _I, ctypes.POINTER(_I),
+                             ctypes.POINTER(ctypes.POINTER(_D)), ctypes.POINTER(_I), _V]),
+    "hmg_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)]),
+    "hmg_batch_destroy": (_I, [_P]),
     "hmg_fine_applies": (ctypes.c_longlong, [_P]),
     "hmg_launch_count": (ctypes.c_longlong, []),
     "hmg_status_string": (ctypes.c_char_p, [_I]),
@@ -360,6 +365,49 @@ def noalloc_lengths(dim, nelem_fine, order_fine, order_coarse, halve_mesh):
         nf *= e * int(order_fine) + 1
         nc *= (e // 2 if halve_mesh else e) * int(order_coarse) + 1
     return nf, nc
+
+
+class BatchPlan:
+    """hmg_batch_*: a plan that solves `problems` together, one graph launch per solve."""
+
+    def __init__(self, problems, mode="pcg", maxit_cap=1000):
+        self.problems = list(problems)
+        n = len(self.problems)
+        H = (_P * n)(*[p.h for p in self.problems])
+        h = ctypes.c_void_p()
+        _check(lib().hmg_batch_create(H, n, MODE[mode], int(maxit_cap), ctypes.byref(h)))
+        self.h, self.cap = h, int(maxit_cap)
+
+    def info(self):
+        """(groups, kernels launched per loop iteration)."""
+        g, k = ctypes.c_int(), ctypes.c_longlong()
+        _check(lib().hmg_batch_info(self.h, ctypes.byref(g), ctypes.byref(k)))
+        return g.value, k.value
+
+    def solve(self, bs, us, rtol=1e-8, maxit=None, stream=None):
+        """Returns (statuses, iterations, histories)."""
+        maxit = self.cap if maxit is None else int(maxit)
+        n = len(self.problems)
+        B = (_V * n)(*[_ptr(b, p.ndof(0)) for p, b in zip(self.problems, bs)])
+        U = (_V * n)(*[_ptr(u, p.ndof(0)) for p, u in zip(self.problems, us)])
+        its, sts = (_I * n)(), (_I * n)()
+        hists = [(_D * (maxit + 1))() for _ in range(n)]
+        HP = (ctypes.POINTER(_D) * n)(*[ctypes.cast(x, ctypes.POINTER(_D)) for x in hists])
+        st = lib().hmg_batch_solve(self.h, B, U, float(rtol), maxit, its, HP, sts, _stream(stream))
+        if st not in (HMG_OK, HMG_ENOCONV, HMG_ENAN):
+            _check(st)
+        return list(sts), list(its), [np.array(x[: its[i] + 1]) for i, x in enumerate(hists)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hmg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def restrict_noalloc(dim, nelem_fine, order_fine, order_coarse, halve_mesh, rf, rc, stream=None):

@@ -140,3 +140,87 @@ def test_batched_lockstep_edges(hmg, mode):
     assert sts[1] == 0 and its2[1] == 0
     for P in probs:
         P.close()
+
+
+def _batch(hmg, idx, **over):
+    probs, bs = [], []
+    for i in idx:
+        prob, seed = synth.batched_problem(i)
+        prob = dict(prob, **over)
+        P = hmg.Problem(prob)
+        N = P.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device=DEV)
+        P.rhs(torch.from_numpy(synth.nodal_field(seed, N)).to(DEV), b)
+        probs.append(P)
+        bs.append(b)
+    return probs, bs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_batch_plan_groups_and_repeats(hmg, prec):
+    """A plan over problems of several orders: one group per hierarchy structure, a bounded number
+    of kernels per loop iteration (one launch per operation and group, not per problem), and two
+    solves in a row give every problem the iterations and solution of solving it alone."""
+    probs, bs = _batch(hmg, range(10), smooth_prec=prec)
+    plan = hmg.BatchPlan(probs, "pcg", maxit_cap=300)
+    groups, kpi = plan.info()
+    orders = {P.level_info(0)[1] for P in probs}
+    assert groups == len(orders)
+    assert kpi < 150 * groups
+    alone = []
+    for P, b in zip(probs, bs):
+        u1 = torch.zeros_like(b)
+        st1, it1, _ = P.solve("pcg", b, u1, rtol=1e-8, maxit=300)
+        alone.append((st1, it1, u1))
+    tol = 1e-10 if prec == "fp64" else (1e-8 if prec == "fp32" else 1e-6)
+    for rep in range(2):
+        us = [torch.full_like(b, 3.0) for b in bs]
+        sts, its, hists = plan.solve(bs, us, rtol=1e-8, maxit=300)
+        for (st1, it1, u1), st, it, u, h in zip(alone, sts, its, us, hists):
+            assert st == st1 == 0 and (it == it1 if prec != "bf16" else abs(it - it1) <= 1), (rep, it, it1)
+            assert h[-1] <= 1e-8 * h[0]
+            assert float(torch.linalg.norm(u - u1) / torch.linalg.norm(u1)) < tol
+    plan.close()
+    for P in probs:
+        P.close()
+
+
+def test_batch_plan_mg_mode_2d_and_3d(hmg):
+    """MG iteration in a plan that mixes 2D and 3D problems (separate groups)."""
+    probs, bs = [], []
+    for prob in (synth.mms2d_poisson(8, 4), synth.warped_var3d(4, 2, hier="p", n_hlevels=2),
+                 synth.problem(2, 12, 3, warp_amp=0.1, mu_b=1e3, hier="h", n_hlevels=2)):
+        P = hmg.Problem(prob)
+        N = P.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device=DEV)
+        P.rhs(torch.from_numpy(synth.nodal_field(13, N)).to(DEV), b)
+        probs.append(P)
+        bs.append(b)
+    plan = hmg.BatchPlan(probs, "mg", maxit_cap=100)
+    us = [torch.zeros_like(b) for b in bs]
+    sts, its, hists = plan.solve(bs, us, rtol=1e-8, maxit=100)
+    for P, b, u, st, it in zip(probs, bs, us, sts, its):
+        u1 = torch.zeros_like(b)
+        st1, it1, _ = P.solve("mg", b, u1, rtol=1e-8, maxit=100)
+        assert st == st1 == 0 and it == it1
+        assert float(torch.linalg.norm(u - u1) / torch.linalg.norm(u1)) < 1e-10
+    plan.close()
+    for P in probs:
+        P.close()
+
+
+def test_batched_block_jacobi_falls_back_to_lockstep(hmg):
+    """Element-block Jacobi has no grouped form: a plan refuses it, hmg_solve_batched still solves it."""
+    prob = synth.problem(2, 8, 4, hier="h", n_hlevels=2, smoother="blockjacobi")
+    P = hmg.Problem(prob)
+    N = P.ndof(0)
+    b = torch.zeros(N, dtype=torch.float64, device=DEV)
+    P.rhs(torch.from_numpy(synth.nodal_field(14, N)).to(DEV), b)
+    with pytest.raises(hmg.HmgError):
+        hmg.BatchPlan([P], "pcg")
+    u = torch.zeros_like(b)
+    sts, its, _ = hmg.solve_batched([P], "pcg", [b], [u], rtol=1e-8, maxit=100)
+    u1 = torch.zeros_like(b)
+    st1, it1, _ = P.solve("pcg", b, u1, rtol=1e-8, maxit=100)
+    assert sts[0] == st1 == 0 and its[0] == it1
+    P.close()
