@@ -402,6 +402,8 @@ def run_gpu(args):
     mixed = {} if args.host_loop or args.quick else mixed_block(prob, P, b, flush, stream, solve_ms)
     sweep = [] if args.host_loop or args.quick else sweep_block(flush, stream, peak64, orders=((64, 2), (16, 8), (8, 16)))
     c2 = {} if args.host_loop or args.quick else c2_block(flush, stream)
+    batched = {} if args.host_loop or args.quick else batched_block(args.batch)
+    serving = {} if args.host_loop or args.quick else serve_block(args.requests, args.slots)
 
     if rank == 0:
         cpu = cpu_baseline(args.hier) if not args.quick else None
@@ -438,6 +440,7 @@ def run_gpu(args):
                           "iterations": it_h, "call": "hmg_solve_host (page-locked nodal f -> u)",
                           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "max_rel_diff_vs_device": u_err},
             "mixed_precision": mixed, "sweep_129cube": sweep, "single_solve_16cube_q4": c2,
+            "batched_512": batched, "serving": serving,
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
@@ -607,27 +610,23 @@ def run_batched(args):
     return 0
 
 
-def run_serve(args):
+def serve_block(R=200, slots=8):
     """Serving workload: Poisson arrivals (2,000/s mean) of 2D/3D solves, DOF log-uniform in
-    [1e3, 2e6], p uniform in 1..16, through the continuous-batching server (FP32 V-cycle in FP64
-    PCG); p50/p99 latency (submit to result on the host) and solves/s at the specified rate and
-    at half the measured saturated rate, against the plain FP64 path one request at a time
-    (single-server queue on the same arrivals). One JSON line."""
+    [1e3, 2e6], p uniform in 1..16, all through the continuous-batching server (hmg_server_*):
+    the FP32 V-cycle in FP64 PCG with `slots` workers at the specified rate and at half the
+    measured saturated rate, and the plain FP64 solver through the same server with one worker
+    (one request at a time) and with `slots` workers, on the same arrivals. p50/p99 latency (submit
+    to result on the host, setup of each new hierarchy included) and solves/s."""
     import numpy as np
-    import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     import synth
-    from paper_1402_5938_gb300 import Problem, Server, desc_ndof
-    dev = torch.device("cuda", 0)
-    R = args.requests
+    from paper_1402_5938_gb300 import Server, desc_ndof
     reqs = [synth.serving_request(i) for i in range(R)]
     fs = [synth.nodal_field(seed, desc_ndof(prob)) for prob, seed, _ in reqs]
     gaps = np.array([g for _, _, g in reqs])
 
-    def serve(scale, slots):
-        srv = Server(0, 160 << 30, slots)
+    def serve(scale, nslots, prec):
+        srv = Server(0, 160 << 30, nslots)
         arr = np.cumsum(gaps * scale)
         t0 = time.perf_counter()
         tickets = []
@@ -635,11 +634,12 @@ def run_serve(args):
             dt = t0 + a - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(srv.submit(prob, f, rtol=1e-8, mode="pcg", maxit=500))
-        lat, ok, done_at, failed = [], 0, [], []
+            tickets.append(srv.submit(dict(prob, smooth_prec=prec), f, rtol=1e-8, mode="pcg", maxit=500))
+        lat, ok, done_at, failed, its = [], 0, [], [], []
         for i, ((t, n), a) in enumerate(zip(tickets, arr)):
             st, u, it, res, l = srv.wait(t, n)
             ok += int(st == 0)
+            its.append(it)
             if st != 0:
                 p = reqs[i][0]
                 failed.append({"i": i, "status": st, "iters": it, "dim": p["dim"], "nelem": p["nelem"][0],
@@ -649,36 +649,23 @@ def run_serve(args):
         span = max(done_at)
         srv.close()
         return dict(p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
-                    solves_per_s=R / span, ok=ok, offered_per_s=R / arr[-1], failed=failed)
+                    solves_per_s=R / span, ok=ok, offered_per_s=R / arr[-1], mean_iterations=float(np.mean(its)),
+                    failed=failed, slots=nslots, v_cycle=prec)
 
-    hot = serve(1.0, args.slots)
-    cool = serve(max(1.0, (R / gaps.sum()) / (0.5 * hot["solves_per_s"])), args.slots)
-    # plain FP64 path, one request at a time: service times, then a single-server queue
-    service = []
-    for (prob, _, _), f in zip(reqs, fs):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        P = Problem(dict(prob, smooth_prec="fp64"))
-        N = P.ndof(0)
-        b = torch.zeros(N, dtype=torch.float64, device=dev)
-        P.rhs(torch.from_numpy(f).to(dev), b)
-        u = torch.zeros_like(b)
-        P.solve("pcg", b, u, rtol=1e-8, maxit=500)
-        u.cpu()
-        P.close()
-        service.append(time.perf_counter() - t)
-    arr = np.cumsum(gaps)
-    fin, lat = 0.0, []
-    for a, sv in zip(arr, service):
-        start = max(a, fin)
-        fin = start + sv
-        lat.append(fin - a)
-    print(json.dumps({
-        "serve": f"{R} requests, Poisson 2000/s, {args.slots} slots", "at_2000_per_s": hot,
-        "below_saturation": cool,
-        "fp64_one_at_a_time": {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                               "p99_ms": 1e3 * float(np.percentile(lat, 99)), "solves_per_s": R / fin,
-                               "mean_service_ms": 1e3 * float(np.mean(service))}}), flush=True)
+    hot = serve(1.0, slots, "fp32")
+    cool = serve(max(1.0, (R / gaps.sum()) / (0.5 * hot["solves_per_s"])), slots, "fp32")
+    fp64_one = serve(1.0, 1, "fp64")
+    fp64_slots = serve(1.0, slots, "fp64")
+    return {"serve": f"{R} requests, Poisson 2000/s", "mixed_at_2000_per_s": hot, "mixed_below_saturation": cool,
+            "fp64_one_at_a_time": fp64_one, "fp64_same_slots": fp64_slots,
+            "mixed_over_fp64_one_at_a_time_solves_per_s": hot["solves_per_s"] / fp64_one["solves_per_s"]}
+
+
+def run_serve(args):
+    """The serving workload as its own JSON line (see serve_block)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    print(json.dumps(serve_block(args.requests, args.slots)), flush=True)
     return 0
 
 

@@ -48,9 +48,9 @@ __host__ __device__ constexpr PencilShape pencil_shape(int dim, int n) {
       case 2: return {32, 2, 4, 9};
       case 3: return {32, 3, 9, 27};
       case 4: return {8, 5, 20, 84};
-      case 5: return {16, 5, 25, 126};
+      case 5: return {8, 5, 25, 132};
       case 6: return {8, 7, 42, 252};
-      case 7: return {8, 7, 51, 364};
+      case 7: return {4, 7, 55, 392};
       case 8: return {4, 9, 72, 584};
       case 9: return {4, 9, 81, 744};
       case 10: return {4, 13, 130, 1304};
