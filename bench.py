@@ -41,8 +41,24 @@ L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the headline's FP64 apply kernel, by
 # (kernel, elements): per launch, from the ncu capture named in "traffic_source"; None when the
 # kernel has changed since that capture
-APPLY_TRAFFIC = {}
+APPLY_TRAFFIC = {("k_apply64<3,5,2>", 32768): 229.953024e6 + 12.929792e6}
+TRAFFIC_SOURCE = "ncu capture of k_apply64<3,5,2> on the 32^3 Q4 level: dram__bytes_read.sum + dram__bytes_write.sum"
 REF_ROWS_PER_STEP = 400
+
+
+class L2Flush:
+    """Between timed iterations: write a buffer larger than L2 (256 MB), then read a second one, so
+    that L2 holds none of the timed kernel's data and no dirty lines whose write-back would land in
+    the timed region."""
+
+    def __init__(self, device):
+        import torch
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+        self.r = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def zero_(self):
+        self.w.zero_()
+        self.r.sum()
 
 
 def measured_peaks():
@@ -286,10 +302,19 @@ def mixed_block(prob, P64, b, flush, stream, t64_ms, reps=5):
         x32 = b.float()
         y32 = torch.zeros_like(x32)
         ta = timed_apply(lambda: Pm.apply_f32(0, x32, y32), flush, stream, 10)
+        (E3, p, _) = Pm.level_info(0)
+        dim = 3 if E3[2] > 1 or prob["dim"] == 3 else 2
+        E = E3[0] * E3[1] * E3[2]
+        # algorithmic bytes of the V-cycle operator: its geometric factors (FP32 or 16-bit) once,
+        # x read and y written once in FP32
+        fbytes = E * (p + 1) ** dim * (6 if dim == 3 else 3) * (4 if prec == "fp32" else 2) + 8 * N
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
         out[prec] = {"solve_ms": t, "iterations": it, "status": st,
                      "fp64_rel_residual": float(torch.linalg.norm(b - rm) / torch.linalg.norm(b)),
                      "speedup_vs_fp64": t64_ms / t, "fine_apply_ms": ta, "fine_apply_gdofs": N / (ta * 1e-3) / 1e9,
-                     "fine_apply_variant": Pm.level_variants(0)[1]}
+                     "fine_apply_variant": Pm.level_variants(0)[1], "fine_apply_bytes": fbytes,
+                     "fine_apply_frac_of_hbm": fbytes / (ta * 1e-3) / 1e9 / hbm,
+                     "fine_apply_note": "hmg_apply_f32 (zeroing y + the pencil-form kernel), CUDA events, L2 flushed"}
         Pm.close()
     return out
 
@@ -329,7 +354,7 @@ def run_gpu(args):
     P.rhs(f, b)
     x = torch.from_numpy(synth.uniform_pm1(7, N)).to(dev)
     y = torch.zeros_like(x)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -413,8 +438,8 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "hier": args.hier, "global_batch": world, "dof": N,
                        "parallelism": f"replicas{world}",
-                       "l2": "flushed (256 MB write) before every timed step; the apply's 196.6 MB of FP64 "
-                             "geometric factors also exceed L2",
+                       "l2": "flushed before every timed step (256 MB written, then another 256 MB read, so no "
+                             "dirty lines remain); the apply's 196.6 MB of FP64 geometric factors also exceed L2",
                        "step": "hmg_apply on the finest level, then hmg_solve (PCG + p-MG) to 1e-8",
                        "solve_loop": "host" if args.host_loop else "graph"},
             "apply_ms": t_apply, "solve_ms": solve_ms, "setup_ms": setup_ms, "iterations": its[-1],
@@ -426,7 +451,7 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak64, "unit": "TFLOP/s",
                          "frac": achieved_tf / peak64, "traffic": traffic, "kernel": kern,
                          "units_per_launch": E, "flop_per_unit": flop_per_elem(3, n),
-                         "traffic_source": "ncu capture of this kernel on this workload (profiles/)" if traffic else None,
+                         "traffic_source": TRAFFIC_SOURCE if traffic else None,
                          "note": "FP64 pipe; peak = measured FP64 FMA rate of this GPU (hmg_measure_peak, "
                                  "burst); algorithmic flops 24n^4+15n^3 per element; apply time = hmg_apply "
                                  "(zeroing y + the apply kernel) with CUDA events in the timed steps"},
@@ -524,7 +549,7 @@ def run_sweep(args):
 
     import __graft_entry__
     __graft_entry__.build()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush("cuda")
     for row in sweep_block(flush, torch.cuda.current_stream(), fp64_peak(), ((64, 2), (32, 4), (16, 8), (8, 16))):
         print(json.dumps(dict(row, sweep=row["mesh"])), flush=True)
     return 0
