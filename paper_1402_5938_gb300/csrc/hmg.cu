@@ -284,7 +284,7 @@ hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_low(l.m, l.basis, x, y, l.Glow, l.gsc, alpha, P.desc.smooth_prec, s, l.v32));
+  TRY(launch_apply_low(l.m, l.basis, x, y, l.Glow, l.gsc, alpha, P.desc.smooth_prec, s, l.v32, &l.tc, P.err));
   return HMG_OK;
 }
 
@@ -593,7 +593,8 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     {
       std::lock_guard<std::mutex> lk(mu);
       auto it = cache.find(key);
-      if (it != cache.end()) {
+      const int nv = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : kApplyLowVariants + (l.tc.G ? 1 : 0);
+      if (it != cache.end() && it->second >= 0 && it->second < nv) {  // a decision this level can run
         (prec ? l.v32 : l.v64) = it->second;
         continue;
       }
@@ -605,11 +606,12 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     float best = 1e30f;
     int bv = 0;
     cudaError_t err = cudaSuccess;
-    const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : kApplyLowVariants;
+    const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : kApplyLowVariants + (l.tc.G ? 1 : 0);
     for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
       auto run = [&]() {
         if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v, l.Ke);
-        return launch_apply_low(l.m, l.basis, l.x32, l.r32, l.Glow, l.gsc, 1.0f, P.desc.smooth_prec, s, v);
+        return launch_apply_low(l.m, l.basis, l.x32, l.r32, l.Glow, l.gsc, 1.0f, P.desc.smooth_prec, s, v, &l.tc,
+                                P.err);
       };
       if ((err = run()) != cudaSuccess) break;  // warm-up (also opts the kernel into its smem)
       if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
@@ -840,13 +842,24 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
       }
       if (mixed) {
         TRY(P.alloc((void**)&l.Glow, low_factor_bytes(l.m, D.smooth_prec) + 256));  // prefetch rounding
-        if (D.smooth_prec == HMG_PREC_FP16) TRY(P.alloc((void**)&l.gsc, l.m.nelem * sizeof(float)));
+        if (D.smooth_prec != HMG_PREC_FP32) TRY(P.alloc((void**)&l.gsc, l.m.nelem * sizeof(float)));
+        if (tc16_supported(l.m, D.smooth_prec)) {  // tensor-core form: its factor layout and Phi image
+          std::vector<unsigned char> img;
+          tc16_phi_image(l.basis, img, &l.tc.vsc);
+          void *phi = nullptr, *gtc = nullptr;
+          TRY(P.alloc(&phi, img.size()));
+          TRY(cudaMemcpyAsync(phi, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+          TRY(P.alloc(&gtc, tc16_factor_bytes(l.m)));
+          l.tc.phi = phi;
+          l.tc.G = gtc;
+        }
         TRY(P.alloc((void**)&l.dinv32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.b32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.x32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.r32, n * sizeof(float)));
         TRY(P.alloc((void**)&l.d32, n * sizeof(float)));
         TRY(launch_pack_low(l.G, l.Glow, l.gsc, l.m, D.smooth_prec, s));
+        if (l.tc.G) TRY(launch_pack_tc16(l.G, const_cast<void*>(l.tc.G), l.gsc, l.m, D.smooth_prec, s));
         TRY(to_f32(l.dinv32, l.dinv, n, s));
       }
       CHECK(tune_level(P, l, s));
@@ -1152,7 +1165,11 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     }
     if (mixed) {
       add(low_factor_bytes(m, D.smooth_prec) + 256);
-      if (D.smooth_prec == HMG_PREC_FP16) add((size_t)m.nelem * 4);
+      if (D.smooth_prec != HMG_PREC_FP32) add((size_t)m.nelem * 4);
+      if (tc16_supported(m, D.smooth_prec)) {
+        add(tc16_phi_bytes(m));
+        add(tc16_factor_bytes(m));
+      }
       for (int v = 0; v < 5; ++v) add(n * 4);
     }
     max_stage = std::max(max_stage, gsz * D.dim * (D.dim + 1) * 8);

@@ -2,6 +2,8 @@
 // compile-time node count N = p + 1 (2..17).
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace hmg {
@@ -23,17 +25,37 @@ cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, d
 cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, double* Ke, cudaStream_t s);
 // The operator of the mixed V-cycle, y += alpha * A x with FP32 vectors and arithmetic (the pencil
 // form of pencil.cuh) and geometric factors Glow in precision prec: HMG_PREC_FP32, or 16 bits
-// (HMG_PREC_FP16 with the per-element power-of-two scales gsc, HMG_PREC_BF16 unscaled), in the
-// grouped layout launch_pack_low writes (low_factor_bytes bytes; allocate >= 16 bytes more for
-// the L2 prefetch's rounding). variant 0 loads a thread's factors one phase before the pointwise
-// product, 1 before the first phase (small orders; as 0 otherwise), 2 at their use; setup picks
-// one per level by timing.
+// (HMG_PREC_FP16 / HMG_PREC_BF16, stored divided by the per-element powers of two gsc), in the
+// grouped layout launch_pack_low writes (low_factor_bytes bytes; allocate >= 256 bytes more for
+// the L2 prefetches' rounding). variant 0 loads a thread's factors one phase before the pointwise
+// product, 1 before the first phase (small orders; as 0 otherwise), 2 at their use; variant
+// kApplyLowTc (16-bit factors, 3D, orders <= kTc16MaxN - 1) is the tensor-core form of tc16.cuh,
+// which needs *tc and the device error flag err (set by a timed-out wait). Setup picks the
+// variant per level by timing.
 constexpr int kApplyLowVariants = 3;
+constexpr int kApplyLowTc = 3;
+constexpr int kTc16MaxN = 5;
+// Data of the tensor-core form: the factors in its own layout (tc16_factor_bytes, written by
+// launch_pack_tc16), the reference gradient image (tc16_phi_image, tc16_phi_bytes) and the
+// power of two applied to v.
+struct Tc16Data {
+  const void* G = nullptr;
+  const void* phi = nullptr;
+  float vsc = 1.0f;
+};
 size_t low_factor_bytes(const Mesh& m, int prec);
 cudaError_t launch_apply_low(const Mesh& m, const Basis1D& b, const float* x, float* y, const void* Glow,
-                             const float* gsc, float alpha, int prec, cudaStream_t s, int variant = 0);
-// Glow (zero-filled beforehand) from G [E][NC][NP] in FP64; FP16 also writes gsc[e].
+                             const float* gsc, float alpha, int prec, cudaStream_t s, int variant = 0,
+                             const Tc16Data* tc = nullptr, int* err = nullptr);
+// Glow (zero-filled beforehand) from G [E][NC][NP] in FP64; 16-bit precisions also write gsc[e].
 cudaError_t launch_pack_low(const double* G, void* Glow, float* gsc, const Mesh& m, int prec, cudaStream_t s);
+bool tc16_supported(const Mesh& m, int prec);
+size_t tc16_phi_bytes(const Mesh& m);
+size_t tc16_factor_bytes(const Mesh& m);
+void tc16_phi_image(const Basis1D& b, std::vector<unsigned char>& img, float* vsc);
+// The tensor-core layout of the 16-bit factors (zero-filled beforehand); writes gsc[e] as
+// launch_pack_low does.
+cudaError_t launch_pack_tc16(const double* G, void* Gtc, float* gsc, const Mesh& m, int prec, cudaStream_t s);
 
 // Geometry, stage 1: Gauss-point coordinates and Jacobians into the stage buffer
 // J [E][dim*(dim+1)][NP], from the warp map (coords = nullptr) or given node coordinates

@@ -1,6 +1,7 @@
 // Reduced-precision operator apply of the mixed V-cycle, "pencil" form: y += alpha * A x with
-// FP32 vectors and arithmetic, the geometric factors stored in FP32, FP16 (power-of-two scale per
-// element) or BF16 (paper Sec. 2.3 matrix-free apply, sum factorization).
+// FP32 vectors and arithmetic, the geometric factors stored in FP32, FP16 or BF16 (the 16-bit
+// formats divided by a power-of-two scale per element) (paper Sec. 2.3 matrix-free apply, sum
+// factorization).
 //
 // This operator is bound by memory traffic (the factors: 24 or 12 bytes per Gauss point), so the
 // kernel is shaped to issue few instructions per flop and to keep every memory path busy with
@@ -108,11 +109,12 @@ inline size_t pencil_factor_values(int dim, int n, long long nelem) {
   return (size_t)(groups * s.epb * (dim == 3 ? 6 : 3) * np);
 }
 
-// The NC factors of point q of element slot el of group g, as FP32. FP32: [g][NC][NP][EPB];
-// 16-bit, 3D: pairs of components as 32-bit words [g][3][NP][EPB]; 16-bit, 2D: [g][3][NP][EPB];
-// FP16 values times the element's scale.
+// The NC factors of point q of element slot el of group g, as FP32 (16-bit factors as stored,
+// i.e. divided by the element's scale, which the caller applies to the element's result).
+// FP32: [g][NC][NP][EPB]; 16-bit, 3D: pairs of components as 32-bit words [g][3][NP][EPB];
+// 16-bit, 2D: [g][3][NP][EPB].
 template <int DIM, int N, typename GT>
-__device__ __forceinline__ void load_g(const GT* __restrict__ G, long long g, int el, int q, float sc, float* v) {
+__device__ __forceinline__ void load_g(const GT* __restrict__ G, long long g, int el, int q, float* v) {
   using C = PencilCfg<DIM, N>;
   constexpr int NP = C::NP, NC = C::NC, EPB = C::EPB;
   if constexpr (std::is_same<GT, float>::value) {
@@ -124,21 +126,17 @@ __device__ __forceinline__ void load_g(const GT* __restrict__ G, long long g, in
 #pragma unroll
     for (int w = 0; w < 3; ++w) {
       const unsigned u = __ldg(p + (long long)w * NP * EPB);
-      if constexpr (std::is_same<GT, __half>::value) {
-        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
-        v[2 * w] = f.x * sc;
-        v[2 * w + 1] = f.y * sc;
-      } else {
-        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
-        v[2 * w] = f.x;
-        v[2 * w + 1] = f.y;
-      }
+      float2 f;
+      if constexpr (std::is_same<GT, __half>::value) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+      else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+      v[2 * w] = f.x;
+      v[2 * w + 1] = f.y;
     }
   } else {
     const GT* p = G + (g * 3 * NP + q) * EPB + el;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      if constexpr (std::is_same<GT, __half>::value) v[c] = __half2float(p[(long long)c * NP * EPB]) * sc;
+      if constexpr (std::is_same<GT, __half>::value) v[c] = __half2float(p[(long long)c * NP * EPB]);
       else v[c] = __bfloat162float(p[(long long)c * NP * EPB]);
     }
   }
@@ -229,7 +227,9 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
                       (DIM == 3 ? (((b == 0) & ((fl >> 2) & 1)) | ((b == N - 1) & ((fl >> 3) & 1))) : false);
   const int f_lo = DIM == 3 ? ((fl >> 4) & 1) : ((fl >> 2) & 1);
   const int f_hi = DIM == 3 ? ((fl >> 5) & 1) : ((fl >> 3) & 1);
-  const float sc = (gsc != nullptr && valid) ? gsc[e] : 1.0f;
+  // 16-bit factors are stored divided by a per-element power of two; the element's result is
+  // scaled back at the scatter (exact, so the same as scaling each factor)
+  const float asc = alpha * ((gsc != nullptr && valid) ? gsc[e] : 1.0f);
 
   // tile offsets: x-line (j = a, k = b) stride 1; y-line (i = a, k = b) stride PJ; z-line
   // (i = a, j = b) stride PK. 2D: x-line (j = a), y-line (i = a).
@@ -244,7 +244,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   if constexpr (GPRE) {
     if (valid) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) load_g<DIM, N, GT>(G, g, el, qidx(k), sc, gpre + k * NC);
+      for (int k = 0; k < N; ++k) load_g<DIM, N, GT>(G, g, el, qidx(k), gpre + k * NC);
     }
   }
   float v[N], w[N];
@@ -290,7 +290,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   if constexpr (GAHEAD) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), sc, gl + k * NC);
+      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), gl + k * NC);
       else {
 #pragma unroll
         for (int c = 0; c < NC; ++c) gl[k * NC + c] = 0.0f;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   for (int k = 0; k < N; ++k) {
     float gj[GM == 2 ? NC : 1];
     if constexpr (GM == 2) {    // factors read at their use
-      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), sc, gj);
+      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), gj);
       else {
 #pragma unroll
         for (int c = 0; c < NC; ++c) gj[c] = 0.0f;
@@ -390,7 +390,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const bool bd = bd_lat | ((k == 0) & f_lo) | ((k == N - 1) & f_hi);
-      if (!bd) atomicAdd(y + nb + k * sline, alpha * w[k]);
+      if (!bd) atomicAdd(y + nb + k * sline, asc * w[k]);
     }
   }
 }
@@ -428,8 +428,8 @@ cudaError_t launch_pencil(const Mesh& m, const Basis1D& b, const float* x, float
 }
 
 // Grouped reduced-precision factors of one element per block from G[e][c][q] (FP64): FP32 as
-// they are; FP16 divided by gsc[e], the power of two that puts the element's largest |G| / gsc in
-// [0.5, 1); BF16 unscaled (gsc = nullptr). Layouts as load_g reads them; the buffer is zero-filled
+// they are (gsc = nullptr); FP16 and BF16 divided by gsc[e], the power of two that puts the
+// element's largest |G| / gsc in [0.5, 1). Layouts as load_g reads them; the buffer is zero-filled
 // beforehand, so the padding elements of the last group stay zero.
 template <typename GT>
 __global__ void k_pack_grouped(const double* __restrict__ G, GT* __restrict__ out, float* __restrict__ gsc,

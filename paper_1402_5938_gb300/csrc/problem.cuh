@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ops.cuh"
 #include "vector.cuh"
 
 namespace hmg {
@@ -21,11 +22,12 @@ struct Level {
   double* Ke = nullptr;   // element matrices of a low-order FP64 level (dense-apply variant)
   double* Kb = nullptr;   // block Jacobi: inverses of the element-interior blocks [E][MI][MI]
   double* dinv_s = nullptr;  // block Jacobi: D^-1 on shared nodes, 0 at element-interior nodes
-  float* gsc = nullptr;   // FP16: per-element power-of-two factor scales
+  float* gsc = nullptr;   // 16-bit factors: per-element power-of-two scales
+  Tc16Data tc{};          // tensor-core form of the 16-bit apply: its factor layout, Phi image, v scale
   float* dinv32 = nullptr;
   double lam = 0.0;       // Chebyshev bound
-  int v64 = 0, v32 = 0;   // apply block-shape variants chosen by the autotuner (v32: of the
-                          // V-cycle operator, FP32 or 16-bit)
+  int v64 = 0, v32 = 0;   // apply variants chosen by the autotuner (v32: of the V-cycle
+                          // operator, FP32 or 16-bit)
   double *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr;
   float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *d32 = nullptr;
   Axis1D P[3]{}, PT[3]{};  // transfer to the next coarser level: P rows fine, PT rows coarse

@@ -36,8 +36,10 @@ def _t(a, dt=torch.float64):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device=DEV, dtype=dt)
 
 
-def abs_bound_scale(d, x_full):
-    """S = sum_e |K_e|^T |G_e| |K_e| |x_e| (all factors in absolute value), full-length."""
+def abs_bound_scale(d, x_full, elem_max=False):
+    """S = sum_e |K_e|^T |G_e| |K_e| |x_e| (all factors in absolute value), full-length. With
+    elem_max, every |G_e| entry and every |x_e| entry is replaced by the element's largest one
+    (the scale of errors that are absolute relative to an element's largest value)."""
     Phi, dPhi, W = d.basis_tables()
     el = np.arange(d.n_elem)
     xq, J, detJ = d.element_geometry(el, (Phi, dPhi, W))
@@ -46,8 +48,12 @@ def abs_bound_scale(d, x_full):
     G = c[:, :, None, None] * np.einsum("eqki,eqli->eqkl", Jinv, Jinv)
     nodes = d.element_nodes(el)
     X = np.abs(x_full)[nodes]                                        # (e, a)
+    G = np.abs(G)
+    if elem_max:
+        X = np.broadcast_to(X.max(axis=1, keepdims=True), X.shape)
+        G = np.broadcast_to(G.max(axis=(1, 2, 3), keepdims=True), G.shape)
     U = np.stack([X @ np.abs(dPhi[k]).T for k in range(d.dim)], axis=-1)   # (e, q, k)
-    V = np.einsum("eqkl,eqk->eql", np.abs(G), U)
+    V = np.einsum("eqkl,eqk->eql", G, U)
     Se = sum(V[:, :, l] @ np.abs(dPhi[l]) for l in range(d.dim))    # (e, a)
     S = np.zeros(d.N)
     np.add.at(S, nodes.ravel(), Se.ravel())
