@@ -24,7 +24,8 @@
 // the scatter of a warp also touch runs of consecutive nodes. A thread's factors are loaded into
 // registers one phase before the pointwise product (after a bulk L2 prefetch of the block's factor
 // slab at the start), before the first phase (small orders), or at their use: three variants
-// that trade load latency against registers, chosen per level by timing.
+// that trade load latency against registers, chosen per level by timing; prefetched factors stay
+// in their stored form (16-bit pairs) until the pointwise product converts them.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -97,8 +98,6 @@ struct PencilCfg {
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr int NBUF = DIM == 3 ? 4 : 3;
   static constexpr size_t SMEM = (size_t)NBUF * EPB * EP * sizeof(float);
-  // factors kept in registers from the start (GPRE) only while they stay few
-  static constexpr bool PRE_OK = NC * N <= 42;
 };
 
 // Values of the grouped factor layout of one level (elements padded to whole groups of EPB).
@@ -109,35 +108,51 @@ inline size_t pencil_factor_values(int dim, int n, long long nelem) {
   return (size_t)(groups * s.epb * (dim == 3 ? 6 : 3) * np);
 }
 
-// The NC factors of point q of element slot el of group g, as FP32 (16-bit factors as stored,
-// i.e. divided by the element's scale, which the caller applies to the element's result).
-// FP32: [g][NC][NP][EPB]; 16-bit, 3D: pairs of components as 32-bit words [g][3][NP][EPB];
-// 16-bit, 2D: [g][3][NP][EPB].
+// Words of point q's factors as stored (RW per point: FP32 NC values; 16-bit 3D three pairs;
+// 16-bit 2D three values, one per word), so that prefetched factors occupy half the registers
+// in 16 bits; unpack_g converts them to FP32 at their use.
+template <int DIM, typename GT>
+struct RawG {
+  static constexpr int RW = std::is_same<GT, float>::value ? (DIM == 3 ? 6 : 3) : 3;
+};
 template <int DIM, int N, typename GT>
-__device__ __forceinline__ void load_g(const GT* __restrict__ G, long long g, int el, int q, float* v) {
+__device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, int el, int q, uint32_t* w) {
   using C = PencilCfg<DIM, N>;
   constexpr int NP = C::NP, NC = C::NC, EPB = C::EPB;
   if constexpr (std::is_same<GT, float>::value) {
     const float* p = G + (g * NC * NP + q) * EPB + el;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) v[c] = __ldg(p + (long long)c * NP * EPB);
+    for (int c = 0; c < NC; ++c) w[c] = __float_as_uint(__ldg(p + (long long)c * NP * EPB));
   } else if constexpr (DIM == 3) {
     const unsigned* p = reinterpret_cast<const unsigned*>(G) + (g * 3 * NP + q) * EPB + el;
 #pragma unroll
-    for (int w = 0; w < 3; ++w) {
-      const unsigned u = __ldg(p + (long long)w * NP * EPB);
-      float2 f;
-      if constexpr (std::is_same<GT, __half>::value) f = __half22float2(*reinterpret_cast<const __half2*>(&u));
-      else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
-      v[2 * w] = f.x;
-      v[2 * w + 1] = f.y;
-    }
+    for (int c = 0; c < 3; ++c) w[c] = __ldg(p + (long long)c * NP * EPB);
   } else {
-    const GT* p = G + (g * 3 * NP + q) * EPB + el;
+    const unsigned short* p = reinterpret_cast<const unsigned short*>(G) + (g * 3 * NP + q) * EPB + el;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c] = __ldg(p + (long long)c * NP * EPB);
+  }
+}
+template <int DIM, typename GT>
+__device__ __forceinline__ void unpack_g(const uint32_t* w, float* v) {
+  if constexpr (std::is_same<GT, float>::value) {
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? 6 : 3); ++c) v[c] = __uint_as_float(w[c]);
+  } else if constexpr (DIM == 3) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      if constexpr (std::is_same<GT, __half>::value) v[c] = __half2float(p[(long long)c * NP * EPB]);
-      else v[c] = __bfloat162float(p[(long long)c * NP * EPB]);
+      float2 f;
+      if constexpr (std::is_same<GT, __half>::value) f = __half22float2(*reinterpret_cast<const __half2*>(&w[c]));
+      else f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[c]));
+      v[2 * c] = f.x;
+      v[2 * c + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const unsigned short u = (unsigned short)w[c];
+      if constexpr (std::is_same<GT, __half>::value) v[c] = __half2float(__ushort_as_half(u));
+      else v[c] = __bfloat162float(__ushort_as_bfloat16(u));
     }
   }
 }
@@ -240,11 +255,16 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
 
   constexpr bool GPRE = GM == 1;       // factors loaded before the first phase
   constexpr bool GAHEAD = GM == 0;     // ... one phase before the pointwise product
-  float gpre[GPRE ? NC * N : 1];
+  constexpr int RW = RawG<DIM, GT>::RW;
+  uint32_t gpre[GPRE ? RW * N : 1];
   if constexpr (GPRE) {
-    if (valid) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) load_g<DIM, N, GT>(G, g, el, qidx(k), gpre + k * NC);
+    for (int k = 0; k < N; ++k) {
+      if (valid) load_raw<DIM, N, GT>(G, g, el, qidx(k), gpre + k * RW);
+      else {
+#pragma unroll
+        for (int c = 0; c < RW; ++c) gpre[k * RW + c] = 0u;
+      }
     }
   }
   float v[N], w[N];
@@ -286,14 +306,14 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   __syncthreads();
   // the thread's factors: loaded here (unless GPRE loaded them at the start), one phase before
   // the pointwise product needs them, so that their latency overlaps the derivative phase
-  float gl[GAHEAD ? NC * N : 1];
+  uint32_t gl[GAHEAD ? RW * N : 1];
   if constexpr (GAHEAD) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), gl + k * NC);
+      if (valid) load_raw<DIM, N, GT>(G, g, el, qidx(k), gl + k * RW);
       else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) gl[k * NC + c] = 0.0f;
+        for (int c = 0; c < RW; ++c) gl[k * RW + c] = 0u;
       }
     }
   }
@@ -322,15 +342,16 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   float vl[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    float gj[GM == 2 ? NC : 1];
+    uint32_t gj[GM == 2 ? RW : 1];
     if constexpr (GM == 2) {    // factors read at their use
-      if (valid) load_g<DIM, N, GT>(G, g, el, qidx(k), gj);
+      if (valid) load_raw<DIM, N, GT>(G, g, el, qidx(k), gj);
       else {
 #pragma unroll
-        for (int c = 0; c < NC; ++c) gj[c] = 0.0f;
+        for (int c = 0; c < RW; ++c) gj[c] = 0u;
       }
     }
-    const float* gv = GM == 2 ? gj : (GPRE ? gpre + k * NC : gl + k * NC);
+    float gv[NC];
+    unpack_g<DIM, GT>(GM == 2 ? gj : (GPRE ? gpre + k * RW : gl + k * RW), gv);
     const float ux = GX[ol + k * SL];
     if (DIM == 3) {
       const float uy = GY[ol + k * SL];
@@ -423,13 +444,14 @@ template <int DIM, int N, typename GT>
 cudaError_t launch_pencil(const Mesh& m, const Basis1D& b, const float* x, float* y, const GT* G, const float* gsc,
                           float alpha, int variant, cudaStream_t s) {
   if (variant == 2) return launch_pencil_gm<DIM, N, GT, 2>(m, b, x, y, G, gsc, alpha, s);
-  if (variant == 1 && PencilCfg<DIM, N>::PRE_OK) return launch_pencil_gm<DIM, N, GT, 1>(m, b, x, y, G, gsc, alpha, s);
+  // factors kept in registers from the start only while they stay few
+  if (variant == 1 && RawG<DIM, GT>::RW * N <= 42) return launch_pencil_gm<DIM, N, GT, 1>(m, b, x, y, G, gsc, alpha, s);
   return launch_pencil_gm<DIM, N, GT, 0>(m, b, x, y, G, gsc, alpha, s);
 }
 
 // Grouped reduced-precision factors of one element per block from G[e][c][q] (FP64): FP32 as
 // they are (gsc = nullptr); FP16 and BF16 divided by gsc[e], the power of two that puts the
-// element's largest |G| / gsc in [0.5, 1). Layouts as load_g reads them; the buffer is zero-filled
+// element's largest |G| / gsc in [0.5, 1). Layouts as load_raw reads them; the buffer is zero-filled
 // beforehand, so the padding elements of the last group stay zero.
 template <typename GT>
 __global__ void k_pack_grouped(const double* __restrict__ G, GT* __restrict__ out, float* __restrict__ gsc,

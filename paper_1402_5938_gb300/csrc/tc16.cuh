@@ -16,10 +16,10 @@
 // point (read coalesced, one tile ahead in L2) and the tile's nodes.
 //
 // A tile is a block of 8 x 4 x 4 elements. Its nodes form a box of (8p+1) x (4p+1) x (4p+1)
-// nodes that is gathered once, row by row with asynchronous copies (consecutive lanes, consecutive
-// nodes), into shared memory, from where each element takes its n^3 values: element-wise loads
-// touch 16 sectors per warp access and cost several times more. The element results are added
-// into y with one atomic per element node.
+// nodes that is gathered once, row by row (consecutive lanes, consecutive nodes), into shared
+// memory, from where each element takes its n^3 values: element-wise loads touch 16 sectors per
+// warp access and cost several times more. The element results are added into y with one atomic
+// per element node.
 //
 // Operands of the products are FP16: each element's nodal values are divided by a power of two
 // (largest |x| / s_x in [0.5, 1)), the factors are stored divided by a per-element power of two
@@ -80,6 +80,7 @@ struct Tc16Cfg {
   static constexpr int TMEM_COLS = 4 * NPAD <= 32 ? 32 : 4 * NPAD <= 64 ? 64 : 4 * NPAD <= 128 ? 128 : 4 * NPAD <= 256 ? 256 : 512;
   static constexpr int THREADS = 17 * 32;
   static_assert(TBX * TBY * TBZ == M, "tile block");
+  static_assert(BX <= 64, "a box row is read by two loads per lane");
   static_assert(4 * NPAD <= 512, "grad u and y of a tile must fit tensor memory");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -186,10 +187,6 @@ __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void box_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // First element (ex0, ey0, ez0) of tile t of mesh m (tiles x fastest).
@@ -294,16 +291,25 @@ k_apply_tc16(const float* __restrict__ x, float* __restrict__ y, const uint32_t*
         const int by = (int)(m.Nn[1] - gy0 < BY ? m.Nn[1] - gy0 : BY);
         const int bz = (int)(m.Nn[2] - gz0 < C::BZ ? m.Nn[2] - gz0 : C::BZ);
         const float* xb = x + gz0 * nxy + gy0 * nx + gx0;
-        int ry = warp, rz = 0;
-        while (ry >= by) { ry -= by; ++rz; }
-        for (; rz < bz;) {
-          const float* src = xb + rz * nxy + ry * nx;
-          float* dst = sBox + (rz * BY + ry) * BX;
-          for (int c = lane; c < bx; c += 32) cp_async4(dst + c, src + c);
-          ry += 4;
-          while (ry >= by) { ry -= by; ++rz; }
+        // rows in rounds of 8 per warp, all loads of a round in flight before the stores
+        const int nrows = by * bz;
+        for (int r0 = warp * 8; r0 < nrows; r0 += 32) {
+          float a[8], b[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int r = r0 + q, ry = r % by, rz = r / by;
+            const float* src = xb + rz * nxy + ry * nx;
+            a[q] = (r < nrows && lane < bx) ? __ldg(src + lane) : 0.0f;
+            b[q] = (r < nrows && lane + 32 < bx) ? __ldg(src + lane + 32) : 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int r = r0 + q, ry = r % by, rz = r / by;
+            float* dst = sBox + (rz * BY + ry) * BX;
+            if (r < nrows && lane < bx) dst[lane] = a[q];
+            if (r < nrows && lane + 32 < bx) dst[lane + 32] = b[q];
+          }
         }
-        cp_async_wait_all();
         box_sync();
         const Elem q = elem(t);
         if (i > 0) tc_wait(d1_full, (uint32_t)((i - 1) & 1), abort, err);  // X read by the last product
