@@ -98,7 +98,7 @@ template <int DIM, int N, typename GT>
 __global__ void __launch_bounds__(PencilCfg<DIM, N>::THREADS)
 kb_apply_low(const float* __restrict__ X, float* __restrict__ Y, const BLev* __restrict__ lev,
              const int2* __restrict__ tab, const int* __restrict__ gid, const int* __restrict__ active,
-             const __grid_constant__ Tab<N, float> t1d, const float alpha) {
+             const __grid_constant__ PencilTab<N, float> t1d, const float alpha) {
   const int2 w = tab[blockIdx.x];
   if (!active[gid[w.x]]) return;
   const BLev& L = lev[w.x];
@@ -535,7 +535,7 @@ struct GroupRun {
         cudaError_t e2 = ensure_smem(kern, C::SMEM);
         if (e2 != cudaSuccess) return e2;
         kern<<<n, C::THREADS, C::SMEM, s>>>(x, y, G.d_lev[k], G.d_tlow[k], G.d_gid, B.active,
-                                            make_tab<N, float>(basis), alpha);
+                                            make_pencil_tab<N, float>(basis), alpha);
         return counted(cudaGetLastError());
       };
       auto by_prec = [&](auto dc) -> cudaError_t {

@@ -574,6 +574,16 @@ void tune_cache_store(const TuneKey& k, int v) {
   }
 }
 
+// Apply variants a level can run: FP64 (the point-parallel shapes, stored element matrices, the
+// FP64 pencil form) or the mixed V-cycle's operator (pencil factor-load timings, tensor-core form).
+std::vector<int> level_variants(const Level& l, bool vcycle_op) {
+  if (!vcycle_op) return apply64_variants(l.m.p + 1, l.Ke != nullptr);
+  std::vector<int> v;
+  for (int k = 0; k < kApplyLowVariants; ++k) v.push_back(k);
+  if (l.tc.G) v.push_back(kApplyLowTc);
+  return v;
+}
+
 hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   if (!autotune_on()) return HMG_OK;
   // tiny levels run at the launch-latency floor whatever the block shape: variant 0 unless the
@@ -593,8 +603,8 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     {
       std::lock_guard<std::mutex> lk(mu);
       auto it = cache.find(key);
-      const int nv = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : kApplyLowVariants + (l.tc.G ? 1 : 0);
-      if (it != cache.end() && it->second >= 0 && it->second < nv) {  // a decision this level can run
+      const std::vector<int> cand = level_variants(l, prec != 0);
+      if (it != cache.end() && std::find(cand.begin(), cand.end(), it->second) != cand.end()) {  // one this level can run
         (prec ? l.v32 : l.v64) = it->second;
         continue;
       }
@@ -606,8 +616,8 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
     float best = 1e30f;
     int bv = 0;
     cudaError_t err = cudaSuccess;
-    const int nvar = prec == 0 ? kApply64Variants + (l.Ke ? 1 : 0) : kApplyLowVariants + (l.tc.G ? 1 : 0);
-    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
+    for (int v : level_variants(l, prec != 0)) {
+      if (err != cudaSuccess) break;
       auto run = [&]() {
         if (prec == 0) return launch_apply_f64(l.m, l.basis, l.x, l.r, l.G, 1.0, P.err, s, v, l.Ke);
         return launch_apply_low(l.m, l.basis, l.x32, l.r32, l.Glow, l.gsc, 1.0f, P.desc.smooth_prec, s, v, &l.tc,

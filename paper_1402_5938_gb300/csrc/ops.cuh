@@ -10,13 +10,27 @@ namespace hmg {
 
 // y += alpha * A x in FP64 (G [E][NC][NP] in FP64). Variant 3 stages G with bulk TMA copies (when
 // the slab fits in shared memory) and needs G allocated with >= 16 bytes of tail padding; a
-// timed-out wait sets *err (device int) to a nonzero code. `variant` selects the block shape
-// (0..3, 3 = TMA-staged G); setup picks it per level by timing (autotuning).
-constexpr int kApply64Variants = 4;
+// timed-out wait sets *err (device int) to a nonzero code. `variant` selects the form (0..3
+// point-parallel block shapes, 3 = TMA-staged G; 4 dense; 5, 6 pencil, below); setup picks it per
+// level by timing (autotuning).
 // FP64 variant kApply64Dense: stored element matrices Ke (launch_elem_mats) instead of sum
 // factorization, for orders with N <= kMaxNDense; other variants ignore Ke.
 constexpr int kApply64Dense = 4;
 constexpr int kMaxNDense = 3;
+// FP64 variants 5 and 6: the pencil form (one thread per element line, even/odd line products from
+// order 4 on) in FP64 arithmetic on G as stored, factors read at their use (5) or one phase ahead
+// (6, orders with N <= kPencil64AheadMaxN).
+constexpr int kApply64Pencil = 5;
+constexpr int kApply64PencilAhead = 6;
+constexpr int kPencil64AheadMaxN = 9;
+// The FP64 variants a level can run: 0-3, 4 with element matrices, 5, and 6 for N <= 9.
+inline std::vector<int> apply64_variants(int n, bool has_ke) {
+  std::vector<int> v = {0, 1, 2, 3};
+  if (has_ke) v.push_back(kApply64Dense);
+  v.push_back(kApply64Pencil);
+  if (n <= kPencil64AheadMaxN) v.push_back(kApply64PencilAhead);
+  return v;
+}
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, int* err, cudaStream_t s, int variant = 0,
                              const double* Ke = nullptr);

@@ -1,8 +1,11 @@
-// Instantiation and launch of the FP64 operator-apply kernel (all orders, three block shapes).
+// Instantiation and launch of the FP64 operator apply: the point-parallel kernel (all orders, four
+// block shapes), stored element matrices (orders 1-2), and the pencil form in FP64 arithmetic with
+// even/odd line products (pencil.cuh).
 #include <algorithm>
 
 #include "dispatch.cuh"
 #include "ops.cuh"
+#include "pencil.cuh"
 
 namespace hmg {
 
@@ -56,9 +59,25 @@ cudaError_t apply_dense64_dim(const Mesh& m, const Basis1D& b, const double* x, 
   });
 }
 
+template <int DIM>
+cudaError_t apply_pencil64_dim(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* G,
+                               double alpha, int variant, cudaStream_t s) {
+  return dispatch_n(b.n, [&](auto nc) -> cudaError_t {
+    constexpr int N = decltype(nc)::value;
+    if constexpr (N <= kPencil64AheadMaxN) {
+      if (variant == kApply64PencilAhead)
+        return launch_pencil_gm<DIM, N, double, 0, double>(m, b, x, y, G, nullptr, alpha, s);
+    }
+    return launch_pencil_gm<DIM, N, double, 2, double>(m, b, x, y, G, nullptr, alpha, s);
+  });
+}
+
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, int* err, cudaStream_t s, int variant,
                              const double* Ke) {
+  if (variant == kApply64Pencil || variant == kApply64PencilAhead)
+    return m.dim == 3 ? apply_pencil64_dim<3>(m, b, x, y, G, alpha, variant, s)
+                      : apply_pencil64_dim<2>(m, b, x, y, G, alpha, variant, s);
   if (variant == kApply64Dense && Ke != nullptr)
     return m.dim == 3 ? apply_dense64_dim<3>(m, b, x, y, Ke, alpha, s) : apply_dense64_dim<2>(m, b, x, y, Ke, alpha, s);
   return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, err, variant, s)

@@ -85,7 +85,7 @@ __host__ __device__ constexpr PencilShape pencil_shape(int dim, int n) {
   }
 }
 
-template <int DIM, int N>
+template <int DIM, int N, typename T = float>
 struct PencilCfg {
   static constexpr PencilShape SH = pencil_shape(DIM, N);
   static constexpr int NL = DIM == 3 ? N * N : N;           // lines per direction per element
@@ -97,7 +97,7 @@ struct PencilCfg {
   static constexpr int LINES = EPB * NL;
   static constexpr int THREADS = (LINES + 31) / 32 * 32;
   static constexpr int NBUF = DIM == 3 ? 4 : 3;
-  static constexpr size_t SMEM = (size_t)NBUF * EPB * EP * sizeof(float);
+  static constexpr size_t SMEM = (size_t)NBUF * EPB * EP * sizeof(T);
 };
 
 // Values of the grouped factor layout of one level (elements padded to whole groups of EPB).
@@ -108,18 +108,84 @@ inline size_t pencil_factor_values(int dim, int n, long long nelem) {
   return (size_t)(groups * s.epb * (dim == 3 ? 6 : 3) * np);
 }
 
-// Words of point q's factors as stored (RW per point: FP32 NC values; 16-bit 3D three pairs;
-// 16-bit 2D three values, one per word), so that prefetched factors occupy half the registers
-// in 16 bits; unpack_g converts them to FP32 at their use.
+// 1D tables of the pencil form: B (GLL -> Gauss interpolation, B[q][a]) and D (collocated Gauss
+// derivative, D[q][s]) as plain N x N arrays, and the four products a line goes through (B, D,
+// B^T, D^T) in even/odd form. B's nodes and points are symmetric about the element's centre, so
+// A[N-1-i][N-1-j] = s A[i][j] with s = +1 for B and B^T, -1 for D and D^T; with e_j = x_j + x_{N-1-j},
+// o_j = x_j - x_{N-1-j} (j < H = N/2) the product y = A x becomes, for i < H,
+//   a_i = sum_j E_ij e_j (+ A_iH x_H for odd N),  b_i = sum_j O_ij o_j,  y_i = a_i + b_i,
+//   y_{N-1-i} = s (a_i - b_i),
+// E_ij = (A_ij + A_i,N-1-j) / 2, O_ij = (A_ij - A_i,N-1-j) / 2, and for odd N the middle output
+// y_H = sum_j A_Hj (e_j or o_j) (+ A_HH x_H for s = +1): 21 operations instead of 25 at N = 5, 57
+// instead of 81 at N = 9, 177 instead of 289 at N = 17. Packing of each even/odd table: E at
+// [0, H^2), O at [H^2, 2H^2), the middle column A_iH at [2H^2, 2H^2 + H), the middle row A_Hj at
+// [2H^2 + H, 2H^2 + 2H), A_HH at 2H^2 + 2H.
+template <int N, typename T>
+struct PencilTab {
+  T B[N * N];
+  T D[N * N];
+  T eB[N * N], eD[N * N], eBt[N * N], eDt[N * N];
+};
+// Even/odd products pay from N = 5 on (N = 2..4 break even or lose).
+template <int N>
+constexpr bool kUseEvenOdd = N >= 5;
+
+inline void pack_even_odd(int n, const double* A /* A[i * n + j] */, double* out) {
+  const int h = n / 2;
+  for (int i = 0; i < h; ++i)
+    for (int j = 0; j < h; ++j) {
+      out[i * h + j] = 0.5 * (A[i * n + j] + A[i * n + n - 1 - j]);
+      out[h * h + i * h + j] = 0.5 * (A[i * n + j] - A[i * n + n - 1 - j]);
+    }
+  if (n % 2) {
+    for (int i = 0; i < h; ++i) out[2 * h * h + i] = A[i * n + h];
+    for (int j = 0; j < h; ++j) out[2 * h * h + h + j] = A[h * n + j];
+    out[2 * h * h + 2 * h] = A[h * n + h];
+  }
+}
+
+template <int N, typename T>
+PencilTab<N, T> make_pencil_tab(const Basis1D& b) {
+  PencilTab<N, T> t{};
+  double Bt[N * N], Dt[N * N], pk[N * N];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      t.B[i * N + j] = (T)b.B[i * N + j];
+      t.D[i * N + j] = (T)b.D[i * N + j];
+      Bt[i * N + j] = b.B[j * N + i];
+      Dt[i * N + j] = b.D[j * N + i];
+    }
+  const double* src[4] = {b.B, b.D, Bt, Dt};
+  T* dst[4] = {t.eB, t.eD, t.eBt, t.eDt};
+  for (int k = 0; k < 4; ++k) {
+    for (int i = 0; i < N * N; ++i) pk[i] = 0.0;
+    pack_even_odd(N, src[k], pk);
+    for (int i = 0; i < N * N; ++i) dst[k][i] = (T)pk[i];
+  }
+  return t;
+}
+
+// Words of point q's factors as stored, so that prefetched factors keep their stored width
+// (16-bit: half the registers of FP32 values) until unpack_g converts them at their use.
+// Grouped layouts (FP32, FP16, BF16): RW words per point, 32-bit words (FP32 values; 16-bit 3D
+// three component pairs; 16-bit 2D three values, one per word). FP64 factors are read from the
+// element-major layout G[e][c][q] of the FP64 operator, NC doubles per point.
 template <int DIM, typename GT>
 struct RawG {
-  static constexpr int RW = std::is_same<GT, float>::value ? (DIM == 3 ? 6 : 3) : 3;
+  static constexpr bool F64 = std::is_same<GT, double>::value;
+  using W = typename std::conditional<F64, double, uint32_t>::type;
+  static constexpr int RW = F64 ? (DIM == 3 ? 6 : 3) : std::is_same<GT, float>::value ? (DIM == 3 ? 6 : 3) : 3;
 };
 template <int DIM, int N, typename GT>
-__device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, int el, int q, uint32_t* w) {
+__device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, int el, int q,
+                                         typename RawG<DIM, GT>::W* w) {
   using C = PencilCfg<DIM, N>;
   constexpr int NP = C::NP, NC = C::NC, EPB = C::EPB;
-  if constexpr (std::is_same<GT, float>::value) {
+  if constexpr (std::is_same<GT, double>::value) {
+    const double* p = G + (g * EPB + el) * NC * NP + q;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) w[c] = __ldg(p + c * NP);
+  } else if constexpr (std::is_same<GT, float>::value) {
     const float* p = G + (g * NC * NP + q) * EPB + el;
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = __float_as_uint(__ldg(p + (long long)c * NP * EPB));
@@ -133,9 +199,12 @@ __device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, 
     for (int c = 0; c < 3; ++c) w[c] = __ldg(p + (long long)c * NP * EPB);
   }
 }
-template <int DIM, typename GT>
-__device__ __forceinline__ void unpack_g(const uint32_t* w, float* v) {
-  if constexpr (std::is_same<GT, float>::value) {
+template <int DIM, typename GT, typename T>
+__device__ __forceinline__ void unpack_g(const typename RawG<DIM, GT>::W* w, T* v) {
+  if constexpr (std::is_same<GT, double>::value) {
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? 6 : 3); ++c) v[c] = w[c];
+  } else if constexpr (std::is_same<GT, float>::value) {
 #pragma unroll
     for (int c = 0; c < (DIM == 3 ? 6 : 3); ++c) v[c] = __uint_as_float(w[c]);
   } else if constexpr (DIM == 3) {
@@ -158,27 +227,84 @@ __device__ __forceinline__ void unpack_g(const uint32_t* w, float* v) {
 }
 
 // out[i] = sum_m M[i*N + m] in[m] (TRN: M[m*N + i]), M a parameter-space table
-template <int N, bool TRN>
-__device__ __forceinline__ void mat1d(const float* __restrict__ M, const float* in, float* out) {
+template <int N, bool TRN, typename T>
+__device__ __forceinline__ void mat1d(const T* __restrict__ M, const T* in, T* out) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    float s = (TRN ? M[i] : M[i * N]) * in[0];
+    T s = (TRN ? M[i] : M[i * N]) * in[0];
 #pragma unroll
-    for (int m = 1; m < N; ++m) s = fmaf(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
+    for (int m = 1; m < N; ++m) s = fma(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
     out[i] = s;
   }
 }
 // out[i] = acc[i] + sum_m M[m*N + i] in[m]
-template <int N>
-__device__ __forceinline__ void mat1d_t_acc(const float* __restrict__ M, const float* in, const float* acc,
-                                            float* out) {
+template <int N, typename T>
+__device__ __forceinline__ void mat1d_t_acc(const T* __restrict__ M, const T* in, const T* acc, T* out) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    float s = acc[i];
+    T s = acc[i];
 #pragma unroll
-    for (int m = 0; m < N; ++m) s = fmaf(M[m * N + i], in[m], s);
+    for (int m = 0; m < N; ++m) s = fma(M[m * N + i], in[m], s);
     out[i] = s;
   }
+}
+// out = A in with A given by its even/odd packing Q (PencilTab) and symmetry sign S
+template <int N, int S, typename T>
+__device__ __forceinline__ void mat1d_eo(const T* __restrict__ Q, const T* in, T* out) {
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N & 1) != 0;
+  T e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = in[j] + in[N - 1 - j];
+    o[j] = in[j] - in[N - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T a = Q[i * H] * e[0];
+#pragma unroll
+    for (int j = 1; j < H; ++j) a = fma(Q[i * H + j], e[j], a);
+    if constexpr (ODD) a = fma(Q[2 * H * H + i], in[H], a);
+    T b = Q[H * H + i * H] * o[0];
+#pragma unroll
+    for (int j = 1; j < H; ++j) b = fma(Q[H * H + i * H + j], o[j], b);
+    out[i] = a + b;
+    out[N - 1 - i] = S > 0 ? a - b : b - a;
+  }
+  if constexpr (ODD) {
+    if constexpr (S > 0) {
+      T c = Q[2 * H * H + 2 * H] * in[H];
+#pragma unroll
+      for (int j = 0; j < H; ++j) c = fma(Q[2 * H * H + H + j], e[j], c);
+      out[H] = c;
+    } else {
+      T c = Q[2 * H * H + H] * o[0];
+#pragma unroll
+      for (int j = 1; j < H; ++j) c = fma(Q[2 * H * H + H + j], o[j], c);
+      out[H] = c;
+    }
+  }
+}
+// The four line products of the pencil form: even/odd where that saves operations, else plain.
+template <int N, typename T>
+__device__ __forceinline__ void line_B(const PencilTab<N, T>& t, const T* in, T* out) {
+  if constexpr (kUseEvenOdd<N>) mat1d_eo<N, 1>(t.eB, in, out);
+  else mat1d<N, false>(t.B, in, out);
+}
+template <int N, typename T>
+__device__ __forceinline__ void line_D(const PencilTab<N, T>& t, const T* in, T* out) {
+  if constexpr (kUseEvenOdd<N>) mat1d_eo<N, -1>(t.eD, in, out);
+  else mat1d<N, false>(t.D, in, out);
+}
+template <int N, typename T>
+__device__ __forceinline__ void line_Bt(const PencilTab<N, T>& t, const T* in, T* out) {
+  if constexpr (kUseEvenOdd<N>) mat1d_eo<N, 1>(t.eBt, in, out);
+  else mat1d<N, true>(t.B, in, out);
+}
+template <int N, typename T>
+__device__ __forceinline__ void line_Dt(const PencilTab<N, T>& t, const T* in, T* out) {
+  if constexpr (kUseEvenOdd<N>) mat1d_eo<N, -1>(t.eDt, in, out);
+  else mat1d<N, true>(t.D, in, out);
 }
 
 // Byte range [p, p + bytes) rounded out to 16 bytes and prefetched into L2 by bulk operations
@@ -194,19 +320,19 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, size_t bytes) {
 }
 
 // One tile: the group g of EPB elements e0 = g * EPB, ... of mesh m (those below m.nelem),
-// y += alpha A x; `sm` holds PencilCfg::SMEM bytes.
-template <int DIM, int N, typename GT, int GM>
-__device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* __restrict__ y,
+// y += alpha A x in arithmetic T (FP32 with FP32 / 16-bit grouped factors, FP64 with the FP64
+// operator's element-major factors); `sm` holds PencilCfg<DIM, N, T>::SMEM bytes.
+template <int DIM, int N, typename GT, int GM, typename T = float>
+__device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restrict__ y,
                                             const GT* __restrict__ G, const float* __restrict__ gsc, const Mesh& m,
-                                            const Tab<N, float>& tab, const float alpha, const long long g,
-                                            float* sm) {
-  using C = PencilCfg<DIM, N>;
+                                            const PencilTab<N, T>& tab, const T alpha, const long long g, T* sm) {
+  using C = PencilCfg<DIM, N, T>;
   constexpr int NL = C::NL, NP = C::NP, NC = C::NC, PJ = C::PJ, PK = C::PK, EP = C::EP, EPB = C::EPB;
-  constexpr int TS = EPB * EP;       // floats per buffer
-  float* S = sm;                     // interpolation passes (forward and transposed)
-  float* U = S + TS;                 // u at the Gauss points, later the transposed-derivative sum W
-  float* GX = U + TS;                // u_x, later v_x
-  float* GY = GX + TS;               // u_y, later v_y (3D)
+  constexpr int TS = EPB * EP;       // values per buffer
+  T* S = sm;                         // interpolation passes (forward and transposed)
+  T* U = S + TS;                     // u at the Gauss points, later the transposed-derivative sum W
+  T* GX = U + TS;                    // u_x, later v_x
+  T* GY = GX + TS;                   // u_y, later v_y (3D)
   const int t = threadIdx.x;
   const int el = t % EPB;            // element slot of the group
   const int l = t / EPB;             // line of the element
@@ -219,8 +345,11 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   const int a = act ? l % N : 0, b = (DIM == 3 && act) ? l / N : 0;   // line coordinates
   const int eb = act ? el * EP : 0;
   if (t == 0) {
+    // the group's factors (element-major FP64: only the elements of the mesh, the allocation ends
+    // at the last one; grouped layouts are padded to whole groups)
+    const long long ng = std::is_same<GT, double>::value ? (m.nelem - e0 < EPB ? m.nelem - e0 : EPB) : EPB;
     const size_t gbytes = sizeof(GT) * (size_t)NC * NP * EPB;
-    bulk_prefetch_l2(reinterpret_cast<const char*>(G) + g * gbytes, gbytes);
+    bulk_prefetch_l2(reinterpret_cast<const char*>(G) + g * gbytes, sizeof(GT) * (size_t)NC * NP * ng);
   }
   // element position, global node of the line's first node, and boundary masks
   long long nb = 0;
@@ -244,7 +373,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   const int f_hi = DIM == 3 ? ((fl >> 5) & 1) : ((fl >> 3) & 1);
   // 16-bit factors are stored divided by a per-element power of two; the element's result is
   // scaled back at the scatter (exact, so the same as scaling each factor)
-  const float asc = alpha * ((gsc != nullptr && valid) ? gsc[e] : 1.0f);
+  const T asc = alpha * (T)((gsc != nullptr && valid) ? gsc[e] : 1.0f);
 
   // tile offsets: x-line (j = a, k = b) stride 1; y-line (i = a, k = b) stride PJ; z-line
   // (i = a, j = b) stride PK. 2D: x-line (j = a), y-line (i = a).
@@ -256,25 +385,26 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   constexpr bool GPRE = GM == 1;       // factors loaded before the first phase
   constexpr bool GAHEAD = GM == 0;     // ... one phase before the pointwise product
   constexpr int RW = RawG<DIM, GT>::RW;
-  uint32_t gpre[GPRE ? RW * N : 1];
+  using GW = typename RawG<DIM, GT>::W;
+  GW gpre[GPRE ? RW * N : 1];
   if constexpr (GPRE) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if (valid) load_raw<DIM, N, GT>(G, g, el, qidx(k), gpre + k * RW);
       else {
 #pragma unroll
-        for (int c = 0; c < RW; ++c) gpre[k * RW + c] = 0u;
+        for (int c = 0; c < RW; ++c) gpre[k * RW + c] = GW(0);
       }
     }
   }
-  float v[N], w[N];
+  T v[N], w[N];
   // ---- gather along the thread's line (z in 3D, y in 2D) and interpolate along it
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const bool bd = bd_lat | ((k == 0) & f_lo) | ((k == N - 1) & f_hi);
-    v[k] = (valid && !bd) ? __ldg(x + nb + k * sline) : 0.0f;
+    v[k] = (valid && !bd) ? __ldg(x + nb + k * sline) : T(0);
   }
-  mat1d<N, false>(tab.B, v, w);
+  line_B<N>(tab, v, w);
   if (DIM == 3) {
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -283,7 +413,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
     // y-lines: interpolate along y
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = S[oy + k * PJ];
-    mat1d<N, false>(tab.B, v, w);
+    line_B<N>(tab, v, w);
 #pragma unroll
     for (int k = 0; k < N; ++k)
       if (act) S[oy + k * PJ] = w[k];
@@ -296,8 +426,8 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   // ---- x-lines: interpolate along x, differentiate along x
 #pragma unroll
   for (int k = 0; k < N; ++k) v[k] = S[ox + k];
-  mat1d<N, false>(tab.B, v, w);
-  mat1d<N, false>(tab.D, w, v);
+  line_B<N>(tab, v, w);
+  line_D<N>(tab, w, v);
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     if (act) U[ox + k] = w[k];
@@ -306,55 +436,55 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   __syncthreads();
   // the thread's factors: loaded here (unless GPRE loaded them at the start), one phase before
   // the pointwise product needs them, so that their latency overlaps the derivative phase
-  uint32_t gl[GAHEAD ? RW * N : 1];
+  GW gl[GAHEAD ? RW * N : 1];
   if constexpr (GAHEAD) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       if (valid) load_raw<DIM, N, GT>(G, g, el, qidx(k), gl + k * RW);
       else {
 #pragma unroll
-        for (int c = 0; c < RW; ++c) gl[k * RW + c] = 0u;
+        for (int c = 0; c < RW; ++c) gl[k * RW + c] = GW(0);
       }
     }
   }
-  float uz[N];
+  T uz[N];
   if (DIM == 3) {
     // y-lines: u_y; z-lines: u_z (kept in registers)
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = U[oy + k * PJ];
-    mat1d<N, false>(tab.D, v, w);
+    line_D<N>(tab, v, w);
 #pragma unroll
     for (int k = 0; k < N; ++k)
       if (act) GY[oy + k * PJ] = w[k];
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = U[oz + k * PK];
-    mat1d<N, false>(tab.D, v, uz);
+    line_D<N>(tab, v, uz);
     __syncthreads();
   } else {
     // 2D y-lines: u_y in registers
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = U[oy + k * PJ];
-    mat1d<N, false>(tab.D, v, uz);
+    line_D<N>(tab, v, uz);
   }
   // ---- the thread's line (z in 3D, y in 2D): v = G grad u at its points, then D^T along it
   const int ol = DIM == 3 ? oz : oy;
   constexpr int SL = DIM == 3 ? PK : PJ;
-  float vl[N];
+  T vl[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    uint32_t gj[GM == 2 ? RW : 1];
+    GW gj[GM == 2 ? RW : 1];
     if constexpr (GM == 2) {    // factors read at their use
       if (valid) load_raw<DIM, N, GT>(G, g, el, qidx(k), gj);
       else {
 #pragma unroll
-        for (int c = 0; c < RW; ++c) gj[c] = 0u;
+        for (int c = 0; c < RW; ++c) gj[c] = GW(0);
       }
     }
-    float gv[NC];
+    T gv[NC];
     unpack_g<DIM, GT>(GM == 2 ? gj : (GPRE ? gpre + k * RW : gl + k * RW), gv);
-    const float ux = GX[ol + k * SL];
+    const T ux = GX[ol + k * SL];
     if (DIM == 3) {
-      const float uy = GY[ol + k * SL];
+      const T uy = GY[ol + k * SL];
       if (act) GX[ol + k * SL] = gv[0] * ux + gv[1] * uy + gv[2] * uz[k];
       if (act) GY[ol + k * SL] = gv[1] * ux + gv[3] * uy + gv[4] * uz[k];
       vl[k] = gv[2] * ux + gv[4] * uy + gv[5] * uz[k];
@@ -363,7 +493,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
       vl[k] = gv[1] * ux + gv[2] * uz[k];
     }
   }
-  mat1d<N, true>(tab.D, vl, w);
+  line_Dt<N>(tab, vl, w);
 #pragma unroll
   for (int k = 0; k < N; ++k)
     if (act) U[ol + k * SL] = w[k];
@@ -388,7 +518,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
     vl[k] = U[ox + k];
   }
   mat1d_t_acc<N>(tab.D, v, vl, w);
-  mat1d<N, true>(tab.B, w, v);
+  line_Bt<N>(tab, w, v);
 #pragma unroll
   for (int k = 0; k < N; ++k)
     if (act) S[ox + k] = v[k];
@@ -397,7 +527,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
     // y-lines: B_y^T
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = S[oy + k * PJ];
-    mat1d<N, true>(tab.B, v, w);
+    line_Bt<N>(tab, v, w);
 #pragma unroll
     for (int k = 0; k < N; ++k)
       if (act) S[oy + k * PJ] = w[k];
@@ -406,7 +536,7 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   // ---- the thread's line: B^T along it and scatter-add
 #pragma unroll
   for (int k = 0; k < N; ++k) v[k] = S[ol + k * SL];
-  mat1d<N, true>(tab.B, v, w);
+  line_Bt<N>(tab, v, w);
   if (valid) {
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -416,37 +546,38 @@ __device__ __forceinline__ void pencil_tile(const float* __restrict__ x, float* 
   }
 }
 
-template <int DIM, int N, typename GT, int GM>
-__global__ void __launch_bounds__(PencilCfg<DIM, N>::THREADS)
-k_apply_pencil(const float* __restrict__ x, float* __restrict__ y, const GT* __restrict__ G,
-               const float* __restrict__ gsc, const Mesh m, const __grid_constant__ Tab<N, float> tab,
-               const float alpha) {
-  extern __shared__ __align__(16) float sm_pencil[];
-  pencil_tile<DIM, N, GT, GM>(x, y, G, gsc, m, tab, alpha, (long long)blockIdx.x, sm_pencil);
+template <int DIM, int N, typename GT, int GM, typename T>
+__global__ void __launch_bounds__(PencilCfg<DIM, N, T>::THREADS)
+k_apply_pencil(const T* __restrict__ x, T* __restrict__ y, const GT* __restrict__ G, const float* __restrict__ gsc,
+               const Mesh m, const __grid_constant__ PencilTab<N, T> tab, const T alpha) {
+  extern __shared__ __align__(16) unsigned char sm_pencil_raw[];
+  pencil_tile<DIM, N, GT, GM, T>(x, y, G, gsc, m, tab, alpha, (long long)blockIdx.x,
+                                 reinterpret_cast<T*>(sm_pencil_raw));
 }
 
-// The pencil-form apply with factors of type GT in the grouped layout: one group per block.
-// variant: 0 factors loaded one phase before the pointwise product, 1 before the first phase
+// The pencil-form apply: FP32 arithmetic with factors GT in the grouped layout, or FP64 arithmetic
+// with the FP64 operator's factors (GT = T = double); one group per block.
+// variant (GM): 0 factors loaded one phase before the pointwise product, 1 before the first phase
 // (orders with few factors per line; else as 0), 2 at their use.
-template <int DIM, int N, typename GT, int GM>
-cudaError_t launch_pencil_gm(const Mesh& m, const Basis1D& b, const float* x, float* y, const GT* G,
-                             const float* gsc, float alpha, cudaStream_t s) {
-  using C = PencilCfg<DIM, N>;
+template <int DIM, int N, typename GT, int GM, typename T>
+cudaError_t launch_pencil_gm(const Mesh& m, const Basis1D& b, const T* x, T* y, const GT* G, const float* gsc,
+                             T alpha, cudaStream_t s) {
+  using C = PencilCfg<DIM, N, T>;
   const long long blocks = (m.nelem + C::EPB - 1) / C::EPB;
   if (blocks == 0) return cudaSuccess;
-  auto kern = k_apply_pencil<DIM, N, GT, GM>;
+  auto kern = k_apply_pencil<DIM, N, GT, GM, T>;
   cudaError_t e = ensure_smem(kern, C::SMEM);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(x, y, G, gsc, m, make_tab<N, float>(b), alpha);
+  kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(x, y, G, gsc, m, make_pencil_tab<N, T>(b), alpha);
   return counted(cudaGetLastError());
 }
-template <int DIM, int N, typename GT>
-cudaError_t launch_pencil(const Mesh& m, const Basis1D& b, const float* x, float* y, const GT* G, const float* gsc,
-                          float alpha, int variant, cudaStream_t s) {
-  if (variant == 2) return launch_pencil_gm<DIM, N, GT, 2>(m, b, x, y, G, gsc, alpha, s);
+template <int DIM, int N, typename GT, typename T = float>
+cudaError_t launch_pencil(const Mesh& m, const Basis1D& b, const T* x, T* y, const GT* G, const float* gsc,
+                          T alpha, int variant, cudaStream_t s) {
+  if (variant == 2) return launch_pencil_gm<DIM, N, GT, 2, T>(m, b, x, y, G, gsc, alpha, s);
   // factors kept in registers from the start only while they stay few
-  if (variant == 1 && RawG<DIM, GT>::RW * N <= 42) return launch_pencil_gm<DIM, N, GT, 1>(m, b, x, y, G, gsc, alpha, s);
-  return launch_pencil_gm<DIM, N, GT, 0>(m, b, x, y, G, gsc, alpha, s);
+  if (variant == 1 && RawG<DIM, GT>::RW * N <= 42) return launch_pencil_gm<DIM, N, GT, 1, T>(m, b, x, y, G, gsc, alpha, s);
+  return launch_pencil_gm<DIM, N, GT, 0, T>(m, b, x, y, G, gsc, alpha, s);
 }
 
 // Grouped reduced-precision factors of one element per block from G[e][c][q] (FP64): FP32 as
