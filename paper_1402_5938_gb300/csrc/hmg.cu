@@ -181,6 +181,14 @@ hmg_status validate(const hmg_desc* d) {
   for (int a = 0; a < d->dim; ++a)
     if (d->nelem[a] < 1 || d->nelem[a] > (1 << 20)) { set_error("nelem out of range"); return HMG_EINVAL; }
   if (d->n_hlevels < 1 || d->n_hlevels > 30) { set_error("n_hlevels must be >= 1"); return HMG_EINVAL; }
+  {  // kernels index elements and nodes of a level with 32-bit integers
+    long long ne = 1, nn = 1;
+    for (int a = 0; a < d->dim; ++a) {
+      ne *= d->nelem[a];
+      nn *= (long long)d->nelem[a] * d->order + 1;
+    }
+    if (ne >= (1ll << 31) || nn >= (1ll << 31)) { set_error("more than 2^31 - 1 elements or nodes"); return HMG_EINVAL; }
+  }
   if (d->smoother != HMG_SMOOTH_JACOBI && d->smoother != HMG_SMOOTH_CHEB && d->smoother != HMG_SMOOTH_L1JACOBI &&
       d->smoother != HMG_SMOOTH_BLOCKJACOBI) {
     set_error("bad smoother");

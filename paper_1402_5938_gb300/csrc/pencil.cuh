@@ -355,10 +355,13 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   long long nb = 0;
   int fl = 0;
   if (valid) {
-    const int ex = (int)(e % m.E[0]);
-    const long long r = e / m.E[0];
-    const int ey = (int)(r % m.E[1]);
-    const int ez = DIM == 3 ? (int)(r / m.E[1]) : 0;
+    // 32-bit decode (a level's element count is below 2^31): 64-bit divisions by runtime values
+    // cost several times the instructions
+    const unsigned ue = (unsigned)e, E0 = (unsigned)m.E[0], E1 = (unsigned)m.E[1];
+    const unsigned ur = ue / E0;
+    const int ex = (int)(ue - ur * E0);
+    const int ey = (int)(ur % E1);
+    const int ez = DIM == 3 ? (int)(ur / E1) : 0;
     const long long base = ((long long)ez * m.p * m.Nn[1] + (long long)ey * m.p) * m.Nn[0] + (long long)ex * m.p;
     fl = (ex == 0) | ((ex == m.E[0] - 1) << 1) | ((ey == 0) << 2) | ((ey == m.E[1] - 1) << 3);
     if (DIM == 3) fl |= ((ez == 0) << 4) | ((ez == m.E[2] - 1) << 5);
