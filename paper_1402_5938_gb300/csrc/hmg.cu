@@ -585,7 +585,7 @@ void tune_cache_store(const TuneKey& k, int v) {
 // Apply variants a level can run: FP64 (the point-parallel shapes, stored element matrices, the
 // FP64 pencil form) or the mixed V-cycle's operator (pencil factor-load timings, tensor-core form).
 std::vector<int> level_variants(const Level& l, bool vcycle_op) {
-  if (!vcycle_op) return apply64_variants(l.m.p + 1, l.Ke != nullptr);
+  if (!vcycle_op) return apply64_variants(l.m.dim, l.m.p + 1, l.Ke != nullptr);
   std::vector<int> v;
   for (int k = 0; k < kApplyLowVariants; ++k) v.push_back(k);
   if (l.tc.G) v.push_back(kApplyLowTc);
@@ -631,7 +631,17 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
         return launch_apply_low(l.m, l.basis, l.x32, l.r32, l.Glow, l.gsc, 1.0f, P.desc.smooth_prec, s, v, &l.tc,
                                 P.err);
       };
-      if ((err = run()) != cudaSuccess) break;  // warm-up (also opts the kernel into its smem)
+      // warm-up (also opts the kernel into its smem); a variant this level cannot launch (its
+      // configuration refused, no fault) is skipped
+      if ((err = run()) != cudaSuccess) {
+        if (err == cudaErrorInvalidValue || err == cudaErrorInvalidConfiguration ||
+            err == cudaErrorLaunchOutOfResources) {
+          cudaGetLastError();
+          err = cudaSuccess;
+          continue;
+        }
+        break;
+      }
       if ((err = cudaEventRecord(e0, s)) != cudaSuccess) break;
       for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run();
       if (err == cudaSuccess) err = cudaEventRecord(e1, s);

@@ -23,12 +23,18 @@ constexpr int kMaxNDense = 3;
 constexpr int kApply64Pencil = 5;
 constexpr int kApply64PencilAhead = 6;
 constexpr int kPencil64AheadMaxN = 9;
-// The FP64 variants a level can run: 0-3, 4 with element matrices, 5, and 6 for N <= 9.
-inline std::vector<int> apply64_variants(int n, bool has_ke) {
+// Whether the FP64 pencil form's tile (4 or 3 buffers of EPB elements in FP64) fits a block's
+// shared memory (not at 3D N = 15, 16).
+bool pencil64_fits(int dim, int n);
+// The FP64 variants a level can run: 0-3, 4 with element matrices, 5 where the pencil tile fits,
+// and 6 for N <= 9.
+inline std::vector<int> apply64_variants(int dim, int n, bool has_ke) {
   std::vector<int> v = {0, 1, 2, 3};
   if (has_ke) v.push_back(kApply64Dense);
-  v.push_back(kApply64Pencil);
-  if (n <= kPencil64AheadMaxN) v.push_back(kApply64PencilAhead);
+  if (pencil64_fits(dim, n)) {
+    v.push_back(kApply64Pencil);
+    if (n <= kPencil64AheadMaxN) v.push_back(kApply64PencilAhead);
+  }
   return v;
 }
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,

@@ -59,6 +59,12 @@ cudaError_t apply_dense64_dim(const Mesh& m, const Basis1D& b, const double* x, 
   });
 }
 
+bool pencil64_fits(int dim, int n) {
+  const PencilShape sh = pencil_shape(dim, n);
+  const size_t bytes = (size_t)(dim == 3 ? 4 : 3) * sh.epb * sh.ep * sizeof(double);
+  return bytes <= 227 * 1024;
+}
+
 template <int DIM>
 cudaError_t apply_pencil64_dim(const Mesh& m, const Basis1D& b, const double* x, double* y, const double* G,
                                double alpha, int variant, cudaStream_t s) {
@@ -75,9 +81,11 @@ cudaError_t apply_pencil64_dim(const Mesh& m, const Basis1D& b, const double* x,
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, int* err, cudaStream_t s, int variant,
                              const double* Ke) {
-  if (variant == kApply64Pencil || variant == kApply64PencilAhead)
+  if (variant == kApply64Pencil || variant == kApply64PencilAhead) {
+    if (!pencil64_fits(m.dim, b.n)) return cudaErrorInvalidValue;
     return m.dim == 3 ? apply_pencil64_dim<3>(m, b, x, y, G, alpha, variant, s)
                       : apply_pencil64_dim<2>(m, b, x, y, G, alpha, variant, s);
+  }
   if (variant == kApply64Dense && Ke != nullptr)
     return m.dim == 3 ? apply_dense64_dim<3>(m, b, x, y, Ke, alpha, s) : apply_dense64_dim<2>(m, b, x, y, Ke, alpha, s);
   return m.dim == 3 ? apply64_dim<3>(m, b, x, y, G, alpha, err, variant, s)

@@ -51,3 +51,46 @@ def test_autotune_cache_file_round_trip(tmp_path):
     assert tuned2 == []                           # every decision came from the file
     assert r1[1] == r2[1] == "0" and r1[2] == r2[2]
     assert abs(float(r1[3]) - float(r2[3])) <= 1e-8 * float(r1[3])
+
+
+HIGH_ORDER = r"""
+import sys, torch
+sys.path.insert(0, {root!r})
+import numpy as np, synth
+from paper_1402_5938_gb300 import Problem
+prob = synth.problem(3, (3, 2, 2), {order}, warp_amp=0.1, mu_b=1e3, hier="p", n_hlevels=1)
+P = Problem(dict(prob, smooth_prec={prec!r}))
+N = P.ndof(0)
+x = torch.from_numpy(synth.uniform_pm1(9, N)).cuda()
+y = torch.zeros_like(x)
+P.apply(0, x, y)
+print("RESULT", P.level_variants(0)[0], P.level_variants(0)[1], float(y.norm()))
+"""
+
+
+@pytest.mark.parametrize("order", [14, 15, 16])
+def test_autotune_times_every_variant_at_high_3d_orders(order):
+    """A 3D level of order 14-16 large enough to be timed (12 elements, >= 32,768 Gauss points): setup
+    times every variant it can run and succeeds (FP64 and the mixed V-cycle's operator); the chosen
+    FP64 variant's apply equals variant 0's (pinned by the decision cache) to rounding."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import tempfile
+    import __graft_entry__
+    __graft_entry__.build()
+    out = {}
+    for pin in (None, 0):
+        env = dict(os.environ)
+        env.pop("HMG_AUTOTUNE_CACHE", None)
+        if pin is not None:
+            f = tempfile.NamedTemporaryFile("w", suffix=".txt", delete=False)
+            f.write(f"0 3 {order} 12 0 {pin}\n0 3 {order} 12 2 0\n")
+            f.close()
+            env["HMG_AUTOTUNE_CACHE"] = f.name
+        r = subprocess.run([sys.executable, "-c", HIGH_ORDER.format(root=ROOT, order=order, prec="fp16")], env=env,
+                           cwd=ROOT, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res = [ln for ln in r.stdout.splitlines() if ln.startswith("RESULT")][0].split()
+        out[pin] = (int(res[1]), int(res[2]), float(res[3]))
+    assert out[0][0] == 0
+    assert abs(out[None][2] - out[0][2]) <= 1e-12 * out[0][2]
