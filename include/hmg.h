@@ -155,10 +155,11 @@ hmg_status hmg_level_info(const hmg_problem* prob, int level, int* nelem3, int* 
 size_t hmg_device_bytes(const hmg_problem* prob);
 /* Apply variants the setup's autotuner chose on a level (no counterpart in the paper):
  * FP64 operator (0-2 point-parallel block shapes, 3 with TMA-staged factors, 4 stored dense element
- * matrices for orders 1-2, 5 and 6 the pencil form with even/odd line products, factors read at
- * their use (5) or one phase ahead (6, orders <= 8)) and the mixed V-cycle's operator (pencil form,
- * when a thread loads its factors: 0 one phase before the pointwise product, 1 before the first
- * phase, 2 at their use; 3 the tensor-core form, 16-bit factors at 3D orders 1-4). */
+ * matrices for orders 1-2, 5 and 6 the pencil form with even/odd line products at orders >= 7,
+ * factors read at their use (5) or one phase ahead (6, orders 7-8)) and the mixed V-cycle's operator
+ * (pencil form, when a thread loads its factors: 0 one phase before the pointwise product, 1 before
+ * the first phase, 2 at their use; 3 the tensor-core form, 16-bit factors at 3D orders 1-4, built
+ * when the environment sets HMG_TC16=1). */
 hmg_status hmg_level_variants(const hmg_problem* prob, int level, int* v_fp64, int* v_vcycle);
 
 /* Physical node coordinates of a level, written as xyz_dev[c * N + node], c < dim (the warp map,

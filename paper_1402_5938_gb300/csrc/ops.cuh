@@ -26,12 +26,14 @@ constexpr int kPencil64AheadMaxN = 9;
 // Whether the FP64 pencil form's tile (4 or 3 buffers of EPB elements in FP64) fits a block's
 // shared memory (not at 3D N = 15, 16).
 bool pencil64_fits(int dim, int n);
-// The FP64 variants a level can run: 0-3, 4 with element matrices, 5 where the pencil tile fits,
-// and 6 for N <= 9.
+// The FP64 variants a level can run: 0-3, 4 with element matrices, and from order 7 on (where
+// its even/odd products save enough to compete; measured slower at order 4, equal at order 2)
+// 5 where the pencil tile fits and 6 for N <= 9.
+constexpr int kPencil64MinN = 8;
 inline std::vector<int> apply64_variants(int dim, int n, bool has_ke) {
   std::vector<int> v = {0, 1, 2, 3};
   if (has_ke) v.push_back(kApply64Dense);
-  if (pencil64_fits(dim, n)) {
+  if (n >= kPencil64MinN && pencil64_fits(dim, n)) {
     v.push_back(kApply64Pencil);
     if (n <= kPencil64AheadMaxN) v.push_back(kApply64PencilAhead);
   }
@@ -69,6 +71,10 @@ cudaError_t launch_apply_low(const Mesh& m, const Basis1D& b, const float* x, fl
                              const Tc16Data* tc = nullptr, int* err = nullptr);
 // Glow (zero-filled beforehand) from G [E][NC][NP] in FP64; 16-bit precisions also write gsc[e].
 cudaError_t launch_pack_low(const double* G, void* Glow, float* gsc, const Mesh& m, int prec, cudaStream_t s);
+// The tensor-core form is built only with HMG_TC16=1 in the environment (opt-in): it
+// measured slower than the pencil form on every level it supports, and building it costs a second
+// copy of the factors and autotuning time at setup.
+bool tc16_enabled();
 bool tc16_supported(const Mesh& m, int prec);
 size_t tc16_phi_bytes(const Mesh& m);
 size_t tc16_factor_bytes(const Mesh& m);

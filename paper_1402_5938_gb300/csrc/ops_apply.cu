@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "dispatch.cuh"
@@ -68,8 +69,16 @@ cudaError_t launch_tc16(const Mesh& m, const float* x, float* y, const void* G, 
 
 }  // namespace
 
+bool tc16_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("HMG_TC16");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 bool tc16_supported(const Mesh& m, int prec) {
-  return m.dim == 3 && m.p + 1 <= kTc16MaxN && (prec == HMG_PREC_FP16 || prec == HMG_PREC_BF16);
+  return tc16_enabled() && m.dim == 3 && m.p + 1 <= kTc16MaxN && (prec == HMG_PREC_FP16 || prec == HMG_PREC_BF16);
 }
 
 size_t tc16_factor_bytes(const Mesh& m) { return tc16_factor_words(m) * 4; }

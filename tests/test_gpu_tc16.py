@@ -1,6 +1,6 @@
 """The tensor-core form of the 16-bit V-cycle operator (3D, orders 1-4; variant 3 of the reduced-
-precision apply) against the FP64 oracle, pinned through the autotuner's decision cache in a fresh
-process so that it runs on every level of each hierarchy.
+precision apply, built when HMG_TC16=1) against the FP64 oracle, pinned through the autotuner's
+decision cache in a fresh process so that it runs on every level of each hierarchy.
 
 y = A_k x (Sec. 2.1, Sec. 2.3's matrix-free apply) computed as two FP16 tensor-core products per
 tile of 128 elements (X Phi, then V Phi^T, FP32 accumulation) around the pointwise G grad u. Per
@@ -127,7 +127,7 @@ def test_tc16_within_rounding_bound_on_every_level(tmp_path, oracle_ref, prec):
     probs = _problems()
     cache = tmp_path / "tune.txt"
     _pin_file(cache, probs, {"fp16": 2, "bf16": 3}[prec])
-    env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache))
+    env = dict(os.environ, HMG_AUTOTUNE_CACHE=str(cache), HMG_TC16="1")   # the form is built on request
     out = subprocess.run([sys.executable, "-c", SCRIPT.format(root=ROOT, ref=oracle_ref, cases=probs, prec=prec)],
                          env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert out.returncode == 0, out.stderr[-3000:]
