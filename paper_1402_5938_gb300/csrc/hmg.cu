@@ -548,11 +548,12 @@ bool autotune_on() {
   return on;
 }
 
-// Autotuner decisions, keyed by (device, dim, order, elements, precision kind). With
-// HMG_AUTOTUNE_CACHE=<file> they persist across processes: the file's lines
-// "device dim order elements kind variant" are read once, and new decisions are appended, so a
-// later process (for instance one run under a profiler, whose timings would be distorted)
-// reuses them instead of timing again.
+// Autotuner decisions, keyed by (device, dim, order, elements, precision kind), and the first
+// decision of each size class under elements = -k (element counts in [2^(k-1), 2^k)), which a level
+// without its own entry reuses. With HMG_AUTOTUNE_CACHE=<file> they persist across processes: the
+// file's lines "device dim order elements kind variant" are read once, and new decisions are
+// appended, so a later process (for instance one run under a profiler, whose timings would be
+// distorted) reuses them instead of timing again.
 using TuneKey = std::tuple<int, int, int, long long, int>;
 std::map<TuneKey, int>& tune_cache() {
   static std::map<TuneKey, int> cache = [] {
@@ -608,11 +609,20 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
   for (int prec = 0; prec < (mixed ? 2 : 1); ++prec) {
     const int kind = prec == 0 ? 0 : P.desc.smooth_prec;
     const auto key = std::make_tuple(dev, l.m.dim, l.m.p, l.m.nelem, kind);
+    // size class: element counts in [2^(k-1), 2^k) share a decision (entry -k), so a stream of
+    // similar problems (a server's) times each class once
+    int cls = 0;
+    for (long long n = l.m.nelem; n > 0; n >>= 1) ++cls;
+    const auto ckey = std::make_tuple(dev, l.m.dim, l.m.p, -(long long)cls, kind);
     {
       std::lock_guard<std::mutex> lk(mu);
-      auto it = cache.find(key);
       const std::vector<int> cand = level_variants(l, prec != 0);
-      if (it != cache.end() && std::find(cand.begin(), cand.end(), it->second) != cand.end()) {  // one this level can run
+      auto runnable = [&](std::map<TuneKey, int>::iterator it) {
+        return it != cache.end() && std::find(cand.begin(), cand.end(), it->second) != cand.end();
+      };
+      auto it = cache.find(key);
+      if (!runnable(it)) it = cache.find(ckey);
+      if (runnable(it)) {  // a decision this level can run: its own, else its size class's
         (prec ? l.v32 : l.v64) = it->second;
         continue;
       }
@@ -665,6 +675,7 @@ hmg_status tune_level(ProblemImpl& P, Level& l, cudaStream_t s) {
               l.m.p, l.m.nelem, kind == 0 ? "fp64" : (kind == HMG_PREC_FP32 ? "fp32" : "16-bit"), bv, best / 3);
     std::lock_guard<std::mutex> lk(mu);
     tune_cache_store(key, bv);
+    if (cache.find(ckey) == cache.end()) tune_cache_store(ckey, bv);
   }
   TRY(cudaMemsetAsync(l.r, 0, l.m.N * sizeof(double), s));
   if (mixed) TRY(cudaMemsetAsync(l.r32, 0, l.m.N * sizeof(float), s));

@@ -1,6 +1,8 @@
 """Autotuner decisions persist across processes through HMG_AUTOTUNE_CACHE: the first process
-times the apply variants and appends its choices to the file, a second process reads them and
-times nothing (no autotune trace lines), and both solve to the same result."""
+times the apply variants and appends its choices to the file (each level's own decision and the
+first decision of its size class), a second process reads them and times nothing (no autotune trace
+lines), and both solve to the same result; a level of another element count in the same size class
+reuses the class's decision without timing."""
 import os
 import subprocess
 import sys
@@ -45,12 +47,20 @@ def test_autotune_cache_file_round_trip(tmp_path):
     r1, tuned1 = _run(env)
     lines = cache.read_text().split("\n")
     entries = [ln.split() for ln in lines if ln.strip()]
-    assert tuned1 and len(entries) == len(tuned1)
+    own = [e for e in entries if int(e[3]) > 0]          # a level's own decision
+    cls = [e for e in entries if int(e[3]) < 0]          # the first decision of its size class
+    assert tuned1 and len(own) == len(tuned1) and 0 < len(cls) <= len(own)
     assert all(len(e) == 6 and all(x.lstrip("-").isdigit() for x in e) for e in entries)
     r2, tuned2 = _run(env)
     assert tuned2 == []                           # every decision came from the file
     assert r1[1] == r2[1] == "0" and r1[2] == r2[2]
     assert abs(float(r1[3]) - float(r2[3])) <= 1e-8 * float(r1[3])
+    # a mesh of 20^3 elements: each timed level (20^3 Q2 and Q1, 8,000 elements) is in the size
+    # class [4096, 8192) of the 16^3 problem's level of equal order and takes its decision untimed
+    r3 = subprocess.run([sys.executable, "-c", SNIPPET.replace("warped_var3d(16, 2,", "warped_var3d(20, 2,").format(root=ROOT)],
+                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r3.returncode == 0, r3.stderr[-2000:]
+    assert [ln for ln in r3.stderr.splitlines() if ln.startswith("hmg autotune:")] == []
 
 
 HIGH_ORDER = r"""
