@@ -70,3 +70,35 @@ def test_lagrange_cardinal_partition_and_polynomial_reproduction(p):
     poly = np.polynomial.Polynomial(c)
     assert np.allclose(L @ poly(r), poly(x), atol=1e-11)
     assert np.allclose(dL @ poly(r), poly.deriv()(x), atol=1e-8 * p ** 2)
+
+
+@pytest.mark.parametrize("p", range(1, 17))
+def test_1d_tables_are_centro_symmetric(p):
+    """The GLL nodes and the Gauss points are symmetric about the element's centre, so the
+    interpolation table B[q][a] = l_a(g_q) is centro-symmetric and the collocated Gauss derivative
+    D[q][s] = l^G_s'(g_q) skew-centro-symmetric: A[n-1-i][n-1-j] = +-A[i][j]. The even/odd line
+    products of the pencil form rest on this; the half-size products of sums and differences then
+    reproduce A x (checked here on seeded vectors for B, D and their transposes)."""
+    r = basis.gll_nodes(p)
+    g, _ = basis.gauss_rule(p + 1)
+    n = p + 1
+    B = basis.lagrange_values(r, g)            # [q][a]
+    D = basis.lagrange_derivatives(g, g)       # [q][s]
+    assert np.allclose(B[::-1, ::-1], B, atol=1e-13 * np.abs(B).max())
+    assert np.allclose(D[::-1, ::-1], -D, atol=1e-13 * np.abs(D).max())
+    rng = np.random.default_rng(p)
+    h = n // 2
+    for A, sgn in ((B, 1.0), (D, -1.0), (B.T, 1.0), (D.T, -1.0)):
+        x = rng.uniform(-1.0, 1.0, n)
+        e = x[:h] + x[::-1][:h]
+        o = x[:h] - x[::-1][:h]
+        E = 0.5 * (A[:h, :h] + A[:h, ::-1][:, :h])
+        O = 0.5 * (A[:h, :h] - A[:h, ::-1][:, :h])
+        a = E @ e + (A[:h, h] * x[h] if n % 2 else 0.0)
+        b = O @ o
+        y = np.empty(n)
+        y[:h] = a + b
+        y[::-1][:h] = sgn * (a - b)
+        if n % 2:
+            y[h] = A[h, :h] @ (e if sgn > 0 else o) + (A[h, h] * x[h] if sgn > 0 else 0.0)
+        assert np.allclose(y, A @ x, atol=1e-12 * np.abs(A).sum(axis=1).max())
