@@ -334,9 +334,11 @@ const char* hmg_last_error(void);
 
 /* Measured arithmetic peak of the current device in TFLOP/s, the denominator of the operator's
  * FP64 roofline (no counterpart in the paper): what = 0 FP64 fused multiply-add on the CUDA cores,
- * 1 FP32 fused multiply-add, 2 FP64 tensor-core MMA (m8n8k4). Independent FMA (MMA) chains in
- * every thread of 8 blocks of 256 threads per SM, best of three timed launches (CUDA events,
- * legacy default stream, synchronized) after a warm-up launch; tens of milliseconds per call. */
+ * 1 FP32 fused multiply-add, 2 FP64 tensor-core MMA (m8n8k4), 3 both FP64 forms at once (half of
+ * each block's warps each: a combined rate no higher than either alone means they share the FP64
+ * units). Independent FMA (MMA) chains in every thread of 8 blocks of 256 threads per SM, best of
+ * three timed launches (CUDA events, legacy default stream, synchronized) after a warm-up launch;
+ * tens of milliseconds per call. */
 hmg_status hmg_measure_peak(int what, double* tflops);
 
 /* Failure-detection self test: one device thread waits, with at most `polls` polls, on an

@@ -56,6 +56,43 @@ __global__ void __launch_bounds__(256) k_dmma_peak(double* out, int iters) {
   if (s == -12345.0) out[blockIdx.x] = s;
 }
 
+// Both at once: warps 0-3 of each block run the FP64 FMA chains, warps 4-7 the FP64 MMAs; if the
+// two used separate units the combined rate would exceed either alone.
+__global__ void __launch_bounds__(256) k_fp64_mixed_peak(double* out, int iters_f, int iters_m) {
+  const int w = threadIdx.x >> 5;
+  double s = 0.0;
+  if (w < 4) {
+    double a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int i = 0; i < iters_f; ++i) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], 1.0 - 1e-12, 1e-9);
+    }
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += a[k];
+  } else {
+    double a = 1e-3 * (threadIdx.x & 7), b = 1.0 - 1e-9 * (threadIdx.x & 3);
+    double d[4][2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) d[k][0] = d[k][1] = 0.0;
+    for (int i = 0; i < iters_m; ++i) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                       : "+d"(d[k][0]), "+d"(d[k][1])
+                       : "d"(a), "d"(b));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += d[k][0] + d[k][1];
+  }
+  if (s == -12345.0) out[blockIdx.x] = s;
+}
+
 template <typename K>
 cudaError_t best_of(K launch, double work, double* rate) {
   cudaEvent_t e0, e1;
@@ -86,8 +123,8 @@ cudaError_t best_of(K launch, double work, double* rate) {
 using namespace hmg;
 
 extern "C" hmg_status hmg_measure_peak(int what, double* tflops) {
-  if (!tflops || what < 0 || what > 2) {
-    set_error("hmg_measure_peak: what must be 0 (FP64 FMA), 1 (FP32 FMA) or 2 (FP64 MMA)");
+  if (!tflops || what < 0 || what > 3) {
+    set_error("hmg_measure_peak: what must be 0 (FP64 FMA), 1 (FP32 FMA), 2 (FP64 MMA) or 3 (both FP64 at once)");
     return HMG_EINVAL;
   }
   int dev = 0, sms = 0;
@@ -113,10 +150,14 @@ extern "C" hmg_status hmg_measure_peak(int what, double* tflops) {
     const double work = 2.0 * kChains * 8 * (double)iters * threads * blocks;
     e = best_of([&] { k_fma_peak<float><<<blocks, threads>>>((float*)out, iters, 1.0f - 1e-6f, 1e-7f); }, work,
                 &rate);
-  } else {
+  } else if (what == 2) {
     const int iters = 1000;
     const double work = 2.0 * 8 * 8 * 4 * 16.0 * iters * (threads / 32) * blocks;
     e = best_of([&] { k_dmma_peak<<<blocks, threads>>>(out, iters); }, work, &rate);
+  } else {
+    const int itf = 2000, itm = 1000;  // about equal time for each half alone
+    const double work = (2.0 * kChains * 8 * (double)itf * 32 * 4 + 2.0 * 8 * 8 * 4 * 16.0 * itm * 4) * blocks;
+    e = best_of([&] { k_fp64_mixed_peak<<<blocks, threads>>>(out, itf, itm); }, work, &rate);
   }
   add_launches(4);
   dev_free(out, 0);

@@ -159,9 +159,10 @@ def _host_ptr(a, n):
 
 
 def measure_peak(what):
-    """hmg_measure_peak: measured TFLOP/s of 'fp64' FMA, 'fp32' FMA or 'fp64_mma' on the current device."""
+    """hmg_measure_peak: measured TFLOP/s of 'fp64' FMA, 'fp32' FMA, 'fp64_mma' or 'fp64_both' (FMA and
+    MMA warps at once) on the current device."""
     v = ctypes.c_double()
-    _check(lib().hmg_measure_peak({"fp64": 0, "fp32": 1, "fp64_mma": 2}[what], ctypes.byref(v)))
+    _check(lib().hmg_measure_peak({"fp64": 0, "fp32": 1, "fp64_mma": 2, "fp64_both": 3}[what], ctypes.byref(v)))
     return v.value
 
 

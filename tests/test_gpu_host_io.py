@@ -4,7 +4,8 @@ hmg_apply_host must give the device apply's result (same kernels: bit for bit up
 the FP64 atomic scatter, so within 1e-14) and hmg_solve_host the solution of hmg_rhs + hmg_solve
 (same iterations; solution within 1e-12), for page-locked and pageable host buffers, and the
 solution must match the oracle's PCG iteration count (Algorithm 1) within +-1.
-hmg_measure_peak: positive, finite rates in the range of a GB300 (FP64 FMA 0.3-5 TFLOP/s, FP32 FMA
+hmg_measure_peak: positive, finite rates in the range of a GB300 (FP64 FMA and MMA warps together no
+faster than the faster alone; FP64 FMA 0.3-5 TFLOP/s, FP32 FMA
 10-300, FP64 MMA 0.1-5)."""
 import numpy as np
 import pytest
@@ -67,7 +68,11 @@ def test_measure_peak_in_range(hmg):
     fp64 = hmg.measure_peak("fp64")
     fp32 = hmg.measure_peak("fp32")
     mma = hmg.measure_peak("fp64_mma")
+    both = hmg.measure_peak("fp64_both")
     assert 0.3 < fp64 < 5.0, fp64
     assert 10.0 < fp32 < 300.0, fp32
     assert 0.1 < mma < 5.0, mma
-    print(f"measured TFLOP/s: FP64 FMA {fp64:.3f}, FP32 FMA {fp32:.2f}, FP64 MMA {mma:.3f}")
+    # FMA and MMA warps together: no faster than the faster of the two alone (one set of FP64
+    # units), so the FP64 FMA rate is the FP64 operator's roof
+    assert 0.1 < both < 1.2 * max(fp64, mma), (both, fp64, mma)
+    print(f"measured TFLOP/s: FP64 FMA {fp64:.3f}, FP32 FMA {fp32:.2f}, FP64 MMA {mma:.3f}, both {both:.3f}")
