@@ -341,6 +341,8 @@ def run_gpu(args):
     prob = workload(args.hier)
     if args.host_loop:  # same kernels launched one by one (for launch lists; graph nodes are not listed)
         prob = dict(prob, solve_graph=0)
+        if args.prec != "fp64":  # the launch list of a mixed-precision solve
+            prob = dict(prob, smooth_prec=args.prec)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     P = Problem(prob)
@@ -441,7 +443,8 @@ def run_gpu(args):
                        "l2": "flushed before every timed step (256 MB written, then another 256 MB read, so no "
                              "dirty lines remain); the apply's 196.6 MB of FP64 geometric factors also exceed L2",
                        "step": "hmg_apply on the finest level, then hmg_solve (PCG + p-MG) to 1e-8",
-                       "solve_loop": "host" if args.host_loop else "graph"},
+                       "solve_loop": "host" if args.host_loop else "graph",
+                       "v_cycle": args.prec if args.host_loop else "fp64"},
             "apply_ms": t_apply, "solve_ms": solve_ms, "setup_ms": setup_ms, "iterations": its[-1],
             "final_rel_residual": rel_res,
             "fine_applies_per_solve": applies,
@@ -1079,7 +1082,7 @@ def main():
     ap.add_argument("--mesh", type=int, default=16, help="--profile-apply: elements per axis")
     ap.add_argument("--order", type=int, default=4, help="--profile-apply: polynomial order")
     ap.add_argument("--prec", choices=["fp64", "fp32", "fp16", "bf16"], default="fp64",
-                    help="--profile-apply: precision")
+                    help="--profile-apply: precision of the applied operator; --host-loop: of the V-cycle")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)
