@@ -230,41 +230,12 @@ kb_axis(const T* __restrict__ in_base, T* __restrict__ out_base, const BPass* __
   const int2 w = tab[blockIdx.x];
   if (!active[gid[w.x]]) return;
   const BPass& P = pass[w.x];
-  const long long o0 = P.od[0], o1 = P.od[1], o2 = P.od[2];
-  const long long t = (long long)w.y + threadIdx.x;
+  const unsigned o0 = (unsigned)P.od[0], o1 = (unsigned)P.od[1], o2 = (unsigned)P.od[2];
+  const unsigned t = (unsigned)w.y + threadIdx.x;
   if (t >= o0 * o1 * o2) return;
-  const T* in = in_base + P.in_off;
-  T* out = out_base + P.out_off;
   const V* val = std::is_same<V, float>::value ? reinterpret_cast<const V*>(P.val32) : reinterpret_cast<const V*>(P.val);
-  long long id[3] = {t % o0, (t / o0) % o1, t / (o0 * o1)};
-  long long idim[3] = {o0, o1, o2};
-  idim[P.axis] = P.n_in;
-  const long long odim[3] = {o0, o1, o2};
-  bool obd = false;
-  if (mask_out) {
-    for (int a = 0; a < 3; ++a)
-      if (odim[a] > 1) obd |= (id[a] == 0) | (id[a] == odim[a] - 1);
-  }
-  T s = T(0);
-  if (!obd) {
-    const int row = (int)id[P.axis];
-    for (int k = P.rowptr[row]; k < P.rowptr[row + 1]; ++k) {
-      long long ii[3] = {id[0], id[1], id[2]};
-      ii[P.axis] = P.col[k];
-      if (mask_in) {
-        bool ibd = false;
-        for (int a = 0; a < 3; ++a)
-          if (idim[a] > 1) ibd |= (ii[a] == 0) | (ii[a] == idim[a] - 1);
-        if (ibd) continue;
-      }
-      s = fma((T)val[k], in[(ii[2] * idim[1] + ii[1]) * idim[0] + ii[0]], s);
-    }
-  }
-  if (acc) {
-    if (!obd) out[t] += s;
-  } else {
-    out[t] = s;
-  }
+  axis_point<T, V>(in_base + P.in_off, out_base + P.out_off, t, o0, o1, o2, P.axis, P.n_in, P.rowptr, P.col, val,
+                   mask_in, mask_out, acc);
 }
 
 // x[gmap[i]] = sum_j Ainv[i][j] b[gmap[j]], one warp per row, 8 rows per block

@@ -342,44 +342,12 @@ __global__ void k_node_coords(double* __restrict__ xyz, const Mesh m, const Gll 
 }
 
 template <typename T, typename V>
-__global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, long long o0, long long o1, long long o2,
+__global__ void k_axis(const T* __restrict__ in, T* __restrict__ out, unsigned o0, unsigned o1, unsigned o2,
                        int axis, int n_in, const int* __restrict__ rowptr, const int* __restrict__ col,
                        const V* __restrict__ val, int mask_in, int mask_out, int acc) {
-  const long long tot = o0 * o1 * o2;
-  long long id[3] = {0, 0, 0};
-  long long idim[3] = {o0, o1, o2};
-  idim[axis] = n_in;
-  const long long odim[3] = {o0, o1, o2};
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    id[0] = t % o0;
-    id[1] = (t / o0) % o1;
-    id[2] = t / (o0 * o1);
-    bool obd = false;
-    if (mask_out) {
-      for (int a = 0; a < 3; ++a)
-        if (odim[a] > 1) obd |= (id[a] == 0) | (id[a] == odim[a] - 1);
-    }
-    T s = T(0);
-    if (!obd) {
-      const int row = (int)id[axis];
-      for (int k = rowptr[row]; k < rowptr[row + 1]; ++k) {
-        long long ii[3] = {id[0], id[1], id[2]};
-        ii[axis] = col[k];
-        if (mask_in) {
-          bool ibd = false;
-          for (int a = 0; a < 3; ++a)
-            if (idim[a] > 1) ibd |= (ii[a] == 0) | (ii[a] == idim[a] - 1);
-          if (ibd) continue;
-        }
-        s = fma((T)val[k], in[(ii[2] * idim[1] + ii[1]) * idim[0] + ii[0]], s);
-      }
-    }
-    if (acc) {
-      if (!obd) out[t] += s;
-    } else {
-      out[t] = s;
-    }
-  }
+  const unsigned tot = o0 * o1 * o2;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += gridDim.x * blockDim.x)
+    axis_point<T, V>(in, out, t, o0, o1, o2, axis, n_in, rowptr, col, val, mask_in, mask_out, acc);
 }
 
 // one warp per output row
@@ -558,11 +526,15 @@ template <typename T>
 cudaError_t axis_pass(const T* in, T* out, const long long od[3], int axis, const Axis1D& M, int mask_in,
                       int mask_out, int accumulate, cudaStream_t s) {
   const long long tot = od[0] * od[1] * od[2];
+  if (tot <= 0) return cudaSuccess;
+  const long long tin = tot / od[axis] * M.n_in;
+  if (tot >= (1LL << 31) || tin >= (1LL << 31)) return cudaErrorInvalidValue;  // 32-bit point indices
+  const unsigned o0 = (unsigned)od[0], o1 = (unsigned)od[1], o2 = (unsigned)od[2];
   if (std::is_same<T, float>::value)
-    k_axis<T, float><<<grid_for(tot), kThreads, 0, s>>>(in, out, od[0], od[1], od[2], axis, M.n_in, M.rowptr,
+    k_axis<T, float><<<grid_for(tot), kThreads, 0, s>>>(in, out, o0, o1, o2, axis, M.n_in, M.rowptr,
                                                          M.col, M.val32, mask_in, mask_out, accumulate);
   else
-    k_axis<T, double><<<grid_for(tot), kThreads, 0, s>>>(in, out, od[0], od[1], od[2], axis, M.n_in, M.rowptr,
+    k_axis<T, double><<<grid_for(tot), kThreads, 0, s>>>(in, out, o0, o1, o2, axis, M.n_in, M.rowptr,
                                                           M.col, M.val, mask_in, mask_out, accumulate);
   return counted(cudaGetLastError());
 }

@@ -37,6 +37,50 @@ struct Axis1D {
   float* val32;      // device, nnz
 };
 
+// One output point t of a 1D transfer pass along `axis` (Sec. 2.2: P and R = P^T act as
+// Kronecker products of 1D factors, applied one axis at a time). The output has extents
+// o0 x o1 x o2 (x fastest); the input has n_in points along `axis` and the output's extents on
+// the other two. mask_in skips input points on the box boundary (Dirichlet nodes), mask_out
+// zeroes output points on it (with acc: leaves them). 32-bit indexing: every level vector and
+// pass intermediate has fewer than 2^31 entries (meshes are validated below that). The point
+// decode is two 32-bit divisions, the input base and the boundary tests of the two other axes
+// are taken once per output, and the row's entries are summed in CSR order.
+template <typename T, typename V>
+__device__ __forceinline__ void axis_point(const T* __restrict__ in, T* __restrict__ out, unsigned t,
+                                           unsigned o0, unsigned o1, unsigned o2, int axis, int n_in,
+                                           const int* __restrict__ rowptr, const int* __restrict__ col,
+                                           const V* __restrict__ val, int mask_in, int mask_out, int acc) {
+  const unsigned q = t / o0, i0 = t - q * o0;
+  const unsigned i2 = q / o1, i1 = q - i2 * o1;
+  const bool b0 = o0 > 1 && (i0 == 0 || i0 == o0 - 1);
+  const bool b1 = o1 > 1 && (i1 == 0 || i1 == o1 - 1);
+  const bool b2 = o2 > 1 && (i2 == 0 || i2 == o2 - 1);
+  const bool obd = mask_out && (b0 || b1 || b2);
+  unsigned row, base, stride;
+  bool other_bd;
+  if (axis == 0) {
+    row = i0, base = (unsigned)n_in * (i1 + o1 * i2), stride = 1, other_bd = b1 || b2;
+  } else if (axis == 1) {
+    row = i1, base = i0 + o0 * (unsigned)n_in * i2, stride = o0, other_bd = b0 || b2;
+  } else {
+    row = i2, base = i0 + o0 * i1, stride = o0 * o1, other_bd = b0 || b1;
+  }
+  T s = T(0);
+  if (!obd && !(mask_in && other_bd)) {
+    const int k1 = rowptr[row + 1];
+    for (int k = rowptr[row]; k < k1; ++k) {
+      const int c = col[k];
+      if (mask_in && n_in > 1 && (c == 0 || c == n_in - 1)) continue;
+      s = fma((T)val[k], in[base + (unsigned)c * stride], s);
+    }
+  }
+  if (acc) {
+    if (!obd) out[t] += s;
+  } else {
+    out[t] = s;
+  }
+}
+
 // reductions over n entries: red_blocks(n) partials, then finish into S (pass the same n)
 int red_blocks(long long n);
 cudaError_t dot_partial(const double* x, const double* y, long long n, double* partial, cudaStream_t s);
