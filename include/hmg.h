@@ -51,6 +51,8 @@ typedef enum {
 } hmg_smoother;
 typedef enum { HMG_MODE_MG = 0, HMG_MODE_PCG = 1 } hmg_mode;
 typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC_BF16 = 3 } hmg_prec;
+/* Arithmetic of the finest level's FP64 operator (hmg_desc.fp64_arith). */
+typedef enum { HMG_ARITH_FP64 = 0, HMG_ARITH_DF64 = 1 } hmg_arith;
 
 /*
  * Problem descriptor (paper Sec. 2 problem statement, Sec. 2.3 meshing, Sec. 4.3 settings).
@@ -92,6 +94,16 @@ typedef enum { HMG_PREC_FP64 = 0, HMG_PREC_FP32 = 1, HMG_PREC_FP16 = 2, HMG_PREC
  *   solve_graph        : 1 (default): hmg_solve runs each solve as one instantiated CUDA graph with
  *                        a device-side loop (no host round trip per iteration); 0: host-driven loop
  *                        that reads the residual norm back every iteration. Same results.
+ *   fp64_arith         : HMG_ARITH_FP64 (default): the finest level's operator (hmg_apply, the PCG
+ *                        and MG residuals, and with an FP64 V-cycle its finest smoothing) in FP64
+ *                        arithmetic, in the fastest form timed at setup. HMG_ARITH_DF64: the same
+ *                        operator (Sec. 2.3) with FP64 vectors and the FP64 factors split into float
+ *                        pairs, computed in double-float arithmetic (pairs of FP32 numbers, about 48
+ *                        significant bits; rounding errors a few 2^-46 relative to the magnitudes
+ *                        summed instead of 2^-53), for GPUs whose FP64 rate is a small fraction of
+ *                        their FP32 rate. Finest orders 1-8 (else FP64 as by default); one more
+ *                        copy of the finest level's factors (8 bytes per value). Not in the paper:
+ *                        an arithmetic choice of this implementation.
  */
 typedef struct hmg_desc {
   int dim;
@@ -120,6 +132,7 @@ typedef struct hmg_desc {
                              else HMG_EINVAL), called on the setup thread once per level;
                              replaces mu_a + mu_b sum cos^2(mu_k pi x_i). */
   void* mu_user;          /* passed to mu_fn */
+  int fp64_arith;         /* hmg_arith of the finest level's FP64 operator (above) */
 } hmg_desc;
 
 typedef struct hmg_problem hmg_problem;

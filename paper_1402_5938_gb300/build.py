@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ops_apply64.cu", "ops_apply.cu", "ops_setup.cu", "blockjac.cu", "vector.cu", "hmg.cu", "batch.cu", "noalloc.cu", "peak.cu", "host_basis.cpp", "server.cpp", "pinned.cpp"]
+SOURCES = ["ops_apply64.cu", "ops_apply_df64.cu", "ops_apply.cu", "ops_setup.cu", "blockjac.cu", "vector.cu", "hmg.cu", "batch.cu", "noalloc.cu", "peak.cu", "host_basis.cpp", "server.cpp", "pinned.cpp"]
 
 
 def _nvcc():

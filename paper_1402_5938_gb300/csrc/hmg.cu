@@ -214,6 +214,7 @@ hmg_status validate(const hmg_desc* d) {
     set_error("bad Chebyshev parameters"); return HMG_EINVAL;
   }
   if (d->smooth_prec < HMG_PREC_FP64 || d->smooth_prec > HMG_PREC_BF16) { set_error("bad smooth_prec"); return HMG_EINVAL; }
+  if (d->fp64_arith != HMG_ARITH_FP64 && d->fp64_arith != HMG_ARITH_DF64) { set_error("bad fp64_arith"); return HMG_EINVAL; }
   return HMG_OK;
 }
 
@@ -286,7 +287,7 @@ template <> struct Acc<float> {
 hmg_status apply_level(ProblemImpl& P, int k, const double* x, double* y, double alpha, cudaStream_t s) {
   Level& l = P.L[k];
   if (k == 0 && !P.capturing) P.fine_applies++;
-  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, P.err, s, l.v64, l.Ke));
+  TRY(launch_apply_f64(l.m, l.basis, x, y, l.G, alpha, P.err, s, l.v64, l.Ke, l.Gdf));
   return HMG_OK;
 }
 hmg_status apply_level(ProblemImpl& P, int k, const float* x, float* y, float alpha, cudaStream_t s) {
@@ -515,7 +516,7 @@ hmg_status arnoldi(ProblemImpl& P, int k, cudaStream_t s) {
     for (int j = 0; j < m; ++j) {
       double* w = V(j + 1);
       TRY(cudaMemsetAsync(w, 0, n * sizeof(double), s));
-      TRY(launch_apply_f64(l.m, l.basis, V(j), w, l.G, 1.0, P.err, s, l.v64, l.Ke));
+      TRY(launch_apply_f64(l.m, l.basis, V(j), w, l.G, 1.0, P.err, s, l.v64, l.Ke, l.Gdf));
       TRY(scale_by(w, l.dinv, n, s));
       for (int pass = 0; pass < 2; ++pass)  // H[0..j][j] accumulates both passes
         TRY(project_out(w, Vb, n, j + 1, n, part, coef, Hd + j, m, s));
@@ -902,6 +903,13 @@ hmg_status setup_impl(ProblemImpl& P, cudaStream_t s) {
         TRY(to_f32(l.dinv32, l.dinv, n, s));
       }
       CHECK(tune_level(P, l, s));
+      if (k == 0 && D.fp64_arith == HMG_ARITH_DF64 && df64_supported(D.dim, l.basis.n)) {
+        // the finest level's FP64 operator in double-float arithmetic: the factors split once into
+        // float pairs (same element-major layout)
+        TRY(P.alloc(&l.Gdf, gsz * nc_of(D.dim) * 2 * sizeof(float) + 256));  // prefetch rounding
+        TRY(launch_split_df64(l.G, l.Gdf, gsz * nc_of(D.dim), s));
+        l.v64 = kApply64Df;
+      }
     }
     {
       Phase ph("setup: transfer stencils", s);
@@ -1193,6 +1201,8 @@ hmg_status estimate_bytes(const hmg_desc& D, size_t* resident, size_t* peak) {
     const Mesh& m = ms[k];
     const size_t gsz = (size_t)(m.nelem * np_of(m)), n = (size_t)m.N;
     add(gsz * nc_of(D.dim) * 8 + 256); add(gsz * 8);
+    if (k == 0 && D.fp64_arith == HMG_ARITH_DF64 && df64_supported(D.dim, m.p + 1))
+      add(gsz * nc_of(D.dim) * 8 + 256);  // float-pair factors of the double-float operator
     for (int v = 0; v < 5; ++v) add(n * 8);
     if (m.p + 1 <= kMaxNDense && k + 1 < ms.size() && (k == 0 || !mixed))
       add((size_t)m.nelem * np_of(m) * np_of(m) * 8);  // element matrices (dense-apply variant)
@@ -1284,6 +1294,7 @@ hmg_status hmg_desc_default(hmg_desc* d) {
   d->arnoldi_seed = 0;
   d->smooth_prec = HMG_PREC_FP64;
   d->solve_graph = 1;
+  d->fp64_arith = HMG_ARITH_FP64;
   d->node_xyz = nullptr;
   d->mu_fn = nullptr;
   d->mu_user = nullptr;

@@ -39,9 +39,20 @@ inline std::vector<int> apply64_variants(int dim, int n, bool has_ke) {
   }
   return v;
 }
+// FP64 variant kApply64Df: the FP64 operator (FP64 vectors, the FP64 factors split once into
+// float pairs, Gdf) in double-float arithmetic (df64.cuh, about 48 significant bits), the pencil
+// form with factors read at their use; for orders with N <= kDf64MaxN where the tile fits. Never
+// chosen by timing: a problem asks for it (hmg_desc.fp64_arith) on its finest level.
+constexpr int kApply64Df = 7;
+constexpr int kDf64MaxN = 9;
+bool df64_supported(int dim, int n);
+cudaError_t launch_apply_df64(const Mesh& m, const Basis1D& b, const double* x, double* y, const void* Gdf,
+                              double alpha, cudaStream_t s);
+// Gdf[i] = (hi, lo) float pair of G[i] (n values; Gdf holds n float2 and >= 256 bytes more)
+cudaError_t launch_split_df64(const double* G, void* Gdf, long long n, cudaStream_t s);
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, int* err, cudaStream_t s, int variant = 0,
-                             const double* Ke = nullptr);
+                             const double* Ke = nullptr, const void* Gdf = nullptr);
 // Ke[(e * NP + b) * NP + a] = K_e[a][b], the element stiffness matrices (all nodes; the apply
 // masks the boundary), by sum-factorized unit columns.
 cudaError_t launch_elem_mats(const Mesh& m, const Basis1D& b, const double* G, double* Ke, cudaStream_t s);

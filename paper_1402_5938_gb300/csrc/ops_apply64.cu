@@ -80,7 +80,11 @@ cudaError_t apply_pencil64_dim(const Mesh& m, const Basis1D& b, const double* x,
 
 cudaError_t launch_apply_f64(const Mesh& m, const Basis1D& b, const double* x, double* y,
                              const double* G, double alpha, int* err, cudaStream_t s, int variant,
-                             const double* Ke) {
+                             const double* Ke, const void* Gdf) {
+  if (variant == kApply64Df) {
+    if (Gdf == nullptr || !df64_supported(m.dim, b.n)) return cudaErrorInvalidValue;
+    return launch_apply_df64(m, b, x, y, Gdf, alpha, s);
+  }
   if (variant == kApply64Pencil || variant == kApply64PencilAhead) {
     if (!pencil64_fits(m.dim, b.n)) return cudaErrorInvalidValue;
     return m.dim == 3 ? apply_pencil64_dim<3>(m, b, x, y, G, alpha, variant, s)

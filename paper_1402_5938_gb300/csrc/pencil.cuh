@@ -34,6 +34,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "dispatch.cuh"
 
 namespace hmg {
@@ -169,12 +170,13 @@ PencilTab<N, T> make_pencil_tab(const Basis1D& b) {
 // (16-bit: half the registers of FP32 values) until unpack_g converts them at their use.
 // Grouped layouts (FP32, FP16, BF16): RW words per point, 32-bit words (FP32 values; 16-bit 3D
 // three component pairs; 16-bit 2D three values, one per word). FP64 factors are read from the
-// element-major layout G[e][c][q] of the FP64 operator, NC doubles per point.
+// element-major layout G[e][c][q] of the FP64 operator, NC doubles per point; double-float factors
+// (df64) from the same layout, NC float pairs per point.
 template <int DIM, typename GT>
 struct RawG {
-  static constexpr bool F64 = std::is_same<GT, double>::value;
-  using W = typename std::conditional<F64, double, uint32_t>::type;
-  static constexpr int RW = F64 ? (DIM == 3 ? 6 : 3) : std::is_same<GT, float>::value ? (DIM == 3 ? 6 : 3) : 3;
+  static constexpr bool EM = std::is_same<GT, double>::value || std::is_same<GT, df64>::value;  // element-major
+  using W = typename std::conditional<EM, GT, uint32_t>::type;
+  static constexpr int RW = EM ? (DIM == 3 ? 6 : 3) : std::is_same<GT, float>::value ? (DIM == 3 ? 6 : 3) : 3;
 };
 template <int DIM, int N, typename GT>
 __device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, int el, int q,
@@ -185,6 +187,13 @@ __device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, 
     const double* p = G + (g * EPB + el) * NC * NP + q;
 #pragma unroll
     for (int c = 0; c < NC; ++c) w[c] = __ldg(p + c * NP);
+  } else if constexpr (std::is_same<GT, df64>::value) {
+    const float2* p = reinterpret_cast<const float2*>(G) + (g * EPB + el) * NC * NP + q;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const float2 f = __ldg(p + c * NP);
+      w[c] = df64(f.x, f.y);
+    }
   } else if constexpr (std::is_same<GT, float>::value) {
     const float* p = G + (g * NC * NP + q) * EPB + el;
 #pragma unroll
@@ -201,7 +210,7 @@ __device__ __forceinline__ void load_raw(const GT* __restrict__ G, long long g, 
 }
 template <int DIM, typename GT, typename T>
 __device__ __forceinline__ void unpack_g(const typename RawG<DIM, GT>::W* w, T* v) {
-  if constexpr (std::is_same<GT, double>::value) {
+  if constexpr (std::is_same<GT, double>::value || std::is_same<GT, df64>::value) {
 #pragma unroll
     for (int c = 0; c < (DIM == 3 ? 6 : 3); ++c) v[c] = w[c];
   } else if constexpr (std::is_same<GT, float>::value) {
@@ -233,7 +242,7 @@ __device__ __forceinline__ void mat1d(const T* __restrict__ M, const T* in, T* o
   for (int i = 0; i < N; ++i) {
     T s = (TRN ? M[i] : M[i * N]) * in[0];
 #pragma unroll
-    for (int m = 1; m < N; ++m) s = fma(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
+    for (int m = 1; m < N; ++m) s = fmadd(TRN ? M[m * N + i] : M[i * N + m], in[m], s);
     out[i] = s;
   }
 }
@@ -244,7 +253,7 @@ __device__ __forceinline__ void mat1d_t_acc(const T* __restrict__ M, const T* in
   for (int i = 0; i < N; ++i) {
     T s = acc[i];
 #pragma unroll
-    for (int m = 0; m < N; ++m) s = fma(M[m * N + i], in[m], s);
+    for (int m = 0; m < N; ++m) s = fmadd(M[m * N + i], in[m], s);
     out[i] = s;
   }
 }
@@ -263,11 +272,11 @@ __device__ __forceinline__ void mat1d_eo(const T* __restrict__ Q, const T* in, T
   for (int i = 0; i < H; ++i) {
     T a = Q[i * H] * e[0];
 #pragma unroll
-    for (int j = 1; j < H; ++j) a = fma(Q[i * H + j], e[j], a);
-    if constexpr (ODD) a = fma(Q[2 * H * H + i], in[H], a);
+    for (int j = 1; j < H; ++j) a = fmadd(Q[i * H + j], e[j], a);
+    if constexpr (ODD) a = fmadd(Q[2 * H * H + i], in[H], a);
     T b = Q[H * H + i * H] * o[0];
 #pragma unroll
-    for (int j = 1; j < H; ++j) b = fma(Q[H * H + i * H + j], o[j], b);
+    for (int j = 1; j < H; ++j) b = fmadd(Q[H * H + i * H + j], o[j], b);
     out[i] = a + b;
     out[N - 1 - i] = S > 0 ? a - b : b - a;
   }
@@ -275,12 +284,12 @@ __device__ __forceinline__ void mat1d_eo(const T* __restrict__ Q, const T* in, T
     if constexpr (S > 0) {
       T c = Q[2 * H * H + 2 * H] * in[H];
 #pragma unroll
-      for (int j = 0; j < H; ++j) c = fma(Q[2 * H * H + H + j], e[j], c);
+      for (int j = 0; j < H; ++j) c = fmadd(Q[2 * H * H + H + j], e[j], c);
       out[H] = c;
     } else {
       T c = Q[2 * H * H + H] * o[0];
 #pragma unroll
-      for (int j = 1; j < H; ++j) c = fma(Q[2 * H * H + H + j], o[j], c);
+      for (int j = 1; j < H; ++j) c = fmadd(Q[2 * H * H + H + j], o[j], c);
       out[H] = c;
     }
   }
@@ -321,9 +330,10 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, size_t bytes) {
 
 // One tile: the group g of EPB elements e0 = g * EPB, ... of mesh m (those below m.nelem),
 // y += alpha A x in arithmetic T (FP32 with FP32 / 16-bit grouped factors, FP64 with the FP64
-// operator's element-major factors); `sm` holds PencilCfg<DIM, N, T>::SMEM bytes.
-template <int DIM, int N, typename GT, int GM, typename T = float>
-__device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restrict__ y,
+// operator's element-major factors, double-float with their float-pair split) on vectors of type
+// X (T, or FP64 vectors for double-float arithmetic); `sm` holds PencilCfg<DIM, N, T>::SMEM bytes.
+template <int DIM, int N, typename GT, int GM, typename T = float, typename X = T>
+__device__ __forceinline__ void pencil_tile(const X* __restrict__ x, X* __restrict__ y,
                                             const GT* __restrict__ G, const float* __restrict__ gsc, const Mesh& m,
                                             const PencilTab<N, T>& tab, const T alpha, const long long g, T* sm) {
   using C = PencilCfg<DIM, N, T>;
@@ -347,7 +357,7 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   if (t == 0) {
     // the group's factors (element-major FP64: only the elements of the mesh, the allocation ends
     // at the last one; grouped layouts are padded to whole groups)
-    const long long ng = std::is_same<GT, double>::value ? (m.nelem - e0 < EPB ? m.nelem - e0 : EPB) : EPB;
+    const long long ng = RawG<DIM, GT>::EM ? (m.nelem - e0 < EPB ? m.nelem - e0 : EPB) : EPB;
     const size_t gbytes = sizeof(GT) * (size_t)NC * NP * EPB;
     bulk_prefetch_l2(reinterpret_cast<const char*>(G) + g * gbytes, sizeof(GT) * (size_t)NC * NP * ng);
   }
@@ -376,7 +386,7 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
   const int f_hi = DIM == 3 ? ((fl >> 5) & 1) : ((fl >> 3) & 1);
   // 16-bit factors are stored divided by a per-element power of two; the element's result is
   // scaled back at the scatter (exact, so the same as scaling each factor)
-  const T asc = alpha * (T)((gsc != nullptr && valid) ? gsc[e] : 1.0f);
+  const T asc = alpha * T((gsc != nullptr && valid) ? gsc[e] : 1.0f);
 
   // tile offsets: x-line (j = a, k = b) stride 1; y-line (i = a, k = b) stride PJ; z-line
   // (i = a, j = b) stride PK. 2D: x-line (j = a), y-line (i = a).
@@ -405,7 +415,7 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     const bool bd = bd_lat | ((k == 0) & f_lo) | ((k == N - 1) & f_hi);
-    v[k] = (valid && !bd) ? __ldg(x + nb + k * sline) : T(0);
+    v[k] = (valid && !bd) ? T(__ldg(x + nb + k * sline)) : T(0);
   }
   line_B<N>(tab, v, w);
   if (DIM == 3) {
@@ -544,31 +554,31 @@ __device__ __forceinline__ void pencil_tile(const T* __restrict__ x, T* __restri
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       const bool bd = bd_lat | ((k == 0) & f_lo) | ((k == N - 1) & f_hi);
-      if (!bd) atomicAdd(y + nb + k * sline, asc * w[k]);
+      if (!bd) atomicAdd(y + nb + k * sline, X(asc * w[k]));
     }
   }
 }
 
-template <int DIM, int N, typename GT, int GM, typename T>
+template <int DIM, int N, typename GT, int GM, typename T, typename X>
 __global__ void __launch_bounds__(PencilCfg<DIM, N, T>::THREADS)
-k_apply_pencil(const T* __restrict__ x, T* __restrict__ y, const GT* __restrict__ G, const float* __restrict__ gsc,
+k_apply_pencil(const X* __restrict__ x, X* __restrict__ y, const GT* __restrict__ G, const float* __restrict__ gsc,
                const Mesh m, const __grid_constant__ PencilTab<N, T> tab, const T alpha) {
   extern __shared__ __align__(16) unsigned char sm_pencil_raw[];
-  pencil_tile<DIM, N, GT, GM, T>(x, y, G, gsc, m, tab, alpha, (long long)blockIdx.x,
-                                 reinterpret_cast<T*>(sm_pencil_raw));
+  pencil_tile<DIM, N, GT, GM, T, X>(x, y, G, gsc, m, tab, alpha, (long long)blockIdx.x,
+                                    reinterpret_cast<T*>(sm_pencil_raw));
 }
 
 // The pencil-form apply: FP32 arithmetic with factors GT in the grouped layout, or FP64 arithmetic
 // with the FP64 operator's factors (GT = T = double); one group per block.
 // variant (GM): 0 factors loaded one phase before the pointwise product, 1 before the first phase
 // (orders with few factors per line; else as 0), 2 at their use.
-template <int DIM, int N, typename GT, int GM, typename T>
-cudaError_t launch_pencil_gm(const Mesh& m, const Basis1D& b, const T* x, T* y, const GT* G, const float* gsc,
+template <int DIM, int N, typename GT, int GM, typename T, typename X = T>
+cudaError_t launch_pencil_gm(const Mesh& m, const Basis1D& b, const X* x, X* y, const GT* G, const float* gsc,
                              T alpha, cudaStream_t s) {
   using C = PencilCfg<DIM, N, T>;
   const long long blocks = (m.nelem + C::EPB - 1) / C::EPB;
   if (blocks == 0) return cudaSuccess;
-  auto kern = k_apply_pencil<DIM, N, GT, GM, T>;
+  auto kern = k_apply_pencil<DIM, N, GT, GM, T, X>;
   cudaError_t e = ensure_smem(kern, C::SMEM);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)blocks, C::THREADS, C::SMEM, s>>>(x, y, G, gsc, m, make_pencil_tab<N, T>(b), alpha);

@@ -24,6 +24,7 @@ struct Level {
   double* dinv_s = nullptr;  // block Jacobi: D^-1 on shared nodes, 0 at element-interior nodes
   float* gsc = nullptr;   // 16-bit factors: per-element power-of-two scales
   Tc16Data tc{};          // tensor-core form of the 16-bit apply: its factor layout, Phi image, v scale
+  void* Gdf = nullptr;    // finest level, double-float operator: G split into float pairs
   float* dinv32 = nullptr;
   double lam = 0.0;       // Chebyshev bound
   int v64 = 0, v32 = 0;   // apply variants chosen by the autotuner (v32: of the V-cycle

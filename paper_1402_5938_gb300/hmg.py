@@ -19,6 +19,7 @@ HIER = {"h": 0, "p": 1}
 SMOOTHER = {"jacobi": 0, "cheb": 1, "l1jacobi": 2, "blockjacobi": 3}
 MODE = {"mg": 0, "pcg": 1}
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+ARITH = {"fp64": 0, "df64": 1}  # arithmetic of the finest level's FP64 operator
 
 
 class HmgError(RuntimeError):
@@ -42,6 +43,7 @@ class Desc(ctypes.Structure):
         ("cheb_lo_frac", ctypes.c_double), ("cheb_safety", ctypes.c_double),
         ("arnoldi_seed", ctypes.c_ulonglong), ("smooth_prec", ctypes.c_int), ("solve_graph", ctypes.c_int),
         ("node_xyz", ctypes.POINTER(ctypes.c_double)), ("mu_fn", MU_FN), ("mu_user", ctypes.c_void_p),
+        ("fp64_arith", ctypes.c_int),
     ]
 
 
@@ -187,6 +189,7 @@ def make_desc(prob: dict) -> Desc:
     d.arnoldi_seed = prob.get("arnoldi_seed", 0)
     d.smooth_prec = PREC[prob.get("smooth_prec", "fp64")]
     d.solve_graph = int(prob.get("solve_graph", 1))
+    d.fp64_arith = ARITH[prob.get("fp64_arith", "fp64")]
     keep = []
     if prob.get("node_xyz") is not None:
         xyz = np.ascontiguousarray(prob["node_xyz"], dtype=np.float64)
