@@ -15,8 +15,9 @@ value = GDOF/s of the order-p operator apply (N / apply time), whole job over al
 (replicas); solve_ms = time to 1e-8 of the same step. e2e: the same apply through the host-
 buffer call hmg_apply_host (page-locked x in, y out, copies inside the timed region), and the
 solve through hmg_solve_host (nodal f in, u out). Further blocks: the same problem's FP32 /
-FP16 / BF16 V-cycles inside FP64 PCG, the order sweep at 129^3 nodes (p = 2, 8, 16), and the
-16^3 Q4 (274,625 DOF) single-solve configuration with its h- and p-hierarchies.
+FP16 / BF16 V-cycles inside FP64 PCG, the finest FP64 operator in double-float arithmetic (its
+apply, and PCG with the FP64 / FP32 / FP16 V-cycles), the order sweep at 129^3 nodes (p = 2, 8,
+16), and the 16^3 Q4 (274,625 DOF) single-solve configuration with its h- and p-hierarchies.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--hier p|h] [--impl reference]
 """
@@ -319,6 +320,44 @@ def mixed_block(prob, P64, b, flush, stream, t64_ms, reps=5):
     return out
 
 
+def df64_block(prob, P64, b, flush, stream, t64_ms, apply64_ms, peak64, reps=5):
+    """The finest level's FP64 operator in double-float arithmetic (fp64_arith = df64: pairs of FP32
+    numbers, FP64 vectors, the FP64 factors split into float pairs): its apply against the native
+    FP64 apply of the timed steps, and PCG solves with the FP64, FP32 and FP16 V-cycles (solve time,
+    iterations, the true FP64 residual of the solution by the native FP64 operator)."""
+    import torch
+    Problem = __import__("paper_1402_5938_gb300").Problem
+    N = b.numel()
+    Pd = Problem(dict(prob, fp64_arith="df64"))
+    yd = torch.zeros_like(b)
+    ta = timed_apply(lambda: Pd.apply(0, b, yd), flush, stream, 20)
+    y64 = torch.zeros_like(b)
+    P64.apply(0, b, y64)
+    Pd.apply(0, b, yd)
+    (E3, p, _) = Pd.level_info(0)
+    flops = E3[0] * E3[1] * E3[2] * flop_per_elem(3, p + 1)
+    out = {"apply_ms": ta, "apply_fp64_ms": apply64_ms, "speedup_vs_fp64_apply": apply64_ms / ta,
+           "apply_gdofs": N / (ta * 1e-3) / 1e9, "fp64_equivalent_tflops": flops / (ta * 1e-3) / 1e12,
+           "fp64_peak_tflops": peak64, "variant": Pd.level_variants(0)[0],
+           "max_rel_diff_vs_fp64": float((yd - y64).abs().max() / y64.abs().max()),
+           "arith": "double-float: pairs of FP32 numbers (about 48 significant bits), FP64 vectors in and out",
+           "note": "hmg_apply with CUDA events, L2 flushed; fp64_equivalent_tflops = the FP64 operator's "
+                   "algorithmic flops (24n^4+15n^3 per element) / time",
+           "solves": {}}
+    Pd.close()
+    for prec in ("fp64", "fp32", "fp16"):
+        Pm = Problem(dict(prob, smooth_prec=prec, fp64_arith="df64"))
+        um = torch.zeros_like(b)
+        t, st, it = timed_solves(Pm, b, um, flush, stream, reps)
+        r = torch.zeros_like(b)
+        P64.apply(0, um, r)
+        out["solves"][prec + "_v_cycle"] = {
+            "solve_ms": t, "iterations": it, "status": st, "speedup_vs_fp64": t64_ms / t,
+            "fp64_rel_residual": float(torch.linalg.norm(b - r) / torch.linalg.norm(b))}
+        Pm.close()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -427,6 +466,7 @@ def run_gpu(args):
 
     # ---- context blocks (not part of the timed steps)
     mixed = {} if args.host_loop or args.quick else mixed_block(prob, P, b, flush, stream, solve_ms)
+    df64 = {} if args.host_loop or args.quick else df64_block(prob, P, b, flush, stream, solve_ms, t_apply, peak64)
     sweep = [] if args.host_loop or args.quick else sweep_block(flush, stream, peak64, orders=((64, 2), (16, 8), (8, 16)))
     c2 = {} if args.host_loop or args.quick else c2_block(flush, stream)
     batched = {} if args.host_loop or args.quick else batched_block(args.batch)
@@ -467,7 +507,8 @@ def run_gpu(args):
             "e2e_solve": {"ms": e2e_solve_ms, "dof_per_s": N / (e2e_solve_ms * 1e-3), "status": st_h,
                           "iterations": it_h, "call": "hmg_solve_host (page-locked nodal f -> u)",
                           "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8, "max_rel_diff_vs_device": u_err},
-            "mixed_precision": mixed, "sweep_129cube": sweep, "single_solve_16cube_q4": c2,
+            "mixed_precision": mixed, "double_float_operator": df64, "sweep_129cube": sweep,
+            "single_solve_16cube_q4": c2,
             "batched_512": batched, "serving": serving,
             "gpu_launches": launches,
             "clocks": clk.summary(),
@@ -1028,14 +1069,15 @@ def run_mesh_independence(args):
 def run_profile_apply(args):
     """Small fixed launch sequence for ncu: build the hierarchy of the warped var-coef problem
     (--mesh elements per axis, --order p, p-multigrid), then two applies on each of the three
-    finest levels (FP64 hmg_apply, or hmg_apply_f32 with --prec fp32/fp16/bf16) after setup's applies."""
+    finest levels (FP64 hmg_apply, or hmg_apply_f32 with --prec fp32/fp16/bf16) after setup's applies;
+    --arith df64: the finest FP64 operator in double-float arithmetic."""
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     import synth
     from paper_1402_5938_gb300 import Problem
-    prob = synth.warped_var3d(args.mesh, args.order, hier=args.hier)
+    prob = dict(synth.warped_var3d(args.mesh, args.order, hier=args.hier), fp64_arith=args.arith)
     if args.prec != "fp64":
         prob = dict(prob, smooth_prec=args.prec)
     P = Problem(prob)
@@ -1083,6 +1125,8 @@ def main():
     ap.add_argument("--order", type=int, default=4, help="--profile-apply: polynomial order")
     ap.add_argument("--prec", choices=["fp64", "fp32", "fp16", "bf16"], default="fp64",
                     help="--profile-apply: precision of the applied operator; --host-loop: of the V-cycle")
+    ap.add_argument("--arith", choices=["fp64", "df64"], default="fp64",
+                    help="--profile-apply: arithmetic of the finest FP64 operator (df64: double-float)")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)
