@@ -686,7 +686,9 @@ def serve_block(R=200, slots=8):
     measured saturated rate, and the plain FP64 solver through the same server with one worker
     (one request at a time) and with `slots` workers, on the same arrivals. p50/p99 latency (submit
     to result on the host, setup of each new hierarchy included) and solves/s. Before the timed
-    runs, 48 other requests of the stream are served untimed in each precision (kernel loading)."""
+    runs, 48 other requests of the stream are served untimed in each precision (kernel loading).
+    One more row: the mixed server whose requests also take the double-float finest operator
+    (fp64_arith = df64, orders 1-8; higher orders keep the native FP64 one)."""
     import numpy as np
 
     import synth
@@ -695,7 +697,7 @@ def serve_block(R=200, slots=8):
     fs = [synth.nodal_field(seed, desc_ndof(prob)) for prob, seed, _ in reqs]
     gaps = np.array([g for _, _, g in reqs])
 
-    def serve(scale, nslots, prec):
+    def serve(scale, nslots, prec, arith="fp64"):
         srv = Server(0, 160 << 30, nslots)
         arr = np.cumsum(gaps * scale)
         t0 = time.perf_counter()
@@ -704,7 +706,8 @@ def serve_block(R=200, slots=8):
             dt = t0 + a - time.perf_counter()
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(srv.submit(dict(prob, smooth_prec=prec), f, rtol=1e-8, mode="pcg", maxit=500))
+            tickets.append(srv.submit(dict(prob, smooth_prec=prec, fp64_arith=arith), f, rtol=1e-8, mode="pcg",
+                                      maxit=500))
         lat, ok, done_at, failed, its = [], 0, [], [], []
         for i, ((t, n), a) in enumerate(zip(tickets, arr)):
             st, u, it, res, l = srv.wait(t, n)
@@ -720,23 +723,24 @@ def serve_block(R=200, slots=8):
         srv.close()
         return dict(p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
                     solves_per_s=R / span, ok=ok, offered_per_s=R / arr[-1], mean_iterations=float(np.mean(its)),
-                    failed=failed, slots=nslots, v_cycle=prec)
+                    failed=failed, slots=nslots, v_cycle=prec, fp64_arith=arith)
 
     # warm-up: 48 other requests of the same stream, untimed, so that no timed run pays the
     # one-time loading of kernels on their first launch (each (dimension, order) brings its own)
-    for prec in ("fp32", "fp64"):
+    for prec, arith in (("fp32", "fp64"), ("fp64", "fp64"), ("fp32", "df64")):
         srv = Server(0, 160 << 30, slots)
         warm = [synth.serving_request(i) for i in range(R, R + 48)]
-        for t, n in [srv.submit(dict(p, smooth_prec=prec), synth.nodal_field(sd, desc_ndof(p)), rtol=1e-8,
-                                mode="pcg", maxit=500) for p, sd, _ in warm]:
+        for t, n in [srv.submit(dict(p, smooth_prec=prec, fp64_arith=arith), synth.nodal_field(sd, desc_ndof(p)),
+                                rtol=1e-8, mode="pcg", maxit=500) for p, sd, _ in warm]:
             srv.wait(t, n)
         srv.close()
     hot = serve(1.0, slots, "fp32")
     cool = serve(max(1.0, (R / gaps.sum()) / (0.5 * hot["solves_per_s"])), slots, "fp32")
     fp64_one = serve(1.0, 1, "fp64")
     fp64_slots = serve(1.0, slots, "fp64")
+    hot_df = serve(1.0, slots, "fp32", "df64")
     return {"serve": f"{R} requests, Poisson 2000/s", "mixed_at_2000_per_s": hot, "mixed_below_saturation": cool,
-            "fp64_one_at_a_time": fp64_one, "fp64_same_slots": fp64_slots,
+            "mixed_df64_at_2000_per_s": hot_df, "fp64_one_at_a_time": fp64_one, "fp64_same_slots": fp64_slots,
             "mixed_over_fp64_one_at_a_time_solves_per_s": hot["solves_per_s"] / fp64_one["solves_per_s"]}
 
 

@@ -67,6 +67,40 @@ def test_descriptor_defaults_follow_the_paper(hmg):
     assert d.arnoldi_iters == 10 and d.cheb_lo_frac == 0.25 and d.n_hlevels == 3
 
 
+def test_descriptor_layout_matches_the_c_header(hmg, tmp_path):
+    """The ctypes descriptor has the C struct's size and every field at the C offset (a field
+    added on one side only would shift the ones after it), and the defaults leave the finest
+    operator in native FP64 arithmetic."""
+    import ctypes
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    names = [f[0] for f in hmg.Desc._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "hmg.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(hmg_desc));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(hmg_desc, {n}));\n' for n in names) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(hmg.Desc)
+    for n, off in zip(names, vals[1:]):
+        assert getattr(hmg.Desc, n).offset == off, n
+    d = hmg.Desc()
+    assert hmg.lib().hmg_desc_default(ctypes.byref(d)) == 0
+    assert d.fp64_arith == 0
+    prob = dict(dim=3, nelem=(2, 2, 2), order=4)
+    assert hmg.make_desc(prob).fp64_arith == 0
+    assert hmg.make_desc(dict(prob, fp64_arith="df64")).fp64_arith == 1
+
+
 def test_status_strings(hmg):
     lib = hmg.lib()
     for s in range(-7, 1):
@@ -109,7 +143,7 @@ def test_header_is_plain_c(tmp_path):
         "  hmg_problem* p = 0;\n"
         "  (void)d; (void)p;\n"
         "  return (int)HMG_OK + (int)HMG_HIER_P + (int)HMG_SMOOTH_BLOCKJACOBI + (int)HMG_MODE_PCG +\n"
-        "         (int)HMG_PREC_BF16 - 7;\n"
+        "         (int)HMG_PREC_BF16 + (int)HMG_ARITH_DF64 - 8;\n"
         "}\n")
     r = subprocess.run([cc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I",
                         os.path.join(root, "include"), "-c", str(src), "-o", str(tmp_path / "use_hmg.o")],

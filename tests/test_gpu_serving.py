@@ -83,6 +83,7 @@ def test_server_rejects_requests_beyond_budget(hmg):
 def test_estimate_bounds_allocation(hmg):
     for prob in (synth.warped_var3d(8, 4, hier="h"), synth.warped_var3d(8, 4, hier="p"),
                  dict(synth.warped_var3d(4, 8, hier="p"), smooth_prec="fp32"), synth.mms2d_poisson(8, 4),
+                 dict(synth.warped_var3d(8, 4, hier="p"), smooth_prec="fp32", fp64_arith="df64"),
                  dict(synth.warped_var3d(4, 6, hier="p"), smoother="blockjacobi"),
                  synth.problem(2, 8, 8, hier="h", smoother="l1jacobi")):
         res, peak = hmg.estimate_bytes(prob)
