@@ -45,6 +45,7 @@ struct BLev {
   long long off;          // the member's segment in the level's super-vectors
   const double* G;        // FP64 factors [E][NC][NP]
   const void* Glow;       // reduced-precision factors (grouped layout)
+  const void* Gdf;        // finest level, double-float operator: the FP64 factors as float pairs
   const float* gsc;
   const double* Ainv;     // coarsest level: dense inverse of the interior operator
   const long long* gmap;  // interior -> global node
@@ -105,6 +106,20 @@ kb_apply_low(const float* __restrict__ X, float* __restrict__ Y, const BLev* __r
   extern __shared__ __align__(16) float smem_blow[];
   pencil_tile<DIM, N, GT, 2>(X + L.off, Y + L.off, static_cast<const GT*>(L.Glow), L.gsc, L.m, t1d, alpha,
                              (long long)w.y, smem_blow);
+}
+
+// the finest FP64 operator in double-float arithmetic (members built with fp64_arith = df64)
+template <int DIM, int N>
+__global__ void __launch_bounds__(PencilCfg<DIM, N, df64>::THREADS)
+kb_apply_df64(const double* __restrict__ X, double* __restrict__ Y, const BLev* __restrict__ lev,
+              const int2* __restrict__ tab, const int* __restrict__ gid, const int* __restrict__ active,
+              const __grid_constant__ PencilTab<N, df64> t1d, const df64 alpha) {
+  const int2 w = tab[blockIdx.x];
+  if (!active[gid[w.x]]) return;
+  const BLev& L = lev[w.x];
+  extern __shared__ __align__(16) unsigned char smem_bdf[];
+  pencil_tile<DIM, N, df64, 2, df64, double>(X + L.off, Y + L.off, static_cast<const df64*>(L.Gdf), nullptr, L.m,
+                                             t1d, alpha, (long long)w.y, reinterpret_cast<df64*>(smem_bdf));
 }
 
 // ---- elementwise steps over super-vectors: one block per chunk, chunk -> member ----
@@ -351,6 +366,9 @@ long long round_chunk(long long n) { return (n + kChunk - 1) / kChunk * kChunk; 
 struct BGroup {
   int dim = 0, nlev = 0, prec = 0, smoother = 0, nu_pre = 0, nu_post = 0;
   bool mixed = false, flexible = false;
+  bool df64 = false;               // finest FP64 operator in double-float arithmetic
+  int2* d_tdf = nullptr;           // its work table (member, group of elements), level 0
+  int n_tdf = 0;
   std::vector<int> gids;           // plan-wide ids of the members
   std::vector<int> orders;         // per level
   int* d_gid = nullptr;
@@ -464,7 +482,41 @@ struct GroupRun {
   cudaStream_t s;
   const hmg_desc& D;  // the first member's descriptor (the group shares the smoother settings)
 
+  hmg_status apply_df64(const double* x, double* y, double alpha) {
+    if (G.n_tdf == 0) return HMG_OK;
+    Basis1D basis;
+    make_basis(G.orders[0], &basis);
+    auto go = [&](auto nc, auto dc) -> cudaError_t {
+      constexpr int N = decltype(nc)::value, DIM = decltype(dc)::value;
+      using C = PencilCfg<DIM, N, df64>;
+      auto kern = kb_apply_df64<DIM, N>;
+      cudaError_t e2 = ensure_smem(kern, C::SMEM);
+      if (e2 != cudaSuccess) return e2;
+      kern<<<G.n_tdf, C::THREADS, C::SMEM, s>>>(x, y, G.d_lev[0], G.d_tdf, G.d_gid, B.active,
+                                                 make_pencil_tab<N, df64>(basis), df64(alpha));
+      return counted(cudaGetLastError());
+    };
+    auto by_dim = [&](auto nc) -> cudaError_t {
+      return G.dim == 3 ? go(nc, std::integral_constant<int, 3>{}) : go(nc, std::integral_constant<int, 2>{});
+    };
+    static_assert(kDf64MaxN == 9, "the dispatch below covers N = 2..9");
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (basis.n) {
+      case 2: e = by_dim(std::integral_constant<int, 2>{}); break;
+      case 3: e = by_dim(std::integral_constant<int, 3>{}); break;
+      case 4: e = by_dim(std::integral_constant<int, 4>{}); break;
+      case 5: e = by_dim(std::integral_constant<int, 5>{}); break;
+      case 6: e = by_dim(std::integral_constant<int, 6>{}); break;
+      case 7: e = by_dim(std::integral_constant<int, 7>{}); break;
+      case 8: e = by_dim(std::integral_constant<int, 8>{}); break;
+      case 9: e = by_dim(std::integral_constant<int, 9>{}); break;
+      default: break;
+    }
+    BTRY(e);
+    return HMG_OK;
+  }
   hmg_status apply64(int k, const double* x, double* y, double alpha) {
+    if (k == 0 && G.df64) return apply_df64(x, y, alpha);
     const int n = G.n_t64[k];
     if (n == 0) return HMG_OK;
     const int dim = G.dim, v = G.v64[k];
@@ -779,7 +831,8 @@ hmg_status add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cud
 // Signature of a hierarchy's structure: members of one group share it.
 std::vector<long long> signature(const ProblemImpl& P) {
   const hmg_desc& D = P.desc;
-  std::vector<long long> s = {D.dim, (long long)P.L.size(), D.smoother, D.nu_pre, D.nu_post, D.smooth_prec};
+  std::vector<long long> s = {D.dim, (long long)P.L.size(), D.smoother, D.nu_pre, D.nu_post, D.smooth_prec,
+                              (long long)(P.L[0].v64 == kApply64Df)};
   for (const Level& l : P.L) s.push_back(l.m.p);
   return s;
 }
@@ -792,6 +845,7 @@ hmg_status build_group(BatchPlan& B, BGroup& G) {
   G.prec = D0.smooth_prec;
   G.mixed = D0.smooth_prec != HMG_PREC_FP64;
   G.flexible = D0.smooth_prec == HMG_PREC_FP16 || D0.smooth_prec == HMG_PREC_BF16;
+  G.df64 = P0.L[0].v64 == kApply64Df;
   G.smoother = D0.smoother;
   G.nu_pre = D0.nu_pre;
   G.nu_post = D0.nu_post;
@@ -824,7 +878,7 @@ hmg_status build_group(BatchPlan& B, BGroup& G) {
   for (int k = 0; k < G.nlev; ++k) {
     std::vector<BLev> lev(nm);
     std::vector<int> cmem;
-    std::vector<int2> t64, tlow;
+    std::vector<int2> t64, tlow, tdf;
     long long o = 0;
     // the FP64 apply of a group: block shape 0 (about one warp of whole elements per block), which
     // suits the small meshes batches are made of
@@ -841,6 +895,7 @@ hmg_status build_group(BatchPlan& B, BGroup& G) {
       L.off = o;
       L.G = l.G;
       L.Glow = l.Glow;
+      L.Gdf = l.Gdf;
       L.gsc = l.gsc;
       L.Ainv = l.Ainv;
       L.gmap = l.gmap;
@@ -850,6 +905,8 @@ hmg_status build_group(BatchPlan& B, BGroup& G) {
       for (long long e = 0; e < l.m.nelem; e += neg) t64.push_back(make_int2(m, (int)e));
       if (G.mixed)
         for (long long g = 0; g * epb < l.m.nelem; ++g) tlow.push_back(make_int2(m, (int)g));
+      if (k == 0 && G.df64)  // the double-float pencil form groups elements as the FP32 one does
+        for (long long g = 0; g * epb < l.m.nelem; ++g) tdf.push_back(make_int2(m, (int)g));
       o += seg;
     }
     G.len[k] = o;
@@ -861,6 +918,10 @@ hmg_status build_group(BatchPlan& B, BGroup& G) {
     if (need64) BTRY(B.upload(&G.d_t64[k], t64));
     G.n_tlow[k] = G.mixed ? (int)tlow.size() : 0;
     if (G.mixed) BTRY(B.upload(&G.d_tlow[k], tlow));
+    if (k == 0 && G.df64) {
+      G.n_tdf = (int)tdf.size();
+      BTRY(B.upload(&G.d_tdf, tdf));
+    }
     // V-cycle vectors and the smoother's inverse diagonal, in the V-cycle precision
     void** vs[4] = {&G.vb[k], &G.vx[k], &G.vr[k], &G.vd[k]};
     for (void** v : vs) BTRY(B.alloc((unsigned char**)v, (size_t)o * vsz));

@@ -185,6 +185,48 @@ def test_batch_plan_groups_and_repeats(hmg, prec):
         P.close()
 
 
+def test_batch_plan_double_float_operator(hmg):
+    """Members built with the double-float finest operator (fp64_arith = df64) form groups of
+    their own and run it inside the plan: two solves in a row give every member the iterations and
+    solution of solving it alone, and its true FP64 residual (native FP64 operator) meets 1e-8."""
+    probs, bs = [], []
+    for i in range(8):
+        prob, seed = synth.batched_problem(i)
+        prob = dict(prob, smooth_prec="fp32", fp64_arith="df64" if i % 2 == 0 else "fp64")
+        P = hmg.Problem(prob)
+        assert (P.level_variants(0)[0] == 7) == (i % 2 == 0)
+        N = P.ndof(0)
+        b = torch.zeros(N, dtype=torch.float64, device=DEV)
+        P.rhs(torch.from_numpy(synth.nodal_field(seed, N)).to(DEV), b)
+        probs.append(P)
+        bs.append(b)
+    plan = hmg.BatchPlan(probs, "pcg", maxit_cap=300)
+    groups, _ = plan.info()
+    assert groups == len({(P.level_info(0)[1], P.level_variants(0)[0] == 7) for P in probs})
+    alone = []
+    for P, b in zip(probs, bs):
+        u1 = torch.zeros_like(b)
+        st1, it1, _ = P.solve("pcg", b, u1, rtol=1e-8, maxit=300)
+        alone.append((st1, it1, u1))
+    for rep in range(2):
+        us = [torch.full_like(b, 3.0) for b in bs]
+        sts, its, hists = plan.solve(bs, us, rtol=1e-8, maxit=300)
+        for i, ((st1, it1, u1), st, it, u) in enumerate(zip(alone, sts, its, us)):
+            assert st == st1 == 0 and it == it1, (rep, i, it, it1)
+            assert float(torch.linalg.norm(u - u1) / torch.linalg.norm(u1)) < 1e-8
+    for i, (P, b, u) in enumerate(zip(probs, bs, us)):
+        if i % 2:
+            continue
+        ref = hmg.Problem(dict(synth.batched_problem(i)[0], smooth_prec="fp32"))
+        r = torch.zeros_like(b)
+        ref.apply(0, u, r)
+        assert float(torch.linalg.norm(b - r) / torch.linalg.norm(b)) <= 1.1e-8
+        ref.close()
+    plan.close()
+    for P in probs:
+        P.close()
+
+
 def test_batch_plan_mg_mode_2d_and_3d(hmg):
     """MG iteration in a plan that mixes 2D and 3D problems (separate groups)."""
     probs, bs = [], []
