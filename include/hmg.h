@@ -172,7 +172,8 @@ size_t hmg_device_bytes(const hmg_problem* prob);
  * factors read at their use (5) or one phase ahead (6, orders 7-8)) and the mixed V-cycle's operator
  * (pencil form, when a thread loads its factors: 0 one phase before the pointwise product, 1 before
  * the first phase, 2 at their use; 3 the tensor-core form, 16-bit factors at 3D orders 1-4, built
- * when the environment sets HMG_TC16=1). */
+ * when the environment sets HMG_TC16=1). FP64 variant 7 on the finest level: the double-float
+ * operator that hmg_desc.fp64_arith = HMG_ARITH_DF64 asks for (never chosen by timing). */
 hmg_status hmg_level_variants(const hmg_problem* prob, int level, int* v_fp64, int* v_vcycle);
 
 /* Physical node coordinates of a level, written as xyz_dev[c * N + node], c < dim (the warp map,
