@@ -102,8 +102,11 @@ typedef enum { HMG_ARITH_FP64 = 0, HMG_ARITH_DF64 = 1 } hmg_arith;
  *                        significant bits; rounding errors a few 2^-46 relative to the magnitudes
  *                        summed instead of 2^-53), for GPUs whose FP64 rate is a small fraction of
  *                        their FP32 rate. Finest orders 1-8 (else FP64 as by default); one more
- *                        copy of the finest level's factors (8 bytes per value). Not in the paper:
- *                        an arithmetic choice of this implementation.
+ *                        copy of the finest level's factors (8 bytes per value). Values (factors,
+ *                        x, intermediates) must stay inside FP32's exponent range (magnitudes
+ *                        below about 3e38; below about 1e-31 the low word loses bits, below 1e-38
+ *                        the value itself). Not in the paper: an arithmetic choice of this
+ *                        implementation.
  */
 typedef struct hmg_desc {
   int dim;
